@@ -1,0 +1,366 @@
+"""Benchmark of the equilibrium projection on GB300 (one JSON line on stdout, rank 0).
+
+Workload: one 512^3 periodic field, FP32, 5000 Voronoi grains with per-grain stress ~ N(0, 200 MPa)
+per Voigt component plus voxel noise ~ N(0, 20 MPa), DDO (modified wavevector).  A step is one
+eq_project of the field (every pass of the hot path including the FP64 mean and norm
+finalisation).  The field (3.2 GB in, 3.2 GB out) is larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank projects its own field (replicas, no collective on the data path);
+value = voxels of all ranks / max elapsed over ranks.  ``--impl reference`` times the CPU FP64
+oracle (the only other place this file runs it) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "equilibrated voxels/s at 512³ (FP32 vs FP64), % HBM roofline; served p50/p99"
+UNIT = "voxels/s"
+N = 512
+GRAINS = 5000
+SEED = 210501612 + 2            # workload seed of the 512^3 Voronoi field (rank added)
+BYTES_PER_VOXEL_PASS = 48        # FP32: read 6 x 4 B + write 6 x 4 B per voxel
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=N)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64, cuFFT, e2e and CPU comparison legs")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------ CPU oracle leg
+
+def cpu_oracle_sample(n_cpu: int = 256):
+    """Time the FP64 oracle on one n_cpu^3 field of the same recipe (grains scaled with volume)."""
+    import oracle
+    from fieldgen import voronoi_stress_field
+    grains = max(8, int(round(GRAINS * (n_cpu / N) ** 3)))
+    s = voronoi_stress_field((n_cpu,) * 3, grains, 200.0, 20.0, SEED).numpy()
+    t0 = time.perf_counter()
+    out = oracle.project(s, "ddo")
+    oracle.norms(s, out, "ddo")
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    return {"value": n_cpu ** 3 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one {n_cpu}^3 field ({grains} grains, same recipe), FP64 numpy/scipy "
+                      f"oracle: projection + norms, {dt:.2f} s wall on {cores} host threads"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_cpu = 128
+    for _ in range(args.warmup):
+        cpu_oracle_sample(64)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_sample(n_cpu))
+    el = time.perf_counter() - t0
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{N}^3 Voronoi {GRAINS} grains DDO; each reference step is a "
+                                   f"bounded sample: one {n_cpu}^3 field of the same recipe",
+                       "grid": [N, N, N], "op": "ddo"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join("/tmp", f"eq_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9 or (self.uuid and self.uuid not in parts[0]):
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ GPU legs
+
+def cufft_baseline(x, steps: int):
+    """Comparison only: torch.fft (cuFFT) r2c/c2r + the projector in torch elementwise ops."""
+    import torch
+    n = x.shape[-1]
+    dev = x.device
+    m = torch.arange(n, device=dev, dtype=torch.float64)
+    s = torch.where(m < n / 2, m, m - n)
+    xi = torch.sin(2 * math.pi * s / n)
+    xi[n // 2] = 0.0
+    xi = xi.float()
+    xz, xy, xx = xi.view(n, 1, 1), xi.view(1, n, 1), xi[: n // 2 + 1].view(1, 1, n // 2 + 1)
+    k2 = xx * xx + xy * xy + xz * xz
+    inv = torch.where(k2 > 0, torch.rsqrt(torch.where(k2 > 0, k2, torch.ones_like(k2))),
+                      torch.zeros_like(k2))
+    n0, n1, n2 = xx * inv, xy * inv, xz * inv
+
+    def step():
+        sh = torch.fft.rfftn(x, dim=(-3, -2, -1))
+        a = sh  # (6, nz, ny, nx/2+1) Voigt xx, yy, zz, yz, xz, xy
+        v0 = a[0] * n0 + a[5] * n1 + a[4] * n2
+        v1 = a[5] * n0 + a[1] * n1 + a[3] * n2
+        v2 = a[4] * n0 + a[3] * n1 + a[2] * n2
+        sc = n0 * v0 + n1 * v1 + n2 * v2
+        o = torch.stack([a[0] - 2 * n0 * v0 + sc * n0 * n0, a[1] - 2 * n1 * v1 + sc * n1 * n1,
+                         a[2] - 2 * n2 * v2 + sc * n2 * n2, a[3] - n1 * v2 - v1 * n2 + sc * n1 * n2,
+                         a[4] - n0 * v2 - v0 * n2 + sc * n0 * n2, a[5] - n0 * v1 - v0 * n1 + sc * n0 * n1])
+        o[:, 0, 0, 0] = a[:, 0, 0, 0]
+        return torch.fft.irfftn(o, s=x.shape[-3:], dim=(-3, -2, -1))
+
+    for _ in range(2):
+        y = step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        y = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return y, ms
+
+
+def kernel_traffic(dominant: str):
+    """DRAM traffic per launch of `dominant` from the committed ncu summary, if the kernel
+    sources are unchanged since it was taken (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic_512cubed_fp32.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("traffic_bytes_per_launch", {}).get(dominant)
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2105_01612_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from fieldgen import voronoi_stress_field
+    import paper_2105_01612_gb300 as eq
+    from paper_2105_01612_gb300 import _build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu_base = None
+    if rank == 0 and not args.no_extras:
+        cpu_base = cpu_oracle_sample(256)          # before any CUDA work on this process
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    _build.build()
+    n = args.size
+    vox = n ** 3
+    x = voronoi_stress_field((n, n, n), GRAINS, 200.0, 20.0, SEED + rank, dtype=torch.float32,
+                             device=dev).unsqueeze(0).contiguous()
+    out = torch.empty_like(x)
+    plan = eq.Plan(n, n, n, torch.float32, 1, "ddo", device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        plan.project(x, out)
+    torch.cuda.synchronize()
+    plan.set_timing(args.steps)
+    props = torch.cuda.get_device_properties(dev)
+    clk = ClockSampler(str(getattr(props, "uuid", "")))
+    clk.start()
+    time.sleep(0.1)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.project(x, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    per_pass, ncalls = plan.pass_ms()
+    nrm = plan.norms()[0]
+    ms_step = ms_total / args.steps
+    value = world * vox * args.steps / (ms_total / 1e3)
+
+    # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
+    peak, peak_kind = measured_peaks()
+    big = {k: v for k, v in per_pass.items() if "finalise" not in k}
+    dominant = max(big, key=big.get)
+    dom_ms = per_pass[dominant] / max(1, ncalls)
+    dom_bytes = BYTES_PER_VOXEL_PASS * vox + (24 * vox if dominant == "z_inverse" else 0)
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    traffic = kernel_traffic(dominant)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{n}^3 periodic field, {GRAINS} Voronoi grains N(0,200 MPa) + "
+                               f"noise N(0,20 MPa), FP32, DDO, one field per GPU",
+                   "grid": [n, n, n], "op": "ddo", "nyq": "keep", "batch_per_gpu": 1,
+                   "l2": "inputs larger than L2 (3.2 GB per field); no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic,
+                     "algorithmic_bytes_per_launch": dom_bytes},
+        "pipeline": {"pass_ms": {k: v / max(1, ncalls) for k, v in per_pass.items()},
+                     "algorithmic_frac": BYTES_PER_VOXEL_PASS * vox / (ms_step / 1e3) / 1e9 / peak,
+                     "five_pass_frac": 5 * BYTES_PER_VOXEL_PASS * vox / (ms_step / 1e3) / 1e9 / peak},
+        "gpu_launches": 7 * args.steps,
+        "clocks": clocks,
+        "norms": {k: nrm[k] for k in ("norm_in", "norm_out", "resid_rel", "div_in_l2", "div_out_l2")},
+    }
+    if rank == 0 and not args.no_extras:
+        # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+        hin = x.cpu().pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        plan.project_host(hin, hout)
+        ke = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            plan.project_host(hin, hout)
+            plan.norms()
+        te = (time.perf_counter() - t0) / ke
+        line["e2e"] = {"value": vox / te, "unit": UNIT, "h2d_bytes_per_step": hin.numel() * 4,
+                       "d2h_bytes_per_step": hout.numel() * 4 + 112,
+                       "ms_per_step": te * 1e3}
+        del hin, hout
+        # the FP64 path on the same field
+        x64 = x.double()
+        o64 = torch.empty_like(x64)
+        p64 = eq.Plan(n, n, n, torch.float64, 1, "ddo", device=dev)
+        p64.project(x64, o64)
+        torch.cuda.synchronize()
+        k64 = max(1, min(args.steps, 3))
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(k64):
+            p64.project(x64, o64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / k64
+        w = torch.tensor([1.0, 1, 1, 2, 2, 2], device=dev, dtype=torch.float64).view(1, 6, 1, 1, 1)
+        d = out.double() - o64
+        fp32_err = math.sqrt(float((w * d * d).sum() / (w * o64 * o64).sum()))
+        del d
+        line["fp64"] = {"value": vox / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                        "fp32_vs_fp64_rel_l2": fp32_err}
+        p64.close()
+        del x64, o64
+        # cuFFT + elementwise projector (comparison baseline, library kernels)
+        y, msc = cufft_baseline(x[0], max(1, min(args.steps, 5)))
+        dd = (y.double() - out[0].double())
+        agree = math.sqrt(float((w[0] * dd * dd).sum() / (w[0] * out[0].double() ** 2).sum()))
+        line["cufft_baseline"] = {"value": vox / (msc / 1e3), "unit": UNIT, "ms_per_step": msc,
+                                  "rel_l2_vs_ours": agree}
+        del y, dd
+        line["cpu_baseline"] = cpu_base
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,128 @@
+/*
+ * eq.h - C ABI of the GB300 equilibrium-projection library (libeq.so).
+ *
+ * The operation (Zhou, Lebensohn, Reischig, Ludwig, Bhattacharya, "Imposing equilibrium on
+ * measured 3-D stress fields using Hodge decomposition and FFT-based optimization"):
+ * given a voxelized symmetric stress field S on a periodic nx x ny x nz grid, return the field
+ * closest to it in L^2 whose divergence vanishes (Sec. 3.2).  By the Hodge decomposition of
+ * Sec. 3.1 (Theorem 2) and the Fourier treatment of Sec. 4 this is, per wavevector k with
+ * operator symbol Xi(k) and n = Xi / |Xi|,
+ *     S^(k) <- S^ - n (x) (S^ n) - (S^ n) (x) n + (n . S^ n) n (x) n,
+ * with the mean (k = 0) kept (Sec. 3.2, c0 = mean of S).  Xi is the continuous wavevector (CDO,
+ * Sec. 4.1, Nyquist symbol 0) or the central-difference "modified" wavevector
+ * sin(2 pi m / N) / h (DDO, Sec. 4.2) used for fields with grain-boundary discontinuities.
+ *
+ * Field layout at the boundary (all entry points): a contiguous array of `batch` fields, each
+ * [6][nz][ny][nx] with x fastest, components in Voigt order (xx, yy, zz, yz, xz, xy), element
+ * type float (EQ_F32) or double (EQ_F64).  Device pointers are CUDA device memory of the
+ * current device, owned by the caller; host pointers are host memory owned by the caller.
+ *
+ * Errors: every entry point returns an eq_status; no C++ exception crosses the ABI.  A failed
+ * call leaves a message for eq_last_error() (per thread).  Errors of work already queued on a
+ * stream (asynchronous CUDA errors) surface at the next eq_norms / eq_serve_poll.
+ */
+#ifndef EQ_H
+#define EQ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EQ_OK = 0,
+  EQ_ERR_INVALID = 1,    /* bad argument, unsupported size or option */
+  EQ_ERR_OOM = 2,        /* device or host allocation failed; over the server's HBM budget */
+  EQ_ERR_CUDA = 3,       /* a CUDA call failed (message in eq_last_error) */
+  EQ_ERR_TIMEOUT = 4,    /* a bounded wait ran out */
+  EQ_ERR_BUSY = 5,       /* server queue full */
+  EQ_PENDING = 6,        /* request not finished yet */
+  EQ_ERR_NOT_FOUND = 7   /* unknown ticket */
+} eq_status;
+
+typedef enum { EQ_F32 = 0, EQ_F64 = 1 } eq_dtype;
+
+/* Derivative symbol: DDO = central-difference modified wavevector (Sec. 4.2, eq. eq:diff);
+ * CDO = continuous wavevector 2 pi s / L with 0 at the Nyquist index (Sec. 4.1). */
+typedef enum { EQ_OP_DDO = 0, EQ_OP_CDO = 1 } eq_op;
+
+/* Modes where the symbol vanishes but k != 0 (the Nyquist corners of an even grid).  KEEP
+ * leaves them unchanged (every field is divergence-free there, so the closest field keeps
+ * them; this keeps the map an orthogonal projection).  ZERO removes them, which is what the
+ * literal Euler-Lagrange route inc(inc(S) / biharmonic) of Sec. 3.2-3.3 produces. */
+typedef enum { EQ_NYQ_KEEP = 0, EQ_NYQ_ZERO = 1 } eq_nyquist;
+
+typedef struct {
+  eq_op op;              /* default EQ_OP_DDO */
+  double hx, hy, hz;     /* voxel spacing, default 1 (all > 0) */
+  eq_nyquist nyq;        /* default EQ_NYQ_KEEP */
+  int want_linf;         /* 1: also compute resid_linf (needs d_in != d_out); default 1 */
+} eq_plan_opts;
+
+/* Per-field diagnostics, FP64.  ||A|| = sqrt(mean over voxels of A:A) with A:B = sum_ij A_ij B_ij
+ * (off-diagonal Voigt entries weigh 2); resid = S_in - S_out; div_* is the RMS of the divergence
+ * vector computed with the plan's operator (Sec. 4, Fig. 1c,d). */
+typedef struct {
+  double mean[6];        /* c0, per Voigt component (Sec. 3.2) */
+  double norm_in, norm_out;
+  double resid_l2, resid_rel, resid_linf;
+  double div_in_l2, div_out_l2;
+  int flags;             /* EQ_FLAG_* */
+} eq_norms_t;
+
+#define EQ_FLAG_NONFINITE 1   /* the input held a NaN or an infinity */
+#define EQ_FLAG_NO_LINF 2     /* resid_linf was not computed (in-place call or want_linf = 0) */
+
+typedef struct eq_plan eq_plan;
+typedef struct eq_server eq_server;
+
+/* Default options (DDO, unit spacing, KEEP, want_linf = 1). */
+void eq_plan_opts_default(eq_plan_opts* opts);
+
+/* Create a plan for `batch` fields of one grid size.  Sizes are 1..1024 per axis.  Allocates
+ * the plan's device tables and reduction buffers on the current device (no field-sized
+ * workspace: the spectrum lives in the caller's output buffer).  opts == NULL: defaults. */
+eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
+                         const eq_plan_opts* opts, eq_plan** out);
+
+/* Project the plan's `batch` fields d_in -> d_out on `cuda_stream` (a cudaStream_t, NULL =
+ * legacy default stream).  d_out may equal d_in (then resid_linf is not computed).  Both must
+ * hold batch * 6 * nx * ny * nz elements of the plan's dtype and be 16-byte aligned.  The call
+ * only enqueues work; it returns before the result is ready.  Steps (Sec. 3.3): forward 3-D
+ * DFT, per-mode projector, inverse DFT, norms; the mean is taken in FP64. */
+eq_status eq_project(eq_plan* plan, const void* d_in, void* d_out, void* cuda_stream);
+
+/* Same as eq_project with host buffers: copies host_in to a plan-owned device buffer
+ * (allocated on first use, 2 x field bytes), projects, copies back to host_out, and waits for
+ * completion.  Host buffers should be pinned for full copy bandwidth. */
+eq_status eq_project_host(eq_plan* plan, const void* host_in, void* host_out, void* cuda_stream);
+
+/* Wait for the plan's last eq_project and copy its `batch` diagnostics to host_out. */
+eq_status eq_norms(eq_plan* plan, eq_norms_t* host_out);
+
+/* Device bytes owned by the plan (tables, reduction buffers, host-call staging if any). */
+size_t eq_plan_workspace_bytes(const eq_plan* plan);
+
+void eq_plan_destroy(eq_plan* plan);
+
+/* Per-pass timing with CUDA events recorded on the launch stream between the kernels of
+ * eq_project (for measurement; off by default).  max_calls > 0 reserves event sets for that many
+ * subsequent eq_project calls and turns timing on; 0 turns it off.  The passes, in order:
+ *   0 z forward, 1 mean finalisation, 2 y forward, 3 x forward + projector + x inverse,
+ *   4 y inverse, 5 z inverse, 6 norm finalisation. */
+#define EQ_NUM_PASSES 7
+eq_status eq_plan_set_timing(eq_plan* plan, int max_calls);
+
+/* Wait for the timed calls and return, per pass, the summed device time in milliseconds over
+ * them (ms_out: EQ_NUM_PASSES entries) and their number; then reset the counters. */
+eq_status eq_plan_pass_ms(eq_plan* plan, double* ms_out, int* ncalls_out);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* eq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EQ_H */

@@ -1,0 +1,178 @@
+"""GB300-native equilibrium projection of voxelized stress fields.
+
+Python face of libeq.so (include/eq.h): the closest L^2 divergence-free field to a measured
+symmetric stress field on a periodic grid (Zhou et al., Sec. 3.2), computed in Fourier space with
+the continuous (CDO, Sec. 4.1) or the central-difference modified wavevector (DDO, Sec. 4.2).
+PyTorch provides device memory and streams; the work runs in the library's CUDA kernels.
+
+Fields are tensors of shape (B, 6, nz, ny, nx) or (6, nz, ny, nx), x fastest, Voigt order
+(xx, yy, zz, yz, xz, xy), float32 or float64, contiguous, on a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import EqError, EqNorms, EqPlanOpts
+
+__all__ = ["Plan", "project", "eq_plan_create", "eq_project", "eq_project_host", "eq_norms",
+           "eq_plan_workspace_bytes", "eq_plan_destroy", "eq_last_error", "eq_plan_set_timing",
+           "eq_plan_pass_ms", "EqError"]
+
+_OPS = {"ddo": _lib.EQ_OP_DDO, "cdo": _lib.EQ_OP_CDO}
+_NYQ = {"keep": _lib.EQ_NYQ_KEEP, "zero": _lib.EQ_NYQ_ZERO}
+_DT = {torch.float32: _lib.EQ_F32, torch.float64: _lib.EQ_F64}
+
+
+def _opts(op="ddo", h=(1.0, 1.0, 1.0), nyq="keep", want_linf=True) -> EqPlanOpts:
+    o = EqPlanOpts()
+    _lib.load().eq_plan_opts_default(ctypes.byref(o))
+    o.op = _OPS[op]
+    o.hx, o.hy, o.hz = (float(v) for v in h)
+    o.nyq = _NYQ[nyq]
+    o.want_linf = 1 if want_linf else 0
+    return o
+
+
+# ---- C-ABI names (thin marshalling) ------------------------------------------------------
+
+def eq_plan_create(nx, ny, nz, dtype=torch.float32, batch=1, op="ddo", h=(1.0, 1.0, 1.0),
+                   nyq="keep", want_linf=True) -> int:
+    """Returns an opaque plan handle (int) on the current CUDA device."""
+    handle = ctypes.c_void_p()
+    opts = _opts(op, h, nyq, want_linf)
+    st = _lib.load().eq_plan_create(int(nx), int(ny), int(nz), _DT[dtype], int(batch),
+                                    ctypes.byref(opts), ctypes.byref(handle))
+    _lib.check(st, "eq_plan_create")
+    return handle.value
+
+
+def eq_project(plan: int, d_in: int, d_out: int, stream: int = 0) -> None:
+    _lib.check(_lib.load().eq_project(plan, d_in, d_out, stream or None), "eq_project")
+
+
+def eq_project_host(plan: int, h_in: int, h_out: int, stream: int = 0) -> None:
+    _lib.check(_lib.load().eq_project_host(plan, h_in, h_out, stream or None), "eq_project_host")
+
+
+def eq_norms(plan: int, batch: int) -> list:
+    arr = (EqNorms * batch)()
+    _lib.check(_lib.load().eq_norms(plan, arr), "eq_norms")
+    return [arr[i].to_dict() for i in range(batch)]
+
+
+def eq_plan_workspace_bytes(plan: int) -> int:
+    return int(_lib.load().eq_plan_workspace_bytes(plan))
+
+
+def eq_plan_destroy(plan: int) -> None:
+    _lib.load().eq_plan_destroy(plan)
+
+
+def eq_plan_set_timing(plan: int, max_calls: int) -> None:
+    _lib.check(_lib.load().eq_plan_set_timing(plan, int(max_calls)), "eq_plan_set_timing")
+
+
+def eq_plan_pass_ms(plan: int):
+    """(dict pass name -> summed ms, number of timed calls) since the last query."""
+    ms = (ctypes.c_double * _lib.EQ_NUM_PASSES)()
+    n = ctypes.c_int()
+    _lib.check(_lib.load().eq_plan_pass_ms(plan, ms, ctypes.byref(n)), "eq_plan_pass_ms")
+    return dict(zip(_lib.PASS_NAMES, list(ms))), n.value
+
+
+def eq_last_error() -> str:
+    return _lib.load().eq_last_error().decode()
+
+
+# ---- convenience object ------------------------------------------------------------------
+
+class Plan:
+    """A plan for `batch` fields of one grid size and dtype on one device."""
+
+    def __init__(self, nx, ny, nz, dtype=torch.float32, batch=1, op="ddo", h=(1.0, 1.0, 1.0),
+                 nyq="keep", want_linf=True, device=None):
+        self.shape = (int(batch), 6, int(nz), int(ny), int(nx))
+        self.dtype = dtype
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        with torch.cuda.device(self.device):
+            self.handle = eq_plan_create(nx, ny, nz, dtype, batch, op, h, nyq, want_linf)
+
+    def _check(self, t: torch.Tensor, name: str):
+        if not t.is_cuda or t.device != self.device:
+            raise ValueError(f"{name} must be on {self.device}")
+        if t.dtype != self.dtype or not t.is_contiguous() or t.numel() != _numel(self.shape):
+            raise ValueError(f"{name} must be a contiguous {self.dtype} tensor of shape {self.shape}")
+
+    def project(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Enqueue the projection of x into out (allocated if None; may be x itself)."""
+        self._check(x, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        self._check(out, "out")
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            eq_project(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
+        return out
+
+    def project_host(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """Host tensors in and out (pinned for full bandwidth); blocks until done."""
+        for t, n in ((x, "x"), (out, "out")):
+            if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() \
+                    or t.numel() != _numel(self.shape):
+                raise ValueError(f"{n} must be a contiguous host {self.dtype} tensor of shape {self.shape}")
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            eq_project_host(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
+        return out
+
+    def norms(self) -> list:
+        with torch.cuda.device(self.device):
+            return eq_norms(self.handle, self.shape[0])
+
+    def set_timing(self, max_calls: int) -> None:
+        eq_plan_set_timing(self.handle, max_calls)
+
+    def pass_ms(self):
+        with torch.cuda.device(self.device):
+            return eq_plan_pass_ms(self.handle)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return eq_plan_workspace_bytes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            eq_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _numel(shape):
+    n = 1
+    for s in shape:
+        n *= s
+    return n
+
+
+def project(x: torch.Tensor, op="ddo", h=(1.0, 1.0, 1.0), nyq="keep", out=None):
+    """Project a (6, nz, ny, nx) or (B, 6, nz, ny, nx) CUDA tensor; returns (out, norms)."""
+    single = x.dim() == 4
+    xb = x.unsqueeze(0) if single else x
+    b, six, nz, ny, nx = xb.shape
+    if six != 6:
+        raise ValueError("expected 6 Voigt components in dimension -4")
+    plan = Plan(nx, ny, nz, x.dtype, b, op, h, nyq, device=x.device)
+    o = plan.project(xb.contiguous(), None if out is None else out.view(xb.shape))
+    nrm = plan.norms()
+    plan.close()
+    o = o.view(x.shape)
+    return o, (nrm[0] if single else nrm)

@@ -1,0 +1,494 @@
+// eq_api.cu - plans and the C ABI entry points of include/eq.h (host runtime).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/eq.h"
+#include "eq_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+eq_status fail(eq_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+eq_status fail_cuda(cudaError_t e, const char* where) {
+  return fail(EQ_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+}  // namespace
+
+namespace eqk {
+bool length_supported(int n) { return is_pow2(n) && n <= 1024; }
+}  // namespace eqk
+
+// ---------------------------------------------------------------- finalisation kernels
+
+// c0 and ||S_in||^2 per field from the first pass's block partials (fixed order, FP64).
+__global__ void k_finalize_mean(const double* __restrict__ part, int grid, int batch, double vol,
+                                double* __restrict__ mean, double* __restrict__ instats) {
+  for (int f = threadIdx.x; f < batch; f += blockDim.x) {
+    double sq = 0.0, nf = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      double sa = 0.0, sb = 0.0;
+      const double* p = part + ((long long)(f * 3 + c) * grid) * 4;
+      for (int g = 0; g < grid; ++g) {
+        sa += p[g * 4 + 0];
+        sb += p[g * 4 + 1];
+        sq += p[g * 4 + 2];
+        nf += p[g * 4 + 3];
+      }
+      mean[f * 6 + 2 * c] = sa / vol;
+      mean[f * 6 + 2 * c + 1] = sb / vol;
+    }
+    instats[f * 2 + 0] = sq;
+    instats[f * 2 + 1] = nf;
+  }
+}
+
+// eq_norms_t per field from the x-pass spectral sums (Parseval) and the last pass's L-inf.
+__global__ void k_finalize_norms(const double* __restrict__ partx, int gridx,
+                                 const double* __restrict__ partl, int gridl, int batch,
+                                 double vol, const double* __restrict__ mean,
+                                 const double* __restrict__ instats, int linf_flag,
+                                 eq_norms_t* __restrict__ out) {
+  for (int f = threadIdx.x; f < batch; f += blockDim.x) {
+    double r2 = 0.0, di = 0.0, dout = 0.0, o2 = 0.0;
+    const double* p = partx + (long long)f * gridx * 4;
+    for (int g = 0; g < gridx; ++g) {
+      r2 += p[g * 4 + 0];
+      di += p[g * 4 + 1];
+      dout += p[g * 4 + 2];
+      o2 += p[g * 4 + 3];
+    }
+    const double v2 = vol * vol;
+    eq_norms_t n;
+    for (int j = 0; j < 6; ++j) n.mean[j] = mean[f * 6 + j];
+    n.norm_in = sqrt(instats[f * 2 + 0] / vol);
+    n.norm_out = sqrt(o2 / v2);
+    n.resid_l2 = sqrt(r2 / v2);
+    n.resid_rel = n.norm_in > 0.0 ? n.resid_l2 / n.norm_in : 0.0;
+    n.div_in_l2 = sqrt(di / v2);
+    n.div_out_l2 = sqrt(dout / v2);
+    double lm = 0.0;
+    if (partl) {
+      const double* q = partl + (long long)f * 3 * gridl;
+      for (int g = 0; g < 3 * gridl; ++g) lm = fmax(lm, q[g]);
+    }
+    n.resid_linf = lm;
+    n.flags = (instats[f * 2 + 1] > 0.0 ? EQ_FLAG_NONFINITE : 0) | linf_flag;
+    out[f] = n;
+  }
+}
+
+// ---------------------------------------------------------------- plan
+
+struct eq_plan {
+  int nx = 0, ny = 0, nz = 0, batch = 0;
+  eq_dtype dtype = EQ_F32;
+  eq_plan_opts opts{};
+  long long V = 0;
+  size_t esize = 4;
+  int device = 0;
+  int sms = 0;
+  // device tables and reduction buffers (one allocation)
+  void* dmem = nullptr;
+  size_t dbytes = 0;
+  void* tw[3] = {nullptr, nullptr, nullptr};   // x, y, z twiddles
+  void* xi[3] = {nullptr, nullptr, nullptr};   // x, y, z operator symbols
+  int* pairs = nullptr;
+  int npairs = 0;
+  double* part1 = nullptr;     // [batch][3][g1][4]
+  double* partx = nullptr;     // [batch][gx][4]
+  double* partl = nullptr;     // [batch][3][gl]
+  double* mean = nullptr;      // [batch][6]
+  double* instats = nullptr;   // [batch][2]
+  eq_norms_t* norms = nullptr; // [batch]
+  int g1 = 1, gy = 1, gx = 1, gl = 1;
+  eqk::PassInfo info_z_f, info_y_f, info_x, info_y_i, info_z_i;
+  cudaEvent_t done = nullptr;
+  bool have_result = false;
+  // staging for eq_project_host
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  // optional per-pass timing: one set of EQ_NUM_PASSES + 1 events per timed call
+  std::vector<cudaEvent_t> tev;
+  int tcap = 0, tused = 0;
+};
+
+namespace {
+
+cudaError_t pass_info(eq_dtype dt, int n, eqk::PassKind k, eqk::PassInfo* out) {
+  return dt == EQ_F32 ? eqk::pass_info_f32(n, k, out) : eqk::pass_info_f64(n, k, out);
+}
+
+template <typename T> void fill_tables(int n, double h, eq_op op, std::vector<unsigned char>& tw,
+                                       std::vector<unsigned char>& xi) {
+  using T2 = typename eqk::V2<T>::t;
+  tw.resize(sizeof(T2) * n);
+  xi.resize(sizeof(T) * n);
+  T2* w = reinterpret_cast<T2*>(tw.data());
+  T* s = reinterpret_cast<T*>(xi.data());
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < n; ++m) {
+    const double ang = -two_pi * double(m) / double(n);
+    w[m].x = T(std::cos(ang));
+    w[m].y = T(std::sin(ang));
+    // signed frequency; the Nyquist index of an even length gets symbol 0 (CDO and DDO)
+    const int sf = (2 * m < n) ? m : m - n;
+    double v;
+    if (2 * m == n) v = 0.0;
+    else if (op == EQ_OP_CDO) v = two_pi * double(sf) / (double(n) * h);
+    else v = std::sin(two_pi * double(sf) / double(n)) / h;
+    s[m] = T(v);
+  }
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
+  const bool f32 = p->dtype == EQ_F32;
+  cudaEvent_t* ev = nullptr;
+  if (p->tused < p->tcap) ev = &p->tev[(size_t)p->tused++ * (EQ_NUM_PASSES + 1)];
+  auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
+  mark(0);
+  const long long V = p->V;
+  const long long fstride = 6 * V;
+  cudaError_t e;
+  // pass 1: z forward, d_in -> d_out, input statistics
+  eqk::StridedArgs a{};
+  a.field_stride = fstride;
+  a.V = V;
+  {
+    a.in = d_in; a.out = d_out; a.ref = nullptr; a.tw = p->tw[2];
+    a.nstride = (long long)p->ny * p->nx; a.inner = a.nstride; a.outer_stride = 0;
+    a.ncols = a.inner;
+    const int B = p->info_z_f.threads / std::max(1, p->nz / std::min(8, p->nz));
+    a.ntiles = (a.ncols + B - 1) / B;
+    a.partials = p->part1; a.mode = 1;
+    dim3 grid(p->g1, p->batch * 3);
+    e = f32 ? eqk::launch_strided_f32(p->nz, false, a, grid, s)
+            : eqk::launch_strided_f64(p->nz, false, a, grid, s);
+    if (e != cudaSuccess) return fail_cuda(e, "z forward pass");
+  }
+  mark(1);
+  k_finalize_mean<<<1, 128, 0, s>>>(p->part1, p->g1, p->batch, double(V), p->mean, p->instats);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "mean finalisation");
+  mark(2);
+  // pass 2: y forward
+  eqk::StridedArgs ay{};
+  ay.field_stride = fstride; ay.V = V;
+  ay.in = d_out; ay.out = d_out; ay.ref = nullptr; ay.tw = p->tw[1];
+  ay.nstride = p->nx; ay.inner = p->nx; ay.outer_stride = (long long)p->ny * p->nx;
+  ay.ncols = (long long)p->nz * p->nx;
+  {
+    const int B = p->info_y_f.threads / std::max(1, p->ny / std::min(8, p->ny));
+    ay.ntiles = (ay.ncols + B - 1) / B;
+  }
+  ay.partials = nullptr; ay.mode = 0;
+  {
+    dim3 grid(p->gy, p->batch * 3);
+    e = f32 ? eqk::launch_strided_f32(p->ny, false, ay, grid, s)
+            : eqk::launch_strided_f64(p->ny, false, ay, grid, s);
+    if (e != cudaSuccess) return fail_cuda(e, "y forward pass");
+  }
+  mark(3);
+  // pass 3: x forward + projector + x inverse
+  {
+    eqk::XArgs x{};
+    x.data = d_out; x.tw = p->tw[0];
+    x.xi_x = p->xi[0]; x.xi_y = p->xi[1]; x.xi_z = p->xi[2];
+    x.pairs = p->pairs; x.mean = p->mean; x.partials = p->partx;
+    x.field_stride = fstride; x.V = V;
+    x.nx = p->nx; x.ny = p->ny; x.nz = p->nz;
+    x.npairs = p->npairs;
+    const int tpc = p->nx / std::min(8, p->nx);
+    const int P = p->info_x.threads / (6 * tpc);
+    x.ngroups = (p->npairs + P - 1) / P;
+    x.nyq_zero = p->opts.nyq == EQ_NYQ_ZERO;
+    x.inv_v = 1.0 / double(V);
+    dim3 grid(p->gx, p->batch);
+    e = f32 ? eqk::launch_xproj_f32(p->nx, x, grid, s) : eqk::launch_xproj_f64(p->nx, x, grid, s);
+    if (e != cudaSuccess) return fail_cuda(e, "x projection pass");
+  }
+  mark(4);
+  // pass 4: y inverse
+  {
+    dim3 grid(p->gy, p->batch * 3);
+    e = f32 ? eqk::launch_strided_f32(p->ny, true, ay, grid, s)
+            : eqk::launch_strided_f64(p->ny, true, ay, grid, s);
+    if (e != cudaSuccess) return fail_cuda(e, "y inverse pass");
+  }
+  mark(5);
+  // pass 5: z inverse (+ residual L-inf against d_in)
+  const bool linf = p->opts.want_linf && d_in != d_out;
+  {
+    eqk::StridedArgs az = a;
+    az.in = d_out; az.out = d_out; az.ref = linf ? d_in : nullptr;
+    az.partials = p->partl; az.mode = 2;
+    dim3 grid(p->gl, p->batch * 3);
+    e = f32 ? eqk::launch_strided_f32(p->nz, true, az, grid, s)
+            : eqk::launch_strided_f64(p->nz, true, az, grid, s);
+    if (e != cudaSuccess) return fail_cuda(e, "z inverse pass");
+  }
+  mark(6);
+  k_finalize_norms<<<1, 128, 0, s>>>(p->partx, p->gx, linf ? p->partl : nullptr, p->gl, p->batch,
+                                     double(V), p->mean, p->instats, linf ? 0 : EQ_FLAG_NO_LINF,
+                                     p->norms);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "norm finalisation");
+  mark(7);
+  if ((e = cudaEventRecord(p->done, s)) != cudaSuccess) return fail_cuda(e, "event record");
+  p->have_result = true;
+  return EQ_OK;
+}
+
+void release(eq_plan* p) {
+  if (!p) return;
+  for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
+  if (p->done) cudaEventDestroy(p->done);
+  if (p->dmem) cudaFree(p->dmem);
+  if (p->stage) cudaFree(p->stage);
+  delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+void eq_plan_opts_default(eq_plan_opts* o) {
+  if (!o) return;
+  o->op = EQ_OP_DDO;
+  o->hx = o->hy = o->hz = 1.0;
+  o->nyq = EQ_NYQ_KEEP;
+  o->want_linf = 1;
+}
+
+const char* eq_last_error(void) { return g_last_error.c_str(); }
+
+eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
+                         const eq_plan_opts* opts, eq_plan** out) {
+  if (!out) return fail(EQ_ERR_INVALID, "eq_plan_create: out is NULL");
+  *out = nullptr;
+  if (dtype != EQ_F32 && dtype != EQ_F64) return fail(EQ_ERR_INVALID, "eq_plan_create: bad dtype");
+  if (batch < 1) return fail(EQ_ERR_INVALID, "eq_plan_create: batch must be >= 1");
+  for (int n : {nx, ny, nz})
+    if (!eqk::length_supported(n))
+      return fail(EQ_ERR_INVALID, "eq_plan_create: axis length " + std::to_string(n) +
+                                      " unsupported (powers of two 1..1024)");
+  eq_plan_opts o;
+  eq_plan_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.op != EQ_OP_DDO && o.op != EQ_OP_CDO) return fail(EQ_ERR_INVALID, "eq_plan_create: bad op");
+  if (o.nyq != EQ_NYQ_KEEP && o.nyq != EQ_NYQ_ZERO)
+    return fail(EQ_ERR_INVALID, "eq_plan_create: bad nyquist policy");
+  if (!(o.hx > 0.0) || !(o.hy > 0.0) || !(o.hz > 0.0) || !std::isfinite(o.hx) ||
+      !std::isfinite(o.hy) || !std::isfinite(o.hz))
+    return fail(EQ_ERR_INVALID, "eq_plan_create: spacing must be finite and > 0");
+
+  eq_plan* p = new (std::nothrow) eq_plan();
+  if (!p) return fail(EQ_ERR_OOM, "eq_plan_create: host allocation failed");
+  p->nx = nx; p->ny = ny; p->nz = nz; p->batch = batch; p->dtype = dtype; p->opts = o;
+  p->V = (long long)nx * ny * nz;
+  p->esize = dtype == EQ_F32 ? 4 : 8;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&p->device)) != cudaSuccess) { release(p); return fail_cuda(e, "cudaGetDevice"); }
+  if ((e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess) {
+    release(p);
+    return fail_cuda(e, "cudaDeviceGetAttribute");
+  }
+  if ((e = pass_info(dtype, nz, eqk::PASS_STRIDED_FWD, &p->info_z_f)) != cudaSuccess ||
+      (e = pass_info(dtype, ny, eqk::PASS_STRIDED_FWD, &p->info_y_f)) != cudaSuccess ||
+      (e = pass_info(dtype, nx, eqk::PASS_XPROJ, &p->info_x)) != cudaSuccess ||
+      (e = pass_info(dtype, ny, eqk::PASS_STRIDED_INV, &p->info_y_i)) != cudaSuccess ||
+      (e = pass_info(dtype, nz, eqk::PASS_STRIDED_INV, &p->info_z_i)) != cudaSuccess) {
+    release(p);
+    return fail_cuda(e, "kernel attributes");
+  }
+  // canonical row pairs of the x pass: rows (kz, ky) whose mirror (-kz, -ky) is not smaller
+  std::vector<int> pairs;
+  for (int kz = 0; kz < nz; ++kz) {
+    const int mz = kz == 0 ? 0 : nz - kz;
+    if (mz < kz) continue;
+    for (int ky = 0; ky < ny; ++ky) {
+      const int my = ky == 0 ? 0 : ny - ky;
+      if (mz == kz && my < ky) continue;
+      pairs.push_back(kz * ny + ky);
+    }
+  }
+  p->npairs = (int)pairs.size();
+  // grids: one resident wave, split over (field, component)
+  auto grid_for = [&](const eqk::PassInfo& inf, long long units, int split) {
+    long long g = (long long)p->sms * std::max(1, inf.blocks_per_sm);
+    g = (g + split - 1) / split;
+    g = std::max(1LL, std::min(g, units));
+    return (int)g;
+  };
+  {
+    const int Bz = p->info_z_f.threads / std::max(1, nz / std::min(8, nz));
+    const int By = p->info_y_f.threads / std::max(1, ny / std::min(8, ny));
+    const long long tz = ((long long)nx * ny + Bz - 1) / Bz;
+    const long long ty = ((long long)nx * nz + By - 1) / By;
+    const int tpc = nx / std::min(8, nx);
+    const int P = p->info_x.threads / (6 * tpc);
+    const long long gxn = (p->npairs + P - 1) / P;
+    p->g1 = grid_for(p->info_z_f, tz, batch * 3);
+    p->gy = grid_for(p->info_y_f, ty, batch * 3);
+    p->gx = grid_for(p->info_x, gxn, batch);
+    p->gl = grid_for(p->info_z_i, tz, batch * 3);
+  }
+  // tables
+  std::vector<unsigned char> tw[3], xi[3];
+  const int lens[3] = {nx, ny, nz};
+  const double hs[3] = {o.hx, o.hy, o.hz};
+  for (int a = 0; a < 3; ++a) {
+    if (dtype == EQ_F32) fill_tables<float>(lens[a], hs[a], o.op, tw[a], xi[a]);
+    else fill_tables<double>(lens[a], hs[a], o.op, tw[a], xi[a]);
+  }
+  size_t off = 0;
+  size_t o_tw[3], o_xi[3];
+  for (int a = 0; a < 3; ++a) { o_tw[a] = off; off = align_up(off + tw[a].size(), 256); }
+  for (int a = 0; a < 3; ++a) { o_xi[a] = off; off = align_up(off + xi[a].size(), 256); }
+  const size_t o_pairs = off; off = align_up(off + sizeof(int) * pairs.size(), 256);
+  const size_t o_p1 = off; off = align_up(off + sizeof(double) * batch * 3 * p->g1 * 4, 256);
+  const size_t o_px = off; off = align_up(off + sizeof(double) * batch * p->gx * 4, 256);
+  const size_t o_pl = off; off = align_up(off + sizeof(double) * batch * 3 * p->gl, 256);
+  const size_t o_mean = off; off = align_up(off + sizeof(double) * batch * 6, 256);
+  const size_t o_is = off; off = align_up(off + sizeof(double) * batch * 2, 256);
+  const size_t o_nr = off; off = align_up(off + sizeof(eq_norms_t) * batch, 256);
+  p->dbytes = off;
+  if ((e = cudaMalloc(&p->dmem, off)) != cudaSuccess) {
+    release(p);
+    cudaGetLastError();
+    return fail(EQ_ERR_OOM, std::string("eq_plan_create: cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  unsigned char* base = static_cast<unsigned char*>(p->dmem);
+  for (int a = 0; a < 3; ++a) {
+    p->tw[a] = base + o_tw[a];
+    p->xi[a] = base + o_xi[a];
+    if ((e = cudaMemcpy(p->tw[a], tw[a].data(), tw[a].size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(p->xi[a], xi[a].data(), xi[a].size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      release(p);
+      return fail_cuda(e, "table upload");
+    }
+  }
+  p->pairs = reinterpret_cast<int*>(base + o_pairs);
+  p->part1 = reinterpret_cast<double*>(base + o_p1);
+  p->partx = reinterpret_cast<double*>(base + o_px);
+  p->partl = reinterpret_cast<double*>(base + o_pl);
+  p->mean = reinterpret_cast<double*>(base + o_mean);
+  p->instats = reinterpret_cast<double*>(base + o_is);
+  p->norms = reinterpret_cast<eq_norms_t*>(base + o_nr);
+  if ((e = cudaMemcpy(p->pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    release(p);
+    return fail_cuda(e, "pair table upload");
+  }
+  if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess) {
+    release(p);
+    return fail_cuda(e, "cudaEventCreate");
+  }
+  *out = p;
+  return EQ_OK;
+}
+
+eq_status eq_project(eq_plan* p, const void* d_in, void* d_out, void* stream) {
+  if (!p || !d_in || !d_out) return fail(EQ_ERR_INVALID, "eq_project: NULL argument");
+  const size_t bytes = (size_t)p->batch * 6 * (size_t)p->V * p->esize;
+  const uintptr_t i0 = (uintptr_t)d_in, o0 = (uintptr_t)d_out;
+  if (i0 != o0 && i0 < o0 + bytes && o0 < i0 + bytes)
+    return fail(EQ_ERR_INVALID, "eq_project: d_in and d_out overlap without being equal");
+  if ((i0 % p->esize) || (o0 % p->esize))
+    return fail(EQ_ERR_INVALID, "eq_project: buffers not aligned to the element size");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device) return fail(EQ_ERR_INVALID, "eq_project: current device differs from the plan's");
+  return enqueue(p, d_in, d_out, static_cast<cudaStream_t>(stream));
+}
+
+eq_status eq_project_host(eq_plan* p, const void* h_in, void* h_out, void* stream) {
+  if (!p || !h_in || !h_out) return fail(EQ_ERR_INVALID, "eq_project_host: NULL argument");
+  const size_t bytes = (size_t)p->batch * 6 * (size_t)p->V * p->esize;
+  cudaError_t e;
+  if (!p->stage) {
+    if ((e = cudaMalloc(&p->stage, 2 * bytes)) != cudaSuccess) {
+      p->stage = nullptr;
+      cudaGetLastError();
+      return fail(EQ_ERR_OOM, std::string("eq_project_host: cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    p->stage_bytes = 2 * bytes;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* d_in = p->stage;
+  void* d_out = static_cast<unsigned char*>(p->stage) + bytes;
+  if ((e = cudaMemcpyAsync(d_in, h_in, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return fail_cuda(e, "eq_project_host: H2D");
+  eq_status st = enqueue(p, d_in, d_out, s);
+  if (st != EQ_OK) return st;
+  if ((e = cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return fail_cuda(e, "eq_project_host: D2H");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail_cuda(e, "eq_project_host: sync");
+  return EQ_OK;
+}
+
+eq_status eq_norms(eq_plan* p, eq_norms_t* host_out) {
+  if (!p || !host_out) return fail(EQ_ERR_INVALID, "eq_norms: NULL argument");
+  if (!p->have_result) return fail(EQ_ERR_INVALID, "eq_norms: no projection enqueued yet");
+  cudaError_t e;
+  if ((e = cudaEventSynchronize(p->done)) != cudaSuccess) return fail_cuda(e, "eq_norms: wait");
+  if ((e = cudaMemcpy(host_out, p->norms, sizeof(eq_norms_t) * p->batch, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return fail_cuda(e, "eq_norms: copy");
+  return EQ_OK;
+}
+
+eq_status eq_plan_set_timing(eq_plan* p, int max_calls) {
+  if (!p || max_calls < 0) return fail(EQ_ERR_INVALID, "eq_plan_set_timing: bad argument");
+  const size_t need = (size_t)max_calls * (EQ_NUM_PASSES + 1);
+  while (p->tev.size() < need) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return fail_cuda(err, "eq_plan_set_timing: cudaEventCreate");
+    p->tev.push_back(e);
+  }
+  p->tcap = max_calls;
+  p->tused = 0;
+  return EQ_OK;
+}
+
+eq_status eq_plan_pass_ms(eq_plan* p, double* ms_out, int* ncalls_out) {
+  if (!p || !ms_out) return fail(EQ_ERR_INVALID, "eq_plan_pass_ms: NULL argument");
+  for (int i = 0; i < EQ_NUM_PASSES; ++i) ms_out[i] = 0.0;
+  cudaError_t e;
+  if (p->tused > 0) {
+    cudaEvent_t last = p->tev[(size_t)(p->tused - 1) * (EQ_NUM_PASSES + 1) + EQ_NUM_PASSES];
+    if ((e = cudaEventSynchronize(last)) != cudaSuccess) return fail_cuda(e, "eq_plan_pass_ms: wait");
+  }
+  for (int c = 0; c < p->tused; ++c) {
+    cudaEvent_t* ev = &p->tev[(size_t)c * (EQ_NUM_PASSES + 1)];
+    for (int i = 0; i < EQ_NUM_PASSES; ++i) {
+      float ms = 0.f;
+      if ((e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1])) != cudaSuccess)
+        return fail_cuda(e, "eq_plan_pass_ms: elapsed");
+      ms_out[i] += ms;
+    }
+  }
+  if (ncalls_out) *ncalls_out = p->tused;
+  p->tused = 0;
+  return EQ_OK;
+}
+
+size_t eq_plan_workspace_bytes(const eq_plan* p) { return p ? p->dbytes + p->stage_bytes : 0; }
+
+void eq_plan_destroy(eq_plan* p) {
+  if (!p) return;
+  if (p->done) cudaEventSynchronize(p->done);
+  release(p);
+}
+
+}  // extern "C"

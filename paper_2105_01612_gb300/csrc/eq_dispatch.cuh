@@ -1,0 +1,68 @@
+// eq_dispatch.cuh - runtime length -> template instance dispatch, included once per dtype.
+#pragma once
+#include "eq_internal.h"
+
+namespace eqk {
+
+template <typename T, int N> struct Inst {
+  static cudaError_t info(PassKind kind, PassInfo* out) {
+    using C = Cfg<T, N>;
+    const void* fn;
+    if (kind == PASS_XPROJ) {
+      fn = reinterpret_cast<const void*>(&k_xproj<T, N>);
+      out->threads = C::X_THREADS;
+      out->smem = C::X_SMEM;
+    } else {
+      fn = kind == PASS_STRIDED_INV ? reinterpret_cast<const void*>(&k_strided<T, N, true>)
+                                    : reinterpret_cast<const void*>(&k_strided<T, N, false>);
+      out->threads = C::STRIDED_THREADS;
+      out->smem = C::STRIDED_SMEM;
+    }
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)out->smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out->blocks_per_sm, fn, out->threads,
+                                                         out->smem);
+  }
+  static cudaError_t strided(bool inv, const StridedArgs& a, dim3 grid, cudaStream_t s) {
+    using C = Cfg<T, N>;
+    if (inv) k_strided<T, N, true><<<grid, C::STRIDED_THREADS, C::STRIDED_SMEM, s>>>(a);
+    else k_strided<T, N, false><<<grid, C::STRIDED_THREADS, C::STRIDED_SMEM, s>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t xproj(const XArgs& a, dim3 grid, cudaStream_t s) {
+    using C = Cfg<T, N>;
+    k_xproj<T, N><<<grid, C::X_THREADS, C::X_SMEM, s>>>(a);
+    return cudaGetLastError();
+  }
+};
+
+#define EQ_FOR_LENGTHS(X) X(1) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
+
+template <typename T> cudaError_t info_t(int n, PassKind kind, PassInfo* out) {
+  switch (n) {
+#define EQ_CASE(N) case N: return Inst<T, N>::info(kind, out);
+    EQ_FOR_LENGTHS(EQ_CASE)
+#undef EQ_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T>
+cudaError_t strided_t(int n, bool inv, const StridedArgs& a, dim3 grid, cudaStream_t s) {
+  switch (n) {
+#define EQ_CASE(N) case N: return Inst<T, N>::strided(inv, a, grid, s);
+    EQ_FOR_LENGTHS(EQ_CASE)
+#undef EQ_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T> cudaError_t xproj_t(int n, const XArgs& a, dim3 grid, cudaStream_t s) {
+  switch (n) {
+#define EQ_CASE(N) case N: return Inst<T, N>::xproj(a, grid, s);
+    EQ_FOR_LENGTHS(EQ_CASE)
+#undef EQ_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace eqk

@@ -1,0 +1,12 @@
+// eq_f32.cu - FP32 instances of the pass kernels.
+#include "eq_dispatch.cuh"
+
+namespace eqk {
+cudaError_t pass_info_f32(int n, PassKind kind, PassInfo* out) { return info_t<float>(n, kind, out); }
+cudaError_t launch_strided_f32(int n, bool inv, const StridedArgs& a, dim3 grid, cudaStream_t s) {
+  return strided_t<float>(n, inv, a, grid, s);
+}
+cudaError_t launch_xproj_f32(int n, const XArgs& a, dim3 grid, cudaStream_t s) {
+  return xproj_t<float>(n, a, grid, s);
+}
+}  // namespace eqk

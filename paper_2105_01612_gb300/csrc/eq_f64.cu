@@ -1,0 +1,12 @@
+// eq_f64.cu - FP64 instances of the pass kernels.
+#include "eq_dispatch.cuh"
+
+namespace eqk {
+cudaError_t pass_info_f64(int n, PassKind kind, PassInfo* out) { return info_t<double>(n, kind, out); }
+cudaError_t launch_strided_f64(int n, bool inv, const StridedArgs& a, dim3 grid, cudaStream_t s) {
+  return strided_t<double>(n, inv, a, grid, s);
+}
+cudaError_t launch_xproj_f64(int n, const XArgs& a, dim3 grid, cudaStream_t s) {
+  return xproj_t<double>(n, a, grid, s);
+}
+}  // namespace eqk

@@ -1,0 +1,171 @@
+// eq_fft.cuh - register/shared-memory FFT core for power-of-two lengths (device code).
+//
+// One transform of length N is held by TPC = N / E threads, E complex elements each: thread t
+// holds element t + TPC * e in register slot e.  A Stockham autosort schedule runs log_R(N)
+// stages of radix R in {8, 4, 2}; in the stage with span Ns the butterfly j reads elements
+// j + r N/R (which are exactly register slots q + r E/R of thread t = j mod TPC), multiplies
+// leg r by W_{Ns R}^{r (j mod Ns)} and writes its outputs to (j / Ns) Ns R + (j mod Ns) + r Ns.
+// Between stages the outputs go through shared memory; after the last stage every output is
+// back in the register slot of its natural index, so the caller can store it directly.
+//
+// The forward transform is unnormalised with exp(-2 pi i m x / N); the inverse uses
+// exp(+2 pi i m x / N) without the 1/N factor (the projector applies 1/(nx ny nz) once).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace eqk {
+
+template <typename T> struct V2;
+template <> struct V2<float> { using t = float2; };
+template <> struct V2<double> { using t = double2; };
+
+template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, typename T2> __device__ __forceinline__ T2 mul_mi(T2 a) {
+  return INV ? T2{-a.y, a.x} : T2{a.y, -a.x};
+}
+
+template <bool INV, typename T2> __device__ __forceinline__ void dft2(T2* v) {
+  T2 a = v[0];
+  v[0] = cadd(a, v[1]);
+  v[1] = csub(a, v[1]);
+}
+
+// X_r = sum_m v_m W4^{r m}, W4 = exp(-+ 2 pi i / 4)
+template <bool INV, typename T2> __device__ __forceinline__ void dft4(T2* v) {
+  T2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+  T2 s13 = cadd(v[1], v[3]), d13 = mul_mi<INV>(csub(v[1], v[3]));
+  v[0] = cadd(s02, s13);
+  v[2] = csub(s02, s13);
+  v[1] = cadd(d02, d13);
+  v[3] = csub(d02, d13);
+}
+
+// radix 8 as two radix-4 transforms of the sums / twiddled differences of v_m and v_{m+4}
+template <bool INV, typename T2> __device__ __forceinline__ void dft8(T2* v) {
+  using T = decltype(v[0].x);
+  const T h = T(0.70710678118654752440);
+  T2 a[4], b[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    a[m] = cadd(v[m], v[m + 4]);
+    b[m] = csub(v[m], v[m + 4]);
+  }
+  // b_m *= W8^m
+  b[1] = INV ? T2{h * (b[1].x - b[1].y), h * (b[1].x + b[1].y)}
+             : T2{h * (b[1].x + b[1].y), h * (b[1].y - b[1].x)};
+  b[2] = mul_mi<INV>(b[2]);
+  b[3] = INV ? T2{-h * (b[3].x + b[3].y), h * (b[3].x - b[3].y)}
+             : T2{h * (b[3].y - b[3].x), -h * (b[3].x + b[3].y)};
+  dft4<INV>(a);
+  dft4<INV>(b);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    v[2 * q] = a[q];
+    v[2 * q + 1] = b[q];
+  }
+}
+
+template <int R, bool INV, typename T2> __device__ __forceinline__ void dftR(T2* v) {
+  if constexpr (R == 8) dft8<INV>(v);
+  else if constexpr (R == 4) dft4<INV>(v);
+  else if constexpr (R == 2) dft2<INV>(v);
+}
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+// radix of stage s for N = 2^L: 8 while three or more bits remain, then 4 or 2
+__host__ __device__ constexpr int stage_radix(int N, int s) {
+  int rem = ilog2(N);
+  for (int i = 0; i < s; ++i) rem -= (rem >= 3 ? 3 : rem);
+  return rem >= 3 ? 8 : (rem == 2 ? 4 : (rem == 1 ? 2 : 1));
+}
+__host__ __device__ constexpr int num_stages(int N) {
+  int rem = ilog2(N), s = 0;
+  while (rem > 0) { rem -= (rem >= 3 ? 3 : rem); ++s; }
+  return s;
+}
+__host__ __device__ constexpr int stage_span(int N, int s) {  // Ns before stage s
+  int ns = 1;
+  for (int i = 0; i < s; ++i) ns *= stage_radix(N, i);
+  return ns;
+}
+
+// One Stockham stage on the thread's registers; leaves outputs in the same slots.
+template <int N, int E, int S, bool INV, typename T2>
+__device__ __forceinline__ void fft_stage(T2 (&x)[E], int t, const T2* __restrict__ tw) {
+  constexpr int R = stage_radix(N, S);
+  constexpr int NS = stage_span(N, S);
+  constexpr int TPC = N / E;
+  constexpr int Q = E / R;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    T2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = x[q + r * Q];
+    if constexpr (NS > 1) {
+      const int k = (t + TPC * q) & (NS - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        T2 w = tw[(r * k) * (N / (NS * R))];
+        if (INV) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    dftR<R, INV>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[q + r * Q] = v[r];
+  }
+}
+
+// Output position of register slot (q, r) after stage S, for thread t.
+template <int N, int E, int S>
+__device__ __forceinline__ int stage_out_pos(int t, int q, int r) {
+  constexpr int R = stage_radix(N, S);
+  constexpr int NS = stage_span(N, S);
+  constexpr int TPC = N / E;
+  const int j = t + TPC * q;
+  return (j / NS) * NS * R + (j & (NS - 1)) + r * NS;
+}
+
+// Full transform of one column.  `idx(i)` maps element index i to the column's shared-memory
+// slot.  All threads of the block must call this together (it synchronises the block).  On
+// entry the caller guarantees the block is done reading `buf` from any earlier use.
+template <int N, int E, bool INV, int S = 0, typename T2, typename IDX>
+__device__ __forceinline__ void fft_column(T2 (&x)[E], int t, T2* buf, const IDX& idx,
+                                           const T2* __restrict__ tw) {
+  if constexpr (S < num_stages(N)) {
+    fft_stage<N, E, S, INV>(x, t, tw);
+    if constexpr (S + 1 < num_stages(N)) {
+      constexpr int R = stage_radix(N, S);
+      constexpr int Q = E / R;
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[idx(stage_out_pos<N, E, S>(t, q, r))] = x[q + r * Q];
+      __syncthreads();
+      constexpr int TPC = N / E;
+#pragma unroll
+      for (int e = 0; e < E; ++e) x[e] = buf[idx(t + TPC * e)];
+      __syncthreads();
+      fft_column<N, E, INV, S + 1>(x, t, buf, idx, tw);
+    }
+  }
+}
+
+// Kahan-compensated FP32/FP64 running sum (per-thread partial of a global FP64 reduction).
+template <typename T> struct Kahan {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T v) {
+    T y = v - c;
+    T tt = s + y;
+    c = (tt - s) - y;
+    s = tt;
+  }
+  __device__ __forceinline__ double value() const { return double(s) - double(c); }
+};
+
+}  // namespace eqk

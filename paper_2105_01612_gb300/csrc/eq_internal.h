@@ -1,0 +1,29 @@
+// eq_internal.h - host-side interface between the C ABI and the per-dtype kernel instances.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "eq_kernels.cuh"
+
+namespace eqk {
+
+struct PassInfo {
+  int threads = 0;
+  size_t smem = 0;
+  int blocks_per_sm = 0;
+};
+
+enum PassKind { PASS_STRIDED_FWD = 0, PASS_STRIDED_INV = 1, PASS_XPROJ = 2 };
+
+// Supported transform lengths of the compiled instances (powers of two 1..1024).
+bool length_supported(int n);
+
+// Launch shape of one pass for length n (sets the max dynamic shared memory attribute).
+cudaError_t pass_info_f32(int n, PassKind kind, PassInfo* out);
+cudaError_t pass_info_f64(int n, PassKind kind, PassInfo* out);
+
+cudaError_t launch_strided_f32(int n, bool inv, const StridedArgs& a, dim3 grid, cudaStream_t s);
+cudaError_t launch_strided_f64(int n, bool inv, const StridedArgs& a, dim3 grid, cudaStream_t s);
+cudaError_t launch_xproj_f32(int n, const XArgs& a, dim3 grid, cudaStream_t s);
+cudaError_t launch_xproj_f64(int n, const XArgs& a, dim3 grid, cudaStream_t s);
+
+}  // namespace eqk

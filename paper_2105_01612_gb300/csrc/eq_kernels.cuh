@@ -1,0 +1,404 @@
+// eq_kernels.cuh - the five HBM passes of the projection and their launch configuration.
+//
+// Data layout: the caller's output buffer holds the spectrum during the call.  The six real
+// Voigt planes of a field are read as three complex fields Z_c = S_{2c} + i S_{2c+1}
+// ((xx, yy), (zz, yz), (xz, xy)), stored split-complex (real part in plane 2c, imaginary part in
+// plane 2c+1).  Every pass reads a tile and writes the same positions, so the whole pipeline
+// runs in place in d_out and d_out may alias d_in.  Pass order:
+//   1. z forward  (reads d_in, writes d_out; FP64 mean / norm partials of the input)
+//   2. y forward
+//   3. x forward + per-mode projector + x inverse (row pairs k, -k together; norm partials)
+//   4. y inverse
+//   5. z inverse  (optional residual L-infinity against d_in)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "eq_fft.cuh"
+
+namespace eqk {
+
+template <typename T, int N> struct Cfg {
+  static constexpr int E = N >= 8 ? 8 : N;
+  static constexpr int TPC = N / E;
+  static constexpr int B0 = sizeof(T) == 4 ? 16 : 8;
+  static constexpr int BW = (256 / TPC > B0) ? 256 / TPC : B0;
+  static constexpr int B = (BW * TPC > 1024) ? 1024 / TPC : BW;          // strided columns
+  static constexpr int STRIDED_THREADS = B * TPC;
+  // x pass: P row pairs (6 P transforms) per block; 6 P TPC must be a multiple of 32
+  static constexpr int PM_ = TPC >= 16 ? 1 : 16 / TPC;
+  static constexpr int PW0 = (256 + 6 * TPC - 1) / (6 * TPC) > 2 ? (256 + 6 * TPC - 1) / (6 * TPC) : 2;
+  static constexpr int PW = (PW0 + PM_ - 1) / PM_ * PM_;
+  static constexpr int PM = 1024 / (6 * TPC) > 0 ? 1024 / (6 * TPC) : 1;
+  static constexpr int P = PW < PM ? PW : PM;                               // x-pass row pairs
+  static constexpr int XCOLS = 6 * P;
+  static constexpr int X_THREADS = XCOLS * TPC;
+  static constexpr int PITCH = N + (N >> 3);
+  using T2 = typename V2<T>::t;
+  static constexpr size_t STRIDED_SMEM = sizeof(T2) * (size_t(N) + size_t(N) * B);
+  static constexpr size_t X_SMEM = sizeof(T2) * (size_t(N) + size_t(XCOLS) * PITCH) + sizeof(T) * N;
+};
+
+struct StridedArgs {
+  const void* in;          // field 0, plane 0 of the source
+  void* out;               // field 0, plane 0 of the destination
+  const void* ref;         // last pass: original input for resid_linf (nullptr = skip)
+  const void* tw;          // N twiddles exp(-2 pi i m / N)
+  long long field_stride;  // elements between fields (6 V)
+  long long V;             // elements per plane
+  long long nstride;       // elements between consecutive points of one transform
+  long long inner;         // columns per outer slab (contiguous index range)
+  long long outer_stride;  // elements between outer slabs
+  long long ncols;         // outer * inner
+  long long ntiles;        // ceil(ncols / B)
+  double* partials;        // first: [batch][3][grid][4]; last: [batch][3][grid] (linf)
+  int mode;                // 0 = middle pass, 1 = first (reductions), 2 = last
+};
+
+struct XArgs {
+  void* data;              // field 0, plane 0 (spectrum, split complex)
+  const void* tw;          // nx twiddles
+  const void* xi_x;        // operator symbol per axis (nx, ny, nz entries)
+  const void* xi_y;
+  const void* xi_z;
+  const int* pairs;        // canonical rows kz * ny + ky whose mirror row is >= itself
+  const double* mean;      // [batch][6] FP64 mean (c0)
+  double* partials;        // [batch][grid][4]
+  long long field_stride;
+  long long V;
+  int nx, ny, nz;
+  int npairs;
+  int ngroups;
+  int nyq_zero;
+  double inv_v;            // 1 / (nx ny nz)
+};
+
+// deterministic block sum of K doubles per thread; result valid in thread 0
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* red /* >= 32*K */) {
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[warp * K + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red[w * K + k];
+      v[k] = s;
+    }
+  }
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) v = fmax(v, red[w]);
+  }
+  return v;
+}
+
+struct IdxStrided {
+  int b, B;
+  __device__ __forceinline__ int operator()(int i) const { return i * B + b; }
+};
+struct IdxRow {
+  int base;
+  __device__ __forceinline__ int operator()(int i) const { return base + i + (i >> 3); }
+};
+
+// Transform along a strided axis (z or y) of all three complex fields of every field.
+// grid = (G, batch * 3); block = Cfg::STRIDED_THREADS.
+template <typename T, int N, bool INV>
+__global__ void __launch_bounds__(Cfg<T, N>::STRIDED_THREADS)
+k_strided(const StridedArgs a) {
+  using C = Cfg<T, N>;
+  using T2 = typename C::T2;
+  constexpr int E = C::E, TPC = C::TPC, B = C::B;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* tw = reinterpret_cast<T2*>(smem_raw);
+  T2* buf = tw + N;
+  __shared__ double red[32 * 4];
+
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = reinterpret_cast<const T2*>(a.tw)[i];
+  __syncthreads();
+
+  const int b = threadIdx.x % B, t = threadIdx.x / B;
+  const int field = blockIdx.y / 3, comp = blockIdx.y % 3;
+  const long long fbase = field * a.field_stride + (2LL * comp) * a.V;
+  const T* in_re = reinterpret_cast<const T*>(a.in) + fbase;
+  const T* in_im = in_re + a.V;
+  T* out_re = reinterpret_cast<T*>(a.out) + fbase;
+  T* out_im = out_re + a.V;
+  const T* ref_re = a.ref ? reinterpret_cast<const T*>(a.ref) + fbase : nullptr;
+  const T* ref_im = ref_re ? ref_re + a.V : nullptr;
+  // Voigt weights of the two planes of complex field `comp`: (1,1), (1,2), (2,2)
+  const T wa = comp == 2 ? T(2) : T(1), wb = comp == 0 ? T(1) : T(2);
+
+  Kahan<T> sa, sb, sq;
+  T nonfinite = T(0);
+  T linf = T(0);
+  const IdxStrided idx{b, B};
+
+  for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const long long col = tile * B + b;
+    const bool valid = col < a.ncols;
+    const long long o = valid ? col / a.inner : 0, ii = valid ? col - o * a.inner : 0;
+    const long long base = o * a.outer_stride + ii;
+    T2 x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const long long off = base + (long long)(t + TPC * e) * a.nstride;
+      x[e] = valid ? T2{in_re[off], in_im[off]} : T2{T(0), T(0)};
+    }
+    if (a.mode == 1 && valid) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        if (!isfinite(x[e].x) || !isfinite(x[e].y)) nonfinite += T(1);
+        sa.add(x[e].x);
+        sb.add(x[e].y);
+        sq.add(wa * x[e].x * x[e].x + wb * x[e].y * x[e].y);
+      }
+    }
+    fft_column<N, E, INV>(x, t, buf, idx, tw);
+    if (valid) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const long long off = base + (long long)(t + TPC * e) * a.nstride;
+        out_re[off] = x[e].x;
+        out_im[off] = x[e].y;
+        if (a.mode == 2 && ref_re) {
+          linf = fmax(linf, fabs(ref_re[off] - x[e].x));
+          linf = fmax(linf, fabs(ref_im[off] - x[e].y));
+        }
+      }
+    }
+  }
+  if (a.mode == 1) {
+    double v[4] = {sa.value(), sb.value(), sq.value(), double(nonfinite)};
+    block_sum<4>(v, red);
+    if (threadIdx.x == 0) {
+      double* p = a.partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 4;
+      p[0] = v[0]; p[1] = v[1]; p[2] = v[2]; p[3] = v[3];
+    }
+  } else if (a.mode == 2 && ref_re) {
+    double m = block_max(double(linf), red);
+    if (threadIdx.x == 0) a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = m;
+  }
+}
+
+// rsqrt in the kernel's precision (library calls)
+__device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
+
+// The per-mode projector and its norm terms for one mode pair (k, -k).
+//   in:  a[c] = Z_c(k), bb[c] = Z_c(-k)  (c = 0..2)
+//   out: a[c] <- Zout_c(k) / V,  bb[c] <- Zout_c(-k) / V
+template <typename T, typename T2>
+__device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T xi1, T xi2,
+                                             bool zero_mode, const double* mean, double vol,
+                                             bool nyq_zero, T inv_v, T mult,
+                                             Kahan<T>& r2, Kahan<T>& di2, Kahan<T>& do2,
+                                             Kahan<T>& o2) {
+  // unpack the six Voigt components of S^(k): S_2c = (A + conj B) / 2, S_2c+1 = -i (A - conj B) / 2
+  T sr[6], si[6];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    sr[2 * c] = T(0.5) * (a[c].x + bb[c].x);
+    si[2 * c] = T(0.5) * (a[c].y - bb[c].y);
+    sr[2 * c + 1] = T(0.5) * (a[c].y + bb[c].y);
+    si[2 * c + 1] = T(0.5) * (bb[c].x - a[c].x);
+  }
+  if (zero_mode && mean) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      sr[j] = T(mean[j] * vol);
+      si[j] = T(0);
+    }
+  }
+  const T k2 = xi0 * xi0 + xi1 * xi1 + xi2 * xi2;
+  T orr[6], oi[6];
+  if (k2 > T(0)) {
+    const T rn = rsqrt_t(k2);
+    const T n0 = xi0 * rn, n1 = xi1 * rn, n2 = xi2 * rn;
+    // Voigt slots: 0 xx, 1 yy, 2 zz, 3 yz, 4 xz, 5 xy
+#define EQ_PROJ(S, O)                                                         \
+    {                                                                          \
+      const T v0 = S[0] * n0 + S[5] * n1 + S[4] * n2;                          \
+      const T v1 = S[5] * n0 + S[1] * n1 + S[3] * n2;                          \
+      const T v2 = S[4] * n0 + S[3] * n1 + S[2] * n2;                          \
+      const T s = n0 * v0 + n1 * v1 + n2 * v2;                                 \
+      O[0] = S[0] - T(2) * n0 * v0 + s * n0 * n0;                              \
+      O[1] = S[1] - T(2) * n1 * v1 + s * n1 * n1;                              \
+      O[2] = S[2] - T(2) * n2 * v2 + s * n2 * n2;                              \
+      O[3] = S[3] - n1 * v2 - v1 * n2 + s * n1 * n2;                           \
+      O[4] = S[4] - n0 * v2 - v0 * n2 + s * n0 * n2;                           \
+      O[5] = S[5] - n0 * v1 - v0 * n1 + s * n0 * n1;                           \
+    }
+    EQ_PROJ(sr, orr)
+    EQ_PROJ(si, oi)
+#undef EQ_PROJ
+  } else {
+    const bool drop = nyq_zero && !zero_mode;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      orr[j] = drop ? T(0) : sr[j];
+      oi[j] = drop ? T(0) : si[j];
+    }
+  }
+  // norm terms (sums of |.|^2 over modes; Parseval turns them into voxel means)
+  {
+    T rr = T(0), oo = T(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const T w = j < 3 ? T(1) : T(2);
+      const T dr = sr[j] - orr[j], dii = si[j] - oi[j];
+      rr += w * (dr * dr + dii * dii);
+      oo += w * (orr[j] * orr[j] + oi[j] * oi[j]);
+    }
+    T din = T(0), dout = T(0);
+#define EQ_DIV(S, ACC)                                                          \
+    {                                                                          \
+      const T d0 = xi0 * S[0] + xi1 * S[5] + xi2 * S[4];                       \
+      const T d1 = xi0 * S[5] + xi1 * S[1] + xi2 * S[3];                       \
+      const T d2 = xi0 * S[4] + xi1 * S[3] + xi2 * S[2];                       \
+      ACC += d0 * d0 + d1 * d1 + d2 * d2;                                      \
+    }
+    EQ_DIV(sr, din) EQ_DIV(si, din) EQ_DIV(orr, dout) EQ_DIV(oi, dout)
+#undef EQ_DIV
+    r2.add(mult * rr);
+    o2.add(mult * oo);
+    di2.add(mult * din);
+    do2.add(mult * dout);
+  }
+  // repack: Zout_c(k) = O_2c + i O_2c+1, Zout_c(-k) = conj(O_2c) + i conj(O_2c+1)
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T or_ = orr[2 * c], oi_ = oi[2 * c], pr = orr[2 * c + 1], pi_ = oi[2 * c + 1];
+    a[c] = T2{(or_ - pi_) * inv_v, (oi_ + pr) * inv_v};
+    bb[c] = T2{(or_ + pi_) * inv_v, (pr - oi_) * inv_v};
+  }
+}
+
+// Fused x pass: forward transform of row pairs (k_y, k_z) and (-k_y, -k_z), projector on every
+// mode pair (k, -k), inverse transform, store.  grid = (G, batch); block = Cfg::X_THREADS.
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<T, N>::X_THREADS)
+k_xproj(const XArgs a) {
+  using C = Cfg<T, N>;
+  using T2 = typename C::T2;
+  constexpr int E = C::E, TPC = C::TPC, P = C::P, PITCH = C::PITCH;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* tw = reinterpret_cast<T2*>(smem_raw);
+  T2* buf = tw + N;
+  T* xix = reinterpret_cast<T*>(buf + C::XCOLS * PITCH);
+  __shared__ double red[32 * 4];
+
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    tw[i] = reinterpret_cast<const T2*>(a.tw)[i];
+    xix[i] = reinterpret_cast<const T*>(a.xi_x)[i];
+  }
+  __syncthreads();
+  const T* xiy = reinterpret_cast<const T*>(a.xi_y);
+  const T* xiz = reinterpret_cast<const T*>(a.xi_z);
+
+  const int col = threadIdx.x / TPC, t = threadIdx.x % TPC;
+  const int slot = col / 6, side = (col % 6) / 3, comp = col % 3;
+  const int field = blockIdx.y;
+  T* fdata = reinterpret_cast<T*>(a.data) + field * a.field_stride;
+  T* pre = fdata + (2LL * comp) * a.V;
+  T* pim = pre + a.V;
+  const double* mean = a.mean ? a.mean + field * 6 : nullptr;
+  const IdxRow idx{col * PITCH};
+  const T inv_v = T(a.inv_v);
+  const double vol = 1.0 / a.inv_v;
+
+  Kahan<T> r2, di2, do2, o2;
+
+  for (int g = blockIdx.x; g < a.ngroups; g += gridDim.x) {
+    const int p = g * P + slot;
+    const bool valid = p < a.npairs;
+    int rowA = 0, rowB = 0;
+    if (valid) {
+      rowA = a.pairs[p];
+      const int kz = rowA / a.ny, ky = rowA - kz * a.ny;
+      const int mz = kz == 0 ? 0 : a.nz - kz, my = ky == 0 ? 0 : a.ny - ky;
+      rowB = mz * a.ny + my;
+    }
+    const bool selfrow = rowA == rowB;
+    const bool active = valid && !(side == 1 && selfrow);
+    const long long roff = (long long)(side == 0 ? rowA : rowB) * N;
+    T2 x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const long long off = roff + t + TPC * e;
+      x[e] = active ? T2{pre[off], pim[off]} : T2{T(0), T(0)};
+    }
+    fft_column<N, E, false>(x, t, buf, idx, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) buf[idx(t + TPC * e)] = x[e];
+    __syncthreads();
+
+    for (int item = threadIdx.x; item < P * N; item += blockDim.x) {
+      const int s2 = item / N, kx = item - s2 * N;
+      const int p2 = g * P + s2;
+      if (p2 >= a.npairs) continue;
+      const int rA = a.pairs[p2];
+      const int kz = rA / a.ny, ky = rA - kz * a.ny;
+      const int mz = kz == 0 ? 0 : a.nz - kz, my = ky == 0 ? 0 : a.ny - ky;
+      const bool self2 = (mz * a.ny + my) == rA;
+      const int kxm = kx == 0 ? 0 : N - kx;
+      if (self2 && kx > kxm) continue;
+      const int colA = s2 * 6, colB = self2 ? s2 * 6 : s2 * 6 + 3;
+      T2 av[3], bv[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        av[c] = buf[(colA + c) * PITCH + kx + (kx >> 3)];
+        bv[c] = buf[(colB + c) * PITCH + kxm + (kxm >> 3)];
+      }
+      const bool selfmode = self2 && kx == kxm;
+      const bool zero_mode = (rA == 0) && kx == 0;
+      project_pair<T>(av, bv, xix[kx], xiy[ky], xiz[kz], zero_mode, mean, vol, a.nyq_zero != 0,
+                      inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        buf[(colA + c) * PITCH + kx + (kx >> 3)] = av[c];
+        if (!selfmode) buf[(colB + c) * PITCH + kxm + (kxm >> 3)] = bv[c];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = buf[idx(t + TPC * e)];
+    __syncthreads();
+    fft_column<N, E, true>(x, t, buf, idx, tw);
+    if (active) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const long long off = roff + t + TPC * e;
+        pre[off] = x[e].x;
+        pim[off] = x[e].y;
+      }
+    }
+  }
+  double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
+  block_sum<4>(v, red);
+  if (threadIdx.x == 0) {
+    double* q = a.partials + ((long long)field * gridDim.x + blockIdx.x) * 4;
+    q[0] = v[0]; q[1] = v[1]; q[2] = v[2]; q[3] = v[3];
+  }
+}
+
+}  // namespace eqk

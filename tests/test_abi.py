@@ -1,0 +1,89 @@
+"""The C-ABI library builds, loads and exports every entry point declared in include/*.h; host
+logic that needs no GPU (argument validation, defaults, struct layout)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(INCLUDE):
+        if f.endswith(".h"):
+            src = open(os.path.join(INCLUDE, f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names.update(re.findall(r"\b(eq_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2105_01612_gb300 import _build, _lib
+    _build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported_and_bound(lib):
+    from paper_2105_01612_gb300 import _lib
+    declared = _declared_symbols()
+    assert "eq_project" in declared and "eq_plan_create" in declared
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.lib_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s+(eq_[a-z0-9_]+)$", out, flags=re.M))
+    assert declared <= exported, declared - exported
+    bound = {name for name, _, _ in _lib.SIGNATURES}
+    assert declared == bound, declared ^ bound
+    for name in declared:
+        getattr(lib, name)
+
+
+def test_struct_layout_matches_the_header(tmp_path):
+    from paper_2105_01612_gb300._lib import EqNorms, EqPlanOpts
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "eq.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(eq_plan_opts),"
+        " offsetof(eq_plan_opts, nyq), sizeof(eq_norms_t), offsetof(eq_norms_t, resid_linf),"
+        " offsetof(eq_norms_t, flags), offsetof(eq_norms_t, div_out_l2)); return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", INCLUDE, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = [ctypes.sizeof(EqPlanOpts), EqPlanOpts.nyq.offset, ctypes.sizeof(EqNorms),
+            EqNorms.resid_linf.offset, EqNorms.flags.offset, EqNorms.div_out_l2.offset]
+    assert got == want
+
+
+def test_defaults_and_argument_validation_without_a_gpu(lib):
+    from paper_2105_01612_gb300._lib import EqPlanOpts, EQ_ERR_INVALID, EQ_OP_DDO, EQ_NYQ_KEEP
+    o = EqPlanOpts()
+    lib.eq_plan_opts_default(ctypes.byref(o))
+    assert (o.op, o.hx, o.hy, o.hz, o.nyq, o.want_linf) == (EQ_OP_DDO, 1.0, 1.0, 1.0, EQ_NYQ_KEEP, 1)
+    h = ctypes.c_void_p()
+    # unsupported length, bad batch, bad spacing, NULL out: rejected before any CUDA call
+    assert lib.eq_plan_create(96, 64, 64, 0, 1, None, ctypes.byref(h)) == EQ_ERR_INVALID
+    assert b"unsupported" in lib.eq_last_error()
+    assert lib.eq_plan_create(64, 64, 64, 0, 0, None, ctypes.byref(h)) == EQ_ERR_INVALID
+    o.hx = -1.0
+    assert lib.eq_plan_create(64, 64, 64, 0, 1, ctypes.byref(o), ctypes.byref(h)) == EQ_ERR_INVALID
+    assert lib.eq_plan_create(64, 64, 64, 0, 1, None, None) == EQ_ERR_INVALID
+    assert lib.eq_plan_create(64, 64, 64, 7, 1, None, ctypes.byref(h)) == EQ_ERR_INVALID
+    assert lib.eq_project(None, None, None, None) == EQ_ERR_INVALID
+    assert lib.eq_norms(None, None) == EQ_ERR_INVALID
+    assert lib.eq_plan_workspace_bytes(None) == 0
+    lib.eq_plan_destroy(None)
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2105_01612_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, flags=re.M), f
+                assert "oracle/" not in txt, f
