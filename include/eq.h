@@ -80,11 +80,22 @@ typedef struct eq_server eq_server;
 /* Default options (DDO, unit spacing, KEEP, want_linf = 1). */
 void eq_plan_opts_default(eq_plan_opts* opts);
 
-/* Create a plan for `batch` fields of one grid size.  Sizes are 1..1024 per axis.  Allocates
+/* Create a plan for `batch` fields of one grid size.  Sizes are 1..1024 per axis (powers of two
+ * take compile-time-specialised kernels; other lengths the runtime-length path, see
+ * eq_plan_create_varlen for its limits).  Allocates
  * the plan's device tables and reduction buffers on the current device (no field-sized
  * workspace: the spectrum lives in the caller's output buffer).  opts == NULL: defaults. */
 eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
                          const eq_plan_opts* opts, eq_plan** out);
+
+/* Create a plan for `count` fields of different grid sizes (dims: nx, ny, nz per field, 3 *
+ * count ints), all projected by one launch per pass (a persistent grid over every field's
+ * tiles).  The fields are packed back to back in the buffers, field f starting at element
+ * 6 * sum_{g < f} nx_g ny_g nz_g.  Each axis length must be 1..1024 and, when it has a prime
+ * factor above 13, at most 512 (it then runs Bluestein's algorithm).  Norms come back in field
+ * order (eq_norms with `count` entries). */
+eq_status eq_plan_create_varlen(const int* dims, int count, eq_dtype dtype,
+                                const eq_plan_opts* opts, eq_plan** out);
 
 /* Project the plan's `batch` fields d_in -> d_out on `cuda_stream` (a cudaStream_t, NULL =
  * legacy default stream).  d_out may equal d_in (then resid_linf is not computed).  Both must

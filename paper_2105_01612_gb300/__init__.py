@@ -17,7 +17,7 @@ import torch
 from . import _lib
 from ._lib import EqError, EqNorms, EqPlanOpts
 
-__all__ = ["Plan", "project", "eq_plan_create", "eq_project", "eq_project_host", "eq_norms",
+__all__ = ["Plan", "VarlenPlan", "project", "eq_plan_create_varlen", "eq_plan_create", "eq_project", "eq_project_host", "eq_norms",
            "eq_plan_workspace_bytes", "eq_plan_destroy", "eq_last_error", "eq_plan_set_timing",
            "eq_plan_pass_ms", "EqError"]
 
@@ -46,6 +46,19 @@ def eq_plan_create(nx, ny, nz, dtype=torch.float32, batch=1, op="ddo", h=(1.0, 1
     st = _lib.load().eq_plan_create(int(nx), int(ny), int(nz), _DT[dtype], int(batch),
                                     ctypes.byref(opts), ctypes.byref(handle))
     _lib.check(st, "eq_plan_create")
+    return handle.value
+
+
+def eq_plan_create_varlen(dims, dtype=torch.float32, op="ddo", h=(1.0, 1.0, 1.0), nyq="keep",
+                          want_linf=True) -> int:
+    """dims: sequence of (nx, ny, nz) per field.  Returns an opaque plan handle."""
+    flat = [int(v) for d in dims for v in d]
+    arr = (ctypes.c_int * len(flat))(*flat)
+    handle = ctypes.c_void_p()
+    opts = _opts(op, h, nyq, want_linf)
+    st = _lib.load().eq_plan_create_varlen(arr, len(dims), _DT[dtype], ctypes.byref(opts),
+                                           ctypes.byref(handle))
+    _lib.check(st, "eq_plan_create_varlen")
     return handle.value
 
 
@@ -95,6 +108,7 @@ class Plan:
     def __init__(self, nx, ny, nz, dtype=torch.float32, batch=1, op="ddo", h=(1.0, 1.0, 1.0),
                  nyq="keep", want_linf=True, device=None):
         self.shape = (int(batch), 6, int(nz), int(ny), int(nx))
+        self.numel = _numel(self.shape)
         self.dtype = dtype
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
@@ -104,7 +118,7 @@ class Plan:
     def _check(self, t: torch.Tensor, name: str):
         if not t.is_cuda or t.device != self.device:
             raise ValueError(f"{name} must be on {self.device}")
-        if t.dtype != self.dtype or not t.is_contiguous() or t.numel() != _numel(self.shape):
+        if t.dtype != self.dtype or not t.is_contiguous() or t.numel() != self.numel:
             raise ValueError(f"{name} must be a contiguous {self.dtype} tensor of shape {self.shape}")
 
     def project(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -122,7 +136,7 @@ class Plan:
         """Host tensors in and out (pinned for full bandwidth); blocks until done."""
         for t, n in ((x, "x"), (out, "out")):
             if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() \
-                    or t.numel() != _numel(self.shape):
+                    or t.numel() != self.numel:
                 raise ValueError(f"{n} must be a contiguous host {self.dtype} tensor of shape {self.shape}")
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         with torch.cuda.device(self.device):
@@ -154,6 +168,38 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class VarlenPlan(Plan):
+    """Fields of different sizes packed back to back in one flat tensor (see pack/unpack)."""
+
+    def __init__(self, dims, dtype=torch.float32, op="ddo", h=(1.0, 1.0, 1.0), nyq="keep",
+                 want_linf=True, device=None):
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        self.dtype = dtype
+        self.numel = sum(6 * nx * ny * nz for nx, ny, nz in self.dims)
+        self.shape = (len(self.dims), self.numel)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        with torch.cuda.device(self.device):
+            self.handle = eq_plan_create_varlen(self.dims, dtype, op, h, nyq, want_linf)
+
+    def _check(self, t, name):
+        if not t.is_cuda or t.device != self.device or t.dtype != self.dtype \
+                or not t.is_contiguous() or t.numel() != self.numel:
+            raise ValueError(f"{name} must be a contiguous {self.dtype} CUDA tensor with "
+                             f"{self.numel} elements on {self.device}")
+
+    def pack(self, fields) -> torch.Tensor:
+        return torch.cat([f.reshape(-1) for f in fields]).to(self.device, self.dtype).contiguous()
+
+    def unpack(self, flat):
+        out, off = [], 0
+        for nx, ny, nz in self.dims:
+            n = 6 * nx * ny * nz
+            out.append(flat[off:off + n].view(6, nz, ny, nx))
+            off += n
+        return out
 
 
 def _numel(shape):

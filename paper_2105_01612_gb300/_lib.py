@@ -45,6 +45,8 @@ SIGNATURES = [
     ("eq_plan_opts_default", None, [ctypes.POINTER(EqPlanOpts)]),
     ("eq_plan_create", c_int, [c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(EqPlanOpts),
                                ctypes.POINTER(c_void_p)]),
+    ("eq_plan_create_varlen", c_int, [ctypes.POINTER(c_int), c_int, c_int,
+                                      ctypes.POINTER(EqPlanOpts), ctypes.POINTER(c_void_p)]),
     ("eq_project", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("eq_project_host", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("eq_norms", c_int, [c_void_p, ctypes.POINTER(EqNorms)]),

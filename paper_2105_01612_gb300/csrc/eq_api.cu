@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/eq.h"
+#include "eq_gen_host.h"
 #include "eq_internal.h"
 
 namespace {
@@ -122,6 +123,9 @@ struct eq_plan {
   // optional per-pass timing: one set of EQ_NUM_PASSES + 1 events per timed call
   std::vector<cudaEvent_t> tev;
   int tcap = 0, tused = 0;
+  // runtime-length path (sizes other than powers of two, uneven batches); null = fast path
+  eqg::GenPlan* gen = nullptr;
+  long long total_elems = 0;   // elements of one call's buffer (all fields, 6 planes)
 };
 
 namespace {
@@ -158,6 +162,15 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
   const bool f32 = p->dtype == EQ_F32;
   cudaEvent_t* ev = nullptr;
   if (p->tused < p->tcap) ev = &p->tev[(size_t)p->tused++ * (EQ_NUM_PASSES + 1)];
+  if (p->gen) {
+    std::string err;
+    eq_status st = eqg::gen_enqueue(p->gen, d_in, d_out, s, ev, &err);
+    if (st != EQ_OK) return fail(st, "eq_project: " + err);
+    cudaError_t e2 = cudaEventRecord(p->done, s);
+    if (e2 != cudaSuccess) return fail_cuda(e2, "event record");
+    p->have_result = true;
+    return EQ_OK;
+  }
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
   mark(0);
   const long long V = p->V;
@@ -256,6 +269,7 @@ void release(eq_plan* p) {
   if (p->done) cudaEventDestroy(p->done);
   if (p->dmem) cudaFree(p->dmem);
   if (p->stage) cudaFree(p->stage);
+  if (p->gen) eqg::gen_destroy(p->gen);
   delete p;
 }
 
@@ -273,30 +287,72 @@ void eq_plan_opts_default(eq_plan_opts* o) {
 
 const char* eq_last_error(void) { return g_last_error.c_str(); }
 
+static eq_status check_opts(const eq_plan_opts* opts, eq_plan_opts* o, const char* who) {
+  eq_plan_opts_default(o);
+  if (opts) *o = *opts;
+  if (o->op != EQ_OP_DDO && o->op != EQ_OP_CDO) return fail(EQ_ERR_INVALID, std::string(who) + ": bad op");
+  if (o->nyq != EQ_NYQ_KEEP && o->nyq != EQ_NYQ_ZERO)
+    return fail(EQ_ERR_INVALID, std::string(who) + ": bad nyquist policy");
+  if (!(o->hx > 0.0) || !(o->hy > 0.0) || !(o->hz > 0.0) || !std::isfinite(o->hx) ||
+      !std::isfinite(o->hy) || !std::isfinite(o->hz))
+    return fail(EQ_ERR_INVALID, std::string(who) + ": spacing must be finite and > 0");
+  return EQ_OK;
+}
+
+static eq_status create_generic(const int* dims, int count, eq_dtype dtype, const eq_plan_opts& o,
+                                eq_plan** out) {
+  eq_plan* p = new (std::nothrow) eq_plan();
+  if (!p) return fail(EQ_ERR_OOM, "eq_plan_create: host allocation failed");
+  p->dtype = dtype; p->opts = o; p->batch = count;
+  p->nx = dims[0]; p->ny = dims[1]; p->nz = dims[2];
+  p->esize = dtype == EQ_F32 ? 4 : 8;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&p->device)) != cudaSuccess) { release(p); return fail_cuda(e, "cudaGetDevice"); }
+  if ((e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess) {
+    release(p);
+    return fail_cuda(e, "cudaDeviceGetAttribute");
+  }
+  std::string err;
+  eq_status st = eqg::gen_plan_create(dims, count, dtype, o, p->sms, &p->gen, &err);
+  if (st != EQ_OK) { release(p); return fail(st, "eq_plan_create: " + err); }
+  p->total_elems = eqg::gen_total_elems(p->gen);
+  p->dbytes = eqg::gen_device_bytes(p->gen);
+  if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess) {
+    release(p);
+    return fail_cuda(e, "cudaEventCreate");
+  }
+  *out = p;
+  return EQ_OK;
+}
+
 eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
                          const eq_plan_opts* opts, eq_plan** out) {
   if (!out) return fail(EQ_ERR_INVALID, "eq_plan_create: out is NULL");
   *out = nullptr;
   if (dtype != EQ_F32 && dtype != EQ_F64) return fail(EQ_ERR_INVALID, "eq_plan_create: bad dtype");
   if (batch < 1) return fail(EQ_ERR_INVALID, "eq_plan_create: batch must be >= 1");
-  for (int n : {nx, ny, nz})
-    if (!eqk::length_supported(n))
+  bool fast = true;
+  for (int n : {nx, ny, nz}) {
+    if (!eqg::gen_length_supported(n))
       return fail(EQ_ERR_INVALID, "eq_plan_create: axis length " + std::to_string(n) +
-                                      " unsupported (powers of two 1..1024)");
+                                      " unsupported (1..1024; lengths with a prime factor above 13"
+                                      " need 2n-1 <= 1024)");
+    fast = fast && eqk::length_supported(n);
+  }
   eq_plan_opts o;
-  eq_plan_opts_default(&o);
-  if (opts) o = *opts;
-  if (o.op != EQ_OP_DDO && o.op != EQ_OP_CDO) return fail(EQ_ERR_INVALID, "eq_plan_create: bad op");
-  if (o.nyq != EQ_NYQ_KEEP && o.nyq != EQ_NYQ_ZERO)
-    return fail(EQ_ERR_INVALID, "eq_plan_create: bad nyquist policy");
-  if (!(o.hx > 0.0) || !(o.hy > 0.0) || !(o.hz > 0.0) || !std::isfinite(o.hx) ||
-      !std::isfinite(o.hy) || !std::isfinite(o.hz))
-    return fail(EQ_ERR_INVALID, "eq_plan_create: spacing must be finite and > 0");
+  eq_status st = check_opts(opts, &o, "eq_plan_create");
+  if (st != EQ_OK) return st;
+  if (!fast) {
+    std::vector<int> dims;
+    for (int b = 0; b < batch; ++b) { dims.push_back(nx); dims.push_back(ny); dims.push_back(nz); }
+    return create_generic(dims.data(), batch, dtype, o, out);
+  }
 
   eq_plan* p = new (std::nothrow) eq_plan();
   if (!p) return fail(EQ_ERR_OOM, "eq_plan_create: host allocation failed");
   p->nx = nx; p->ny = ny; p->nz = nz; p->batch = batch; p->dtype = dtype; p->opts = o;
   p->V = (long long)nx * ny * nz;
+  p->total_elems = (long long)batch * 6 * p->V;
   p->esize = dtype == EQ_F32 ? 4 : 8;
   cudaError_t e;
   if ((e = cudaGetDevice(&p->device)) != cudaSuccess) { release(p); return fail_cuda(e, "cudaGetDevice"); }
@@ -398,9 +454,25 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
   return EQ_OK;
 }
 
+eq_status eq_plan_create_varlen(const int* dims, int count, eq_dtype dtype,
+                                const eq_plan_opts* opts, eq_plan** out) {
+  if (!out) return fail(EQ_ERR_INVALID, "eq_plan_create_varlen: out is NULL");
+  *out = nullptr;
+  if (!dims || count < 1) return fail(EQ_ERR_INVALID, "eq_plan_create_varlen: need dims and count >= 1");
+  if (dtype != EQ_F32 && dtype != EQ_F64) return fail(EQ_ERR_INVALID, "eq_plan_create_varlen: bad dtype");
+  for (int i = 0; i < 3 * count; ++i)
+    if (!eqg::gen_length_supported(dims[i]))
+      return fail(EQ_ERR_INVALID, "eq_plan_create_varlen: axis length " + std::to_string(dims[i]) +
+                                      " unsupported");
+  eq_plan_opts o;
+  eq_status st = check_opts(opts, &o, "eq_plan_create_varlen");
+  if (st != EQ_OK) return st;
+  return create_generic(dims, count, dtype, o, out);
+}
+
 eq_status eq_project(eq_plan* p, const void* d_in, void* d_out, void* stream) {
   if (!p || !d_in || !d_out) return fail(EQ_ERR_INVALID, "eq_project: NULL argument");
-  const size_t bytes = (size_t)p->batch * 6 * (size_t)p->V * p->esize;
+  const size_t bytes = (size_t)p->total_elems * p->esize;
   const uintptr_t i0 = (uintptr_t)d_in, o0 = (uintptr_t)d_out;
   if (i0 != o0 && i0 < o0 + bytes && o0 < i0 + bytes)
     return fail(EQ_ERR_INVALID, "eq_project: d_in and d_out overlap without being equal");
@@ -414,7 +486,7 @@ eq_status eq_project(eq_plan* p, const void* d_in, void* d_out, void* stream) {
 
 eq_status eq_project_host(eq_plan* p, const void* h_in, void* h_out, void* stream) {
   if (!p || !h_in || !h_out) return fail(EQ_ERR_INVALID, "eq_project_host: NULL argument");
-  const size_t bytes = (size_t)p->batch * 6 * (size_t)p->V * p->esize;
+  const size_t bytes = (size_t)p->total_elems * p->esize;
   cudaError_t e;
   if (!p->stage) {
     if ((e = cudaMalloc(&p->stage, 2 * bytes)) != cudaSuccess) {
@@ -442,7 +514,8 @@ eq_status eq_norms(eq_plan* p, eq_norms_t* host_out) {
   if (!p->have_result) return fail(EQ_ERR_INVALID, "eq_norms: no projection enqueued yet");
   cudaError_t e;
   if ((e = cudaEventSynchronize(p->done)) != cudaSuccess) return fail_cuda(e, "eq_norms: wait");
-  if ((e = cudaMemcpy(host_out, p->norms, sizeof(eq_norms_t) * p->batch, cudaMemcpyDeviceToHost)) != cudaSuccess)
+  const eq_norms_t* src = p->gen ? eqg::gen_norms_device(p->gen) : p->norms;
+  if ((e = cudaMemcpy(host_out, src, sizeof(eq_norms_t) * p->batch, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return fail_cuda(e, "eq_norms: copy");
   return EQ_OK;
 }

@@ -1,0 +1,415 @@
+// eq_gen.cuh - runtime-length FFT passes for any grid size and for batches of uneven fields.
+//
+// Lengths whose prime factors are all in {2, 3, 5, 7, 11, 13} run a mixed-radix Stockham
+// schedule; any other length n runs Bluestein's chirp-z algorithm: with c_j = exp(-pi i j^2/n),
+// X_k = c_k sum_j (x_j c_j) conj(c_{k-j}), a circular convolution of length m >= 2n - 1 done with
+// two length-m transforms and the precomputed transform of the chirp.  Inverse transforms use
+// X = conj(DFT(conj(x))).  A block holds C transforms ("columns") in shared memory laid out
+// [element][column] with a padded pitch and ping-pongs between two buffers, one barrier per stage.
+//
+// Work items: a pass over a list of fields enumerates (field, component, chunk of column tiles)
+// or (field, chunk of x-row pairs); each item's warps write their own FP64 partial records, so
+// every reduction is a fixed-order sum (bitwise reproducible, independent of the other fields).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "../../include/eq.h"
+#include "eq_kernels.cuh"
+
+namespace eqg {
+
+using eqk::cadd;
+using eqk::cmul;
+using eqk::csub;
+using eqk::Kahan;
+
+constexpr int MAXST = 20;
+constexpr int WARPS_MAX = 32;
+
+struct AxisPlan {
+  int n;              // logical length
+  int m;              // transform length (n, or the Bluestein length)
+  int blue;           // 1 = Bluestein
+  int nst;            // number of stages of the length-m schedule
+  int radix[MAXST];
+  int tw;             // offset (complex entries) of exp(-2 pi i j / m), j < m, in the pool
+  int chirp;          // Bluestein: n entries c_j = exp(-pi i j^2 / n)
+  int bhat;           // Bluestein: m entries DFT_m(conj c, wrapped) / m
+};
+
+struct FieldDesc {
+  long long in_off;   // element offset of the field (plane 0) in the input buffer
+  long long out_off;  // element offset in the output buffer
+  long long V;        // nx ny nz
+  int nx, ny, nz;
+  int ax[3];          // axis plans of x, y, z
+  int xi[3];          // offsets of the operator symbol tables (real entries) in the xi pool
+  int pairs;          // offset of the canonical x-row pairs in the pair pool
+  int npairs;
+};
+
+struct GenArgs {
+  const void* in;          // input buffer base (first pass) / output base (others)
+  void* out;
+  const void* ref;         // last pass: input for L-inf (nullptr = skip)
+  const FieldDesc* fields;
+  const AxisPlan* axes;
+  const void* cpool;       // complex pool: twiddles, chirps, chirp transforms
+  const void* xipool;      // real pool: operator symbols
+  const int* pairpool;
+  const double* mean;      // [F][6]
+  const long long* item0;  // [F + 1] first work item of each field for this pass
+  double* partials;        // [items][WARPS][4]
+  int nfields;
+  long long nitems;
+  int axis;                // 1 = y, 2 = z for strided passes
+  int mode;                // 0 middle, 1 first, 2 last (strided)
+  int tiles_per_item;      // strided: column tiles of C columns per item; x: row-pair groups
+  int cols;                // C: columns per tile
+  int pitch;               // shared-memory pitch (>= C)
+  int mmax;                // largest transform length among the fields
+  int nyq_zero;
+};
+
+// ---- small DFTs -------------------------------------------------------------------------
+
+template <int R, bool INV, typename T2>
+__device__ __forceinline__ void dft_small(T2 (&v)[R], const T2 (&wr)[R]) {
+  if constexpr (R == 2) eqk::dft2<INV>(v);
+  else if constexpr (R == 4) eqk::dft4<INV>(v);
+  else if constexpr (R == 8) eqk::dft8<INV>(v);
+  else {
+    // direct R-point DFT with the R-th roots wr[q] = W_R^q (already conjugated for INV)
+    T2 o[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      T2 acc = v[0];
+#pragma unroll
+      for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], wr[(r * q) % R]));
+      o[q] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = o[q];
+  }
+}
+
+// one Stockham stage of radix R over C columns: src -> dst
+template <int R, bool INV, typename T2>
+__device__ __forceinline__ void gen_stage(const T2* __restrict__ src, T2* __restrict__ dst, int m,
+                                          int ns, int C, int pitch, const T2* __restrict__ tw) {
+  const int nb = m / R;
+  const int total = nb * C;
+  const int tstep = m / (ns * R);
+  T2 wr[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    T2 w = tw[q * nb];
+    if (INV) w.y = -w.y;
+    wr[q] = w;
+  }
+  for (int w = threadIdx.x; w < total; w += blockDim.x) {
+    const int col = w % C, j = w / C;
+    T2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * pitch + col];
+    const int k = j % ns;
+    if (ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        T2 t = tw[r * k * tstep];
+        if (INV) t.y = -t.y;
+        v[r] = cmul(v[r], t);
+      }
+    }
+    dft_small<R, INV>(v, wr);
+    const int base = (j / ns) * ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[(base + r * ns) * pitch + col] = v[r];
+  }
+}
+
+// Length-m transform of C columns; data starts in a, returns the buffer holding the result.
+template <bool INV, typename T2>
+__device__ T2* gen_fft(T2* a, T2* b, const AxisPlan& ap, int C, int pitch, const T2* tw) {
+  int ns = 1;
+  for (int s = 0; s < ap.nst; ++s) {
+    const int R = ap.radix[s];
+    switch (R) {
+      case 2: gen_stage<2, INV>(a, b, ap.m, ns, C, pitch, tw); break;
+      case 3: gen_stage<3, INV>(a, b, ap.m, ns, C, pitch, tw); break;
+      case 4: gen_stage<4, INV>(a, b, ap.m, ns, C, pitch, tw); break;
+      case 5: gen_stage<5, INV>(a, b, ap.m, ns, C, pitch, tw); break;
+      case 7: gen_stage<7, INV>(a, b, ap.m, ns, C, pitch, tw); break;
+      case 8: gen_stage<8, INV>(a, b, ap.m, ns, C, pitch, tw); break;
+      case 11: gen_stage<11, INV>(a, b, ap.m, ns, C, pitch, tw); break;
+      case 13: gen_stage<13, INV>(a, b, ap.m, ns, C, pitch, tw); break;
+      default: break;
+    }
+    __syncthreads();
+    ns *= R;
+    T2* t = a; a = b; b = t;
+  }
+  return a;
+}
+
+// Full axis transform of the C columns held in `a` (n valid elements each, element-major).
+// For Bluestein the caller has already multiplied by the chirp and zero-filled [n, m).
+// Returns the buffer with the n outputs (before the Bluestein post-chirp, see blue_post).
+template <typename T2>
+__device__ T2* axis_transform(T2* a, T2* b, const AxisPlan& ap, int C, int pitch,
+                              const T2* __restrict__ cpool, bool inv) {
+  const T2* tw = cpool + ap.tw;
+  if (!ap.blue) return inv ? gen_fft<true>(a, b, ap, C, pitch, tw) : gen_fft<false>(a, b, ap, C, pitch, tw);
+  T2* r = gen_fft<false>(a, b, ap, C, pitch, tw);
+  T2* o = (r == a) ? b : a;
+  const T2* bh = cpool + ap.bhat;
+  for (int w = threadIdx.x; w < ap.m * C; w += blockDim.x) {
+    const int col = w % C, k = w / C;
+    r[k * pitch + col] = cmul(r[k * pitch + col], bh[k]);
+  }
+  __syncthreads();
+  return gen_fft<true>(r, o, ap, C, pitch, tw);
+}
+
+// value to place in the work buffer for input element j of a transform (pre-chirp, conj trick)
+template <typename T2>
+__device__ __forceinline__ T2 pre(T2 x, int j, const AxisPlan& ap, const T2* cpool, bool inv) {
+  if (!ap.blue) return x;
+  if (inv) x.y = -x.y;
+  return cmul(x, cpool[ap.chirp + j]);
+}
+template <typename T2>
+__device__ __forceinline__ T2 post(T2 y, int k, const AxisPlan& ap, const T2* cpool, bool inv) {
+  if (!ap.blue) return y;
+  T2 r = cmul(y, cpool[ap.chirp + k]);
+  if (inv) r.y = -r.y;
+  return r;
+}
+
+__device__ __forceinline__ int find_field(const long long* item0, int nf, long long item) {
+  int lo = 0, hi = nf - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (item0[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int K>
+__device__ __forceinline__ void warp_partials(double (&v)[K], double* dst) {
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) dst[(threadIdx.x >> 5) * K + k] = v[k];
+}
+
+// Strided pass (axis y or z) over a list of fields, any lengths.
+// Item = (field, component, chunk of tiles_per_item tiles of C consecutive columns).
+template <typename T, bool INV>
+__global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
+  using T2 = typename eqk::V2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* bufA = reinterpret_cast<T2*>(smem_raw);
+  T2* bufB = bufA + (size_t)a.mmax * a.pitch;
+  const T2* cpool = reinterpret_cast<const T2*>(a.cpool);
+  const int C = a.cols, pitch = a.pitch;
+  const int nw = blockDim.x >> 5;
+
+  for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    const int f = find_field(a.item0, a.nfields, item);
+    const FieldDesc fd = a.fields[f];
+    const AxisPlan& ap = a.axes[fd.ax[a.axis]];
+    const int n = ap.n;
+    long long inner, nstride, outer_stride, ncols;
+    if (a.axis == 2) { inner = (long long)fd.nx * fd.ny; nstride = inner; outer_stride = 0; ncols = inner; }
+    else { inner = fd.nx; nstride = fd.nx; outer_stride = (long long)fd.nx * fd.ny; ncols = (long long)fd.nz * fd.nx; }
+    const long long ntiles = (ncols + C - 1) / C;
+    const long long chunks = (ntiles + a.tiles_per_item - 1) / a.tiles_per_item;
+    const long long local = item - a.item0[f];
+    const int comp = (int)(local / chunks);
+    const long long chunk = local - comp * chunks;
+    const T* in_re = reinterpret_cast<const T*>(a.in) + (a.mode == 1 ? fd.in_off : fd.out_off) + 2LL * comp * fd.V;
+    const T* in_im = in_re + fd.V;
+    T* out_re = reinterpret_cast<T*>(a.out) + fd.out_off + 2LL * comp * fd.V;
+    T* out_im = out_re + fd.V;
+    const T* ref_re = a.ref ? reinterpret_cast<const T*>(a.ref) + fd.in_off + 2LL * comp * fd.V : nullptr;
+    const T wa = comp == 2 ? T(2) : T(1), wb = comp == 0 ? T(1) : T(2);
+    Kahan<T> sa, sb, sq;
+    T nonfinite = T(0), linf = T(0);
+    const bool inv = INV;
+    for (long long tile = chunk * a.tiles_per_item;
+         tile < ntiles && tile < (chunk + 1) * a.tiles_per_item; ++tile) {
+      // load: element j of column col -> bufA[j][col]
+      for (int w = threadIdx.x; w < ap.m * C; w += blockDim.x) {
+        const int col = w % C, j = w / C;
+        const long long c = tile * C + col;
+        T2 x = {T(0), T(0)};
+        if (j < n && c < ncols) {
+          const long long o = c / inner, ii = c - o * inner;
+          const long long off = o * outer_stride + ii + (long long)j * nstride;
+          x = T2{in_re[off], in_im[off]};
+          if (a.mode == 1) {
+            if (!isfinite(x.x) || !isfinite(x.y)) nonfinite += T(1);
+            sa.add(x.x);
+            sb.add(x.y);
+            sq.add(wa * x.x * x.x + wb * x.y * x.y);
+          }
+          x = pre(x, j, ap, cpool, inv);
+        }
+        bufA[j * pitch + col] = x;
+      }
+      __syncthreads();
+      T2* r = axis_transform(bufA, bufB, ap, C, pitch, cpool, inv);
+      for (int w = threadIdx.x; w < n * C; w += blockDim.x) {
+        const int col = w % C, k = w / C;
+        const long long c = tile * C + col;
+        if (c < ncols) {
+          const long long o = c / inner, ii = c - o * inner;
+          const long long off = o * outer_stride + ii + (long long)k * nstride;
+          const T2 y = post(r[k * pitch + col], k, ap, cpool, inv);
+          out_re[off] = y.x;
+          out_im[off] = y.y;
+          if (ref_re) {
+            linf = fmax(linf, fabs(ref_re[off] - y.x));
+            linf = fmax(linf, fabs(ref_re[off + fd.V] - y.y));
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (a.mode == 1) {
+      double v[4] = {sa.value(), sb.value(), sq.value(), double(nonfinite)};
+      warp_partials<4>(v, a.partials + item * WARPS_MAX * 4);
+      for (int k = nw * 4 + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
+        a.partials[item * WARPS_MAX * 4 + k] = 0.0;
+    } else if (a.mode == 2) {
+      double v[1] = {double(linf)};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[0] = fmax(v[0], __shfl_down_sync(0xffffffffu, v[0], o));
+      if ((threadIdx.x & 31) == 0) a.partials[item * WARPS_MAX * 4 + (threadIdx.x >> 5)] = v[0];
+      for (int k = nw + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
+        a.partials[item * WARPS_MAX * 4 + k] = 0.0;
+    }
+  }
+}
+
+// Fused x pass over a list of fields, any lengths.  Item = (field, tiles_per_item groups of P
+// row pairs); C = 6 P columns.
+template <typename T>
+__global__ void __launch_bounds__(512) k_gen_xproj(const GenArgs a) {
+  using T2 = typename eqk::V2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* bufA = reinterpret_cast<T2*>(smem_raw);
+  T2* bufB = bufA + (size_t)a.mmax * a.pitch;
+  const T2* cpool = reinterpret_cast<const T2*>(a.cpool);
+  const T* xipool = reinterpret_cast<const T*>(a.xipool);
+  const int C = a.cols, pitch = a.pitch, P = C / 6;
+  const int nw = blockDim.x >> 5;
+
+  for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    const int f = find_field(a.item0, a.nfields, item);
+    const FieldDesc fd = a.fields[f];
+    const AxisPlan& ap = a.axes[fd.ax[0]];
+    const int nx = fd.nx, ny = fd.ny, nz = fd.nz;
+    const long long local = item - a.item0[f];
+    const int* pairs = a.pairpool + fd.pairs;
+    T* base = reinterpret_cast<T*>(a.out) + fd.out_off;
+    const T* xix = xipool + fd.xi[0];
+    const T* xiy = xipool + fd.xi[1];
+    const T* xiz = xipool + fd.xi[2];
+    const double* mean = a.mean + f * 6;
+    const T inv_v = T(1.0 / double(fd.V));
+    const double vol = double(fd.V);
+    Kahan<T> r2, di2, do2, o2;
+    const int ngroups = (fd.npairs + P - 1) / P;
+    for (int g = (int)(local * a.tiles_per_item);
+         g < ngroups && g < (local + 1) * a.tiles_per_item; ++g) {
+      // load the 6 P rows: column col = slot * 6 + side * 3 + comp
+      for (int w = threadIdx.x; w < ap.m * C; w += blockDim.x) {
+        const int col = w / ap.m, j = w - col * ap.m;      // consecutive threads along a row
+        const int slot = col / 6, side = (col % 6) / 3, comp = col % 3;
+        const int p = g * P + slot;
+        T2 x = {T(0), T(0)};
+        if (j < nx && p < fd.npairs) {
+          const int rA = pairs[p];
+          const int kz = rA / ny, ky = rA - kz * ny;
+          const int rB = (kz == 0 ? 0 : nz - kz) * ny + (ky == 0 ? 0 : ny - ky);
+          if (!(side == 1 && rA == rB)) {
+            const long long off = (long long)(side == 0 ? rA : rB) * nx + j + 2LL * comp * fd.V;
+            x = pre(T2{base[off], base[off + fd.V]}, j, ap, cpool, false);
+          }
+        }
+        bufA[j * pitch + col] = x;
+      }
+      __syncthreads();
+      T2* r = axis_transform(bufA, bufB, ap, C, pitch, cpool, false);
+      if (ap.blue) {
+        for (int w = threadIdx.x; w < nx * C; w += blockDim.x) {
+          const int col = w % C, k = w / C;
+          r[k * pitch + col] = post(r[k * pitch + col], k, ap, cpool, false);
+        }
+        __syncthreads();
+      }
+      for (int it = threadIdx.x; it < P * nx; it += blockDim.x) {
+        const int s2 = it / nx, kx = it - s2 * nx;
+        const int p2 = g * P + s2;
+        if (p2 >= fd.npairs) continue;
+        const int rA = pairs[p2];
+        const int kz = rA / ny, ky = rA - kz * ny;
+        const bool self2 = ((kz == 0 ? 0 : nz - kz) * ny + (ky == 0 ? 0 : ny - ky)) == rA;
+        const int kxm = kx == 0 ? 0 : nx - kx;
+        if (self2 && kx > kxm) continue;
+        const int colA = s2 * 6, colB = self2 ? s2 * 6 : s2 * 6 + 3;
+        T2 av[3], bv[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          av[c] = r[kx * pitch + colA + c];
+          bv[c] = r[kxm * pitch + colB + c];
+        }
+        const bool selfmode = self2 && kx == kxm;
+        eqk::project_pair<T>(av, bv, xix[kx], xiy[ky], xiz[kz], rA == 0 && kx == 0, mean, vol,
+                             a.nyq_zero != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          r[kx * pitch + colA + c] = av[c];
+          if (!selfmode) r[kxm * pitch + colB + c] = bv[c];
+        }
+      }
+      __syncthreads();
+      // inverse: move to bufA (pre-chirp for Bluestein), transform, store
+      T2* other = (r == bufA) ? bufB : bufA;
+      for (int w = threadIdx.x; w < ap.m * C; w += blockDim.x) {
+        const int j = w / C, col = w % C;
+        T2 x = {T(0), T(0)};
+        if (j < nx) x = pre(r[j * pitch + col], j, ap, cpool, true);
+        other[j * pitch + col] = x;
+      }
+      __syncthreads();
+      T2* q = axis_transform(other, r, ap, C, pitch, cpool, true);
+      for (int w = threadIdx.x; w < nx * C; w += blockDim.x) {
+        const int col = w / nx, j = w - col * nx;
+        const int slot = col / 6, side = (col % 6) / 3, comp = col % 3;
+        const int p = g * P + slot;
+        if (p >= fd.npairs) continue;
+        const int rA = pairs[p];
+        const int kz = rA / ny, ky = rA - kz * ny;
+        const int rB = (kz == 0 ? 0 : nz - kz) * ny + (ky == 0 ? 0 : ny - ky);
+        if (side == 1 && rA == rB) continue;
+        const long long off = (long long)(side == 0 ? rA : rB) * nx + j + 2LL * comp * fd.V;
+        const T2 y = post(q[j * pitch + col], j, ap, cpool, true);
+        base[off] = y.x;
+        base[off + fd.V] = y.y;
+      }
+      __syncthreads();
+    }
+    double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
+    warp_partials<4>(v, a.partials + item * WARPS_MAX * 4);
+    for (int k = nw * 4 + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
+      a.partials[item * WARPS_MAX * 4 + k] = 0.0;
+  }
+}
+
+}  // namespace eqg

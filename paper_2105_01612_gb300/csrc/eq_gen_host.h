@@ -1,0 +1,34 @@
+// eq_gen_host.h - host plan of the runtime-length path (any sizes, uneven batches).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/eq.h"
+#include "eq_gen.cuh"
+
+namespace eqg {
+
+cudaError_t gen_occupancy_f32(int kind, int threads, size_t smem, int* blocks);
+cudaError_t gen_occupancy_f64(int kind, int threads, size_t smem, int* blocks);
+cudaError_t gen_launch_f32(int kind, const GenArgs& a, int grid, int threads, size_t smem, cudaStream_t s);
+cudaError_t gen_launch_f64(int kind, const GenArgs& a, int grid, int threads, size_t smem, cudaStream_t s);
+
+struct GenPlan;
+
+// Largest supported axis length and the rule for it (for error messages).
+bool gen_length_supported(int n);
+
+// dims: 3 * count ints (nx, ny, nz per field); fields are packed in order in the buffers.
+eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_plan_opts& o,
+                          int sms, GenPlan** out, std::string* err);
+// Enqueue the passes; ev (nullable) receives EQ_NUM_PASSES + 1 event records.
+eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s, cudaEvent_t* ev,
+                      std::string* err);
+const eq_norms_t* gen_norms_device(const GenPlan* g);
+size_t gen_device_bytes(const GenPlan* g);
+long long gen_total_elems(const GenPlan* g);   // 6 * sum of voxels
+int gen_count(const GenPlan* g);
+void gen_destroy(GenPlan* g);
+
+}  // namespace eqg

@@ -1,0 +1,27 @@
+// eq_gen_inst.cuh - launch wrappers of the runtime-length passes, included once per dtype.
+#pragma once
+#include "eq_gen.cuh"
+
+namespace eqg {
+
+template <typename T> struct GenInst {
+  static const void* fn(int kind) {
+    if (kind == 0) return reinterpret_cast<const void*>(&k_gen_strided<T, false>);
+    if (kind == 1) return reinterpret_cast<const void*>(&k_gen_strided<T, true>);
+    return reinterpret_cast<const void*>(&k_gen_xproj<T>);
+  }
+  static cudaError_t occupancy(int kind, int threads, size_t smem, int* blocks) {
+    cudaError_t e = cudaFuncSetAttribute(fn(kind), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn(kind), threads, smem);
+  }
+  static cudaError_t launch(int kind, const GenArgs& a, int grid, int threads, size_t smem,
+                            cudaStream_t s) {
+    if (kind == 0) k_gen_strided<T, false><<<grid, threads, smem, s>>>(a);
+    else if (kind == 1) k_gen_strided<T, true><<<grid, threads, smem, s>>>(a);
+    else k_gen_xproj<T><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace eqg

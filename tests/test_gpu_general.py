@@ -1,0 +1,103 @@
+"""Parity of the runtime-length path (mixed radix 2..13 and Bluestein) and of uneven batches
+(one launch per pass over all fields) with the FP64 CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from fieldgen import voronoi_stress_field
+import paper_2105_01612_gb300 as eq
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-12, torch.float32: 2e-6}
+W = np.array([1.0, 1, 1, 2, 2, 2])
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2105_01612_gb300 import _build
+    _build.build()
+
+
+def rel(a, b):
+    w = W.reshape((6,) + (1,) * (np.ndim(a) - 1))
+    return math.sqrt(float((w * (a - b) ** 2).sum() / max((w * b ** 2).sum(), 1e-300)))
+
+
+def as_dtype(s, dtype):
+    return s.astype(np.float32).astype(np.float64) if dtype == torch.float32 else s
+
+
+@pytest.mark.parametrize("shape", [(3, 5, 7), (6, 10, 9), (26, 13, 11), (23, 19, 17), (4, 34, 67),
+                                   (2, 3, 97), (5, 2, 250), (37, 31, 33), (1, 1, 7), (7, 1, 1)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_any_size_matches_oracle(shape, dtype):
+    s = as_dtype(voronoi_stress_field(shape, 5, 100.0, 10.0, sum(shape)).numpy(), dtype)
+    for op, nyq, h in (("ddo", "keep", (1.0, 1.0, 1.0)), ("cdo", "zero", (0.7, 1.1, 1.3))):
+        ref = oracle.project(s, op, h, nyq)
+        x = torch.as_tensor(s).to(dtype).cuda().unsqueeze(0)
+        plan = eq.Plan(shape[2], shape[1], shape[0], dtype, 1, op, h, nyq)
+        out = plan.project(x)
+        nrm = plan.norms()[0]
+        plan.close()
+        got = out[0].double().cpu().numpy()
+        assert rel(got, ref) <= TOL[dtype], (op, nyq)
+        want = oracle.norms(s, ref, op, h)
+        for k in ("norm_in", "norm_out", "resid_l2", "div_in_l2"):
+            assert nrm[k] == pytest.approx(want[k], rel=10 * TOL[dtype] + 1e-12, abs=1e-9), k
+
+
+def _varlen_run(dims, dtype, seed0, op="ddo"):
+    fields = [voronoi_stress_field((nz, ny, nx), 7, 150.0, 5.0, seed0 + i, dtype=dtype).numpy()
+              for i, (nx, ny, nz) in enumerate(dims)]
+    plan = eq.VarlenPlan(dims, dtype, op)
+    flat = plan.pack([torch.as_tensor(f) for f in fields])
+    out = torch.empty_like(flat)
+    plan.project(flat, out)
+    nrm = plan.norms()
+    outs = [o.double().cpu().numpy() for o in plan.unpack(out)]
+    plan.close()
+    return fields, outs, nrm
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_uneven_batch_matches_oracle_and_single_runs(dtype):
+    dims = [(16, 16, 16), (12, 20, 9), (33, 7, 14), (64, 8, 8), (5, 97, 3), (30, 30, 30)]
+    fields, outs, nrm = _varlen_run(dims, dtype, 4000)
+    for i, (f, o) in enumerate(zip(fields, outs)):
+        f64 = f.astype(np.float64)
+        ref = oracle.project(f64, "ddo")
+        assert rel(o, ref) <= TOL[dtype], dims[i]
+        want = oracle.norms(f64, ref, "ddo")
+        assert nrm[i]["resid_rel"] == pytest.approx(want["resid_rel"], rel=1e-5)
+        # the field alone gives the same output bits as inside the batch
+        _, alone, _ = _varlen_run([dims[i]], dtype, 4000 + i)
+        assert np.array_equal(alone[0], o), dims[i]
+
+
+def test_batch_of_64_uneven_fields_config_sizes_sampled():
+    """Uneven batch at the sizes of the 64-field workload (each axis uniform in 64..256, FP32):
+    every field's norms are consistent and two sampled fields match the oracle."""
+    rng = np.random.Generator(np.random.PCG64(210501612 + 3))
+    dims = [tuple(int(v) for v in rng.integers(64, 257, size=3)) for _ in range(64)]
+    grains = [int(g) for g in rng.integers(50, 2001, size=64)]
+    plan = eq.VarlenPlan(dims, torch.float32, "ddo")
+    fields = [voronoi_stress_field((nz, ny, nx), grains[i], 150.0, 0.0, 5000 + i,
+                                   dtype=torch.float32, device="cuda")
+              for i, (nx, ny, nz) in enumerate(dims)]
+    flat = plan.pack(fields)
+    out = torch.empty_like(flat)
+    plan.project(flat, out)
+    nrm = plan.norms()
+    outs = plan.unpack(out)
+    for i in (0, 37):
+        f = fields[i].double().cpu().numpy()
+        ref = oracle.project(f, "ddo")
+        assert rel(outs[i].double().cpu().numpy(), ref) <= 2e-6, dims[i]
+    for n in nrm:
+        assert abs(n["norm_in"] ** 2 - n["norm_out"] ** 2 - n["resid_l2"] ** 2) <= 1e-5 * n["norm_in"] ** 2
+        assert n["div_out_l2"] <= 1e-5 * n["div_in_l2"]
+    plan.close()
