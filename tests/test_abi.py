@@ -66,8 +66,12 @@ def test_defaults_and_argument_validation_without_a_gpu(lib):
     assert (o.op, o.hx, o.hy, o.hz, o.nyq, o.want_linf) == (EQ_OP_DDO, 1.0, 1.0, 1.0, EQ_NYQ_KEEP, 1)
     h = ctypes.c_void_p()
     # unsupported length, bad batch, bad spacing, NULL out: rejected before any CUDA call
-    assert lib.eq_plan_create(96, 64, 64, 0, 1, None, ctypes.byref(h)) == EQ_ERR_INVALID
+    assert lib.eq_plan_create(2048, 64, 64, 0, 1, None, ctypes.byref(h)) == EQ_ERR_INVALID
     assert b"unsupported" in lib.eq_last_error()
+    assert lib.eq_plan_create(64, 64, 601, 0, 1, None, ctypes.byref(h)) == EQ_ERR_INVALID
+    dims = (ctypes.c_int * 6)(16, 16, 16, 8, 0, 8)
+    assert lib.eq_plan_create_varlen(dims, 2, 0, None, ctypes.byref(h)) == EQ_ERR_INVALID
+    assert lib.eq_plan_create_varlen(None, 2, 0, None, ctypes.byref(h)) == EQ_ERR_INVALID
     assert lib.eq_plan_create(64, 64, 64, 0, 0, None, ctypes.byref(h)) == EQ_ERR_INVALID
     o.hx = -1.0
     assert lib.eq_plan_create(64, 64, 64, 0, 1, ctypes.byref(o), ctypes.byref(h)) == EQ_ERR_INVALID

@@ -180,7 +180,7 @@ def test_deterministic_and_nonfinite_flag():
 
 def test_errors_surface_as_status():
     with pytest.raises(eq.EqError):
-        eq.Plan(96, 64, 64)
+        eq.Plan(2048, 64, 64)
     plan = eq.Plan(16, 16, 16, torch.float32)
     x = torch.zeros(1, 6, 16, 16, 16, device="cuda")
     with pytest.raises(eq.EqError):
