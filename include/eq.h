@@ -58,6 +58,8 @@ typedef struct {
   double hx, hy, hz;     /* voxel spacing, default 1 (all > 0) */
   eq_nyquist nyq;        /* default EQ_NYQ_KEEP */
   int want_linf;         /* 1: also compute resid_linf (needs d_in != d_out); default 1 */
+  int graph;             /* 1: capture the passes in a CUDA graph on first use of a (d_in, d_out)
+                            pair and replay it while the pair is unchanged; default 1 */
 } eq_plan_opts;
 
 /* Per-field diagnostics, FP64.  ||A|| = sqrt(mean over voxels of A:A) with A:B = sum_ij A_ij B_ij
@@ -77,7 +79,7 @@ typedef struct {
 typedef struct eq_plan eq_plan;
 typedef struct eq_server eq_server;
 
-/* Default options (DDO, unit spacing, KEEP, want_linf = 1). */
+/* Default options (DDO, unit spacing, KEEP, want_linf = 1, graph = 1). */
 void eq_plan_opts_default(eq_plan_opts* opts);
 
 /* Create a plan for `batch` fields of one grid size.  Sizes are 1..1024 per axis (powers of two
@@ -100,7 +102,8 @@ eq_status eq_plan_create_varlen(const int* dims, int count, eq_dtype dtype,
 /* Project the plan's `batch` fields d_in -> d_out on `cuda_stream` (a cudaStream_t, NULL =
  * legacy default stream).  d_out may equal d_in (then resid_linf is not computed).  Both must
  * hold batch * 6 * nx * ny * nz elements of the plan's dtype and be 16-byte aligned.  The call
- * only enqueues work; it returns before the result is ready.  Steps (Sec. 3.3): forward 3-D
+ * only enqueues work; it returns before the result is ready.  Calls on one plan share its
+ * reduction buffers, so they must be ordered (one stream, or synchronised between streams).  Steps (Sec. 3.3): forward 3-D
  * DFT, per-mode projector, inverse DFT, norms; the mean is taken in FP64. */
 eq_status eq_project(eq_plan* plan, const void* d_in, void* d_out, void* cuda_stream);
 
@@ -128,6 +131,35 @@ eq_status eq_plan_set_timing(eq_plan* plan, int max_calls);
 /* Wait for the timed calls and return, per pass, the summed device time in milliseconds over
  * them (ms_out: EQ_NUM_PASSES entries) and their number; then reset the counters. */
 eq_status eq_plan_pass_ms(eq_plan* plan, double* ms_out, int* ncalls_out);
+
+/* ---- serving ------------------------------------------------------------------------
+ * A request loop for single fields arriving over time.  A scheduler thread admits queued
+ * requests in arrival order as soon as one of `max_inflight` slots (CUDA streams) is free and the
+ * request's device footprint (input + output field, 2 x 6 nx ny nz x element size) fits in
+ * `hbm_budget_bytes` next to the requests in flight; each admitted request runs H2D copy,
+ * projection and D2H copy on its slot's stream, so work of different requests overlaps on the
+ * device.  Plans are created per grid size on first use and kept for reuse.  Results of a field
+ * do not depend on what else is in flight (same kernels, fixed-order reductions).
+ * Server calls are thread-safe; the server uses the device current at creation. */
+eq_status eq_server_create(size_t hbm_budget_bytes, int max_inflight, eq_server** out);
+
+/* Queue one field (host buffers, caller-owned, kept alive until eq_serve_poll returns EQ_OK or
+ * the server is destroyed; pinned memory gives full copy bandwidth).  opts == NULL: defaults.
+ * EQ_ERR_OOM if the request alone cannot fit the budget, EQ_ERR_BUSY if the queue is full. */
+eq_status eq_serve_submit(eq_server* server, int nx, int ny, int nz, eq_dtype dtype,
+                          const eq_plan_opts* opts, const void* host_in, void* host_out,
+                          unsigned long long* ticket);
+
+/* Wait up to timeout_us (0 = do not wait) for a request.  EQ_PENDING: not finished yet (the ticket
+ * stays valid).  Otherwise the ticket is consumed: EQ_OK with its norms (nullable) and latency
+ * from submit to completion in seconds (nullable), or the request's error status.
+ * EQ_ERR_NOT_FOUND: unknown or already consumed ticket. */
+eq_status eq_serve_poll(eq_server* server, unsigned long long ticket, int timeout_us,
+                        eq_norms_t* out, double* latency_s);
+
+/* Stop the server: queued requests are cancelled, requests already on the device complete, then
+ * every resource is released.  The server and its tickets are invalid afterwards. */
+void eq_server_destroy(eq_server* server);
 
 /* Message of the calling thread's last failed call ("" if none). */
 const char* eq_last_error(void);

@@ -17,7 +17,7 @@ import torch
 from . import _lib
 from ._lib import EqError, EqNorms, EqPlanOpts
 
-__all__ = ["Plan", "VarlenPlan", "project", "eq_plan_create_varlen", "eq_plan_create", "eq_project", "eq_project_host", "eq_norms",
+__all__ = ["Plan", "VarlenPlan", "Server", "project", "eq_plan_create_varlen", "eq_plan_create", "eq_project", "eq_project_host", "eq_norms",
            "eq_plan_workspace_bytes", "eq_plan_destroy", "eq_last_error", "eq_plan_set_timing",
            "eq_plan_pass_ms", "EqError"]
 
@@ -26,13 +26,14 @@ _NYQ = {"keep": _lib.EQ_NYQ_KEEP, "zero": _lib.EQ_NYQ_ZERO}
 _DT = {torch.float32: _lib.EQ_F32, torch.float64: _lib.EQ_F64}
 
 
-def _opts(op="ddo", h=(1.0, 1.0, 1.0), nyq="keep", want_linf=True) -> EqPlanOpts:
+def _opts(op="ddo", h=(1.0, 1.0, 1.0), nyq="keep", want_linf=True, graph=True) -> EqPlanOpts:
     o = EqPlanOpts()
     _lib.load().eq_plan_opts_default(ctypes.byref(o))
     o.op = _OPS[op]
     o.hx, o.hy, o.hz = (float(v) for v in h)
     o.nyq = _NYQ[nyq]
     o.want_linf = 1 if want_linf else 0
+    o.graph = 1 if graph else 0
     return o
 
 
@@ -200,6 +201,69 @@ class VarlenPlan(Plan):
             out.append(flat[off:off + n].view(6, nz, ny, nx))
             off += n
         return out
+
+
+class Server:
+    """Request loop (eq_server_*): single fields from host memory, admitted by HBM footprint."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 8, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.load().eq_server_create(int(hbm_budget_bytes), int(max_inflight),
+                                                    ctypes.byref(h)), "eq_server_create")
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, x: torch.Tensor, out: torch.Tensor, op="ddo", h=(1.0, 1.0, 1.0),
+               nyq="keep", want_linf=True) -> int:
+        """x, out: host tensors (6, nz, ny, nx), float32/float64, contiguous (pinned is best)."""
+        if x.is_cuda or out.is_cuda or x.shape != out.shape or x.dim() != 4 or x.shape[0] != 6 \
+                or x.dtype != out.dtype or not (x.is_contiguous() and out.is_contiguous()):
+            raise ValueError("x and out must be contiguous host tensors of shape (6, nz, ny, nx)")
+        _, nz, ny, nx = x.shape
+        opts = _opts(op, h, nyq, want_linf)
+        t = ctypes.c_ulonglong()
+        st = _lib.load().eq_serve_submit(self.handle, nx, ny, nz, _DT[x.dtype], ctypes.byref(opts),
+                                         x.data_ptr(), out.data_ptr(), ctypes.byref(t))
+        _lib.check(st, "eq_serve_submit")
+        self._keep[t.value] = (x, out)
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """None while pending; else (norms dict, latency seconds).  Raises on a failed request."""
+        n = EqNorms()
+        lat = ctypes.c_double()
+        st = _lib.load().eq_serve_poll(self.handle, int(ticket), int(timeout_us), ctypes.byref(n),
+                                       ctypes.byref(lat))
+        if st == _lib.EQ_PENDING:
+            return None
+        self._keep.pop(ticket, None)
+        _lib.check(st, "eq_serve_poll")
+        return n.to_dict(), lat.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        import time
+        t0 = time.monotonic()
+        while True:
+            r = self.poll(ticket, 10000)
+            if r is not None:
+                return r
+            if time.monotonic() - t0 > timeout_s:
+                raise TimeoutError(f"request {ticket} not done after {timeout_s} s")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.load().eq_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _numel(shape):

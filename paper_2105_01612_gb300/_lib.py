@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "EQ_OK", 1: "EQ_ERR_INVALID", 2: "EQ_ERR_OOM", 3: "EQ_ERR_CUD
 
 class EqPlanOpts(ctypes.Structure):
     _fields_ = [("op", c_int), ("hx", c_double), ("hy", c_double), ("hz", c_double),
-                ("nyq", c_int), ("want_linf", c_int)]
+                ("nyq", c_int), ("want_linf", c_int), ("graph", c_int)]
 
 
 class EqNorms(ctypes.Structure):
@@ -54,6 +54,12 @@ SIGNATURES = [
     ("eq_plan_set_timing", c_int, [c_void_p, c_int]),
     ("eq_plan_pass_ms", c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
     ("eq_plan_destroy", None, [c_void_p]),
+    ("eq_server_create", c_int, [c_size_t, c_int, ctypes.POINTER(c_void_p)]),
+    ("eq_serve_submit", c_int, [c_void_p, c_int, c_int, c_int, c_int, ctypes.POINTER(EqPlanOpts),
+                                c_void_p, c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]),
+    ("eq_serve_poll", c_int, [c_void_p, ctypes.c_ulonglong, c_int, ctypes.POINTER(EqNorms),
+                              ctypes.POINTER(c_double)]),
+    ("eq_server_destroy", None, [c_void_p]),
     ("eq_last_error", ctypes.c_char_p, []),
 ]
 

@@ -29,6 +29,7 @@ bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 namespace eqk {
 bool length_supported(int n) { return is_pow2(n) && n <= 1024; }
+void set_last_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace eqk
 
 // ---------------------------------------------------------------- finalisation kernels
@@ -126,6 +127,11 @@ struct eq_plan {
   // runtime-length path (sizes other than powers of two, uneven batches); null = fast path
   eqg::GenPlan* gen = nullptr;
   long long total_elems = 0;   // elements of one call's buffer (all fields, 6 planes)
+  // captured CUDA graph of the passes for one (d_in, d_out) pair
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_in = nullptr;
+  void* g_out = nullptr;
 };
 
 namespace {
@@ -166,9 +172,6 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     std::string err;
     eq_status st = eqg::gen_enqueue(p->gen, d_in, d_out, s, ev, &err);
     if (st != EQ_OK) return fail(st, "eq_project: " + err);
-    cudaError_t e2 = cudaEventRecord(p->done, s);
-    if (e2 != cudaSuccess) return fail_cuda(e2, "event record");
-    p->have_result = true;
     return EQ_OK;
   }
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
@@ -258,6 +261,37 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
                                      p->norms);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "norm finalisation");
   mark(7);
+  return EQ_OK;
+}
+
+// Enqueue one projection: replay the plan's captured CUDA graph when the buffers are the ones it
+// was captured with (capturing it first if not), or launch the passes directly when timing.
+eq_status run(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
+  cudaError_t e;
+  const bool timed = p->tused < p->tcap;
+  if (p->opts.graph && !timed) {
+    if (!p->gexec || p->g_in != d_in || p->g_out != d_out) {
+      if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+      if (!p->cap && (e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return fail_cuda(e, "capture stream");
+      if ((e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return fail_cuda(e, "begin capture");
+      eq_status st = enqueue(p, d_in, d_out, p->cap);
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(p->cap, &graph);
+      if (st != EQ_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+      if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return fail_cuda(e, "end capture"); }
+      e = cudaGraphInstantiate(&p->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) { p->gexec = nullptr; return fail_cuda(e, "graph instantiate"); }
+      p->g_in = d_in;
+      p->g_out = d_out;
+    }
+    if ((e = cudaGraphLaunch(p->gexec, s)) != cudaSuccess) return fail_cuda(e, "graph launch");
+  } else {
+    eq_status st = enqueue(p, d_in, d_out, s);
+    if (st != EQ_OK) return st;
+  }
   if ((e = cudaEventRecord(p->done, s)) != cudaSuccess) return fail_cuda(e, "event record");
   p->have_result = true;
   return EQ_OK;
@@ -266,6 +300,8 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
 void release(eq_plan* p) {
   if (!p) return;
   for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->cap) cudaStreamDestroy(p->cap);
   if (p->done) cudaEventDestroy(p->done);
   if (p->dmem) cudaFree(p->dmem);
   if (p->stage) cudaFree(p->stage);
@@ -283,6 +319,7 @@ void eq_plan_opts_default(eq_plan_opts* o) {
   o->hx = o->hy = o->hz = 1.0;
   o->nyq = EQ_NYQ_KEEP;
   o->want_linf = 1;
+  o->graph = 1;
 }
 
 const char* eq_last_error(void) { return g_last_error.c_str(); }
@@ -481,7 +518,7 @@ eq_status eq_project(eq_plan* p, const void* d_in, void* d_out, void* stream) {
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != p->device) return fail(EQ_ERR_INVALID, "eq_project: current device differs from the plan's");
-  return enqueue(p, d_in, d_out, static_cast<cudaStream_t>(stream));
+  return run(p, d_in, d_out, static_cast<cudaStream_t>(stream));
 }
 
 eq_status eq_project_host(eq_plan* p, const void* h_in, void* h_out, void* stream) {
@@ -501,7 +538,7 @@ eq_status eq_project_host(eq_plan* p, const void* h_in, void* h_out, void* strea
   void* d_out = static_cast<unsigned char*>(p->stage) + bytes;
   if ((e = cudaMemcpyAsync(d_in, h_in, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return fail_cuda(e, "eq_project_host: H2D");
-  eq_status st = enqueue(p, d_in, d_out, s);
+  eq_status st = run(p, d_in, d_out, s);
   if (st != EQ_OK) return st;
   if ((e = cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return fail_cuda(e, "eq_project_host: D2H");

@@ -63,7 +63,8 @@ def test_defaults_and_argument_validation_without_a_gpu(lib):
     from paper_2105_01612_gb300._lib import EqPlanOpts, EQ_ERR_INVALID, EQ_OP_DDO, EQ_NYQ_KEEP
     o = EqPlanOpts()
     lib.eq_plan_opts_default(ctypes.byref(o))
-    assert (o.op, o.hx, o.hy, o.hz, o.nyq, o.want_linf) == (EQ_OP_DDO, 1.0, 1.0, 1.0, EQ_NYQ_KEEP, 1)
+    assert (o.op, o.hx, o.hy, o.hz, o.nyq, o.want_linf, o.graph) == \
+        (EQ_OP_DDO, 1.0, 1.0, 1.0, EQ_NYQ_KEEP, 1, 1)
     h = ctypes.c_void_p()
     # unsupported length, bad batch, bad spacing, NULL out: rejected before any CUDA call
     assert lib.eq_plan_create(2048, 64, 64, 0, 1, None, ctypes.byref(h)) == EQ_ERR_INVALID
@@ -81,6 +82,12 @@ def test_defaults_and_argument_validation_without_a_gpu(lib):
     assert lib.eq_norms(None, None) == EQ_ERR_INVALID
     assert lib.eq_plan_workspace_bytes(None) == 0
     lib.eq_plan_destroy(None)
+    # serving: argument checks that precede any CUDA call
+    assert lib.eq_server_create(0, 4, ctypes.byref(h)) == EQ_ERR_INVALID
+    assert lib.eq_server_create(1 << 30, 0, ctypes.byref(h)) == EQ_ERR_INVALID
+    assert lib.eq_serve_submit(None, 8, 8, 8, 0, None, None, None, None) == EQ_ERR_INVALID
+    assert lib.eq_serve_poll(None, 1, 0, None, None) == EQ_ERR_INVALID
+    lib.eq_server_destroy(None)
 
 
 def test_product_path_does_not_import_the_oracle():
