@@ -1,6 +1,7 @@
 // eq_api.cu - plans and the C ABI entry points of include/eq.h (host runtime).
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -116,6 +117,11 @@ struct eq_plan {
   eq_norms_t* norms = nullptr; // [batch]
   int g1 = 1, gy = 1, gx = 1, gl = 1;
   eqk::PassInfo info_z_f, info_y_f, info_x, info_y_i, info_z_i;
+  // TMA-fed strided passes (used when an instance exists and the x extent tiles evenly)
+  eqk::TmaInfo tz, ty;
+  bool tma_z = false, tma_y = false;
+  int gtz = 1, gty = 1;
+  int* err = nullptr;          // raised by a kernel whose bounded wait ran out
   cudaEvent_t done = nullptr;
   bool have_result = false;
   // staging for eq_project_host
@@ -164,6 +170,64 @@ template <typename T> void fill_tables(int n, double h, eq_op op, std::vector<un
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiled>(f);
+  }();
+  return fn;
+}
+
+// 4-D view (x, y, z, plane) of a buffer of `planes` planes; box of `cols` x values and `box`
+// points along the transformed axis (2 = z, 1 = y).
+bool make_map(CUtensorMap* m, const void* base, const eq_plan* p, int axis, int cols, int box) {
+  EncodeTiled enc = encode_fn();
+  if (!enc || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  const cuuint64_t es = p->esize;
+  const cuuint64_t dims[4] = {(cuuint64_t)p->nx, (cuuint64_t)p->ny, (cuuint64_t)p->nz,
+                              (cuuint64_t)(6 * p->batch)};
+  const cuuint64_t strides[3] = {p->nx * es, (cuuint64_t)p->nx * p->ny * es, (cuuint64_t)p->V * es};
+  const cuuint32_t boxd[4] = {(cuuint32_t)cols, axis == 1 ? (cuuint32_t)box : 1u,
+                              axis == 2 ? (cuuint32_t)box : 1u, 1u};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, p->esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+             const_cast<void*>(base), dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Strided pass along `axis` through the TMA kernel; false if not applicable for these buffers.
+bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src, void* dst,
+             const void* ref, double* partials, cudaStream_t s, cudaError_t* e) {
+  if (!on) return false;
+  const eqk::TmaInfo& ti = axis == 2 ? p->tz : p->ty;
+  CUtensorMap map;
+  if (!make_map(&map, src, p, axis, ti.cols, ti.box)) {
+    *e = cudaErrorInvalidValue;
+    return true;
+  }
+  eqk::TmaArgs t{};
+  t.ref = ref; t.out = dst; t.tw = p->tw[axis]; t.partials = partials; t.err = p->err;
+  t.field_stride = 6 * p->V; t.V = p->V;
+  t.nx = p->nx; t.ny = p->ny; t.nz = p->nz;
+  t.axis = axis; t.mode = mode;
+  t.ntiles = (axis == 2 ? (long long)p->ny : (long long)p->nz) * (p->nx / ti.cols);
+  dim3 grid(axis == 2 ? p->gtz : p->gty, p->batch * 3);
+  const int n = axis == 2 ? p->nz : p->ny;
+  *e = p->dtype == EQ_F32 ? eqk::launch_tma_f32(n, inv, map, t, grid, s)
+                          : eqk::launch_tma_f64(n, inv, map, t, grid, s);
+  return true;
+}
+
 eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
   const bool f32 = p->dtype == EQ_F32;
   cudaEvent_t* ev = nullptr;
@@ -176,6 +240,11 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
   }
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
   mark(0);
+  // the TMA passes need 16-byte aligned buffers; decide once per call so the reductions and
+  // their finalisation agree on the grid
+  const bool aligned = !(reinterpret_cast<uintptr_t>(d_in) & 15) && !(reinterpret_cast<uintptr_t>(d_out) & 15);
+  const bool on_z = p->tma_z && aligned, on_y = p->tma_y && aligned;
+  const int gz_used = on_z ? p->gtz : p->g1, gl_used = on_z ? p->gtz : p->gl;
   const long long V = p->V;
   const long long fstride = 6 * V;
   cudaError_t e;
@@ -191,12 +260,14 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     a.ntiles = (a.ncols + B - 1) / B;
     a.partials = p->part1; a.mode = 1;
     dim3 grid(p->g1, p->batch * 3);
-    e = f32 ? eqk::launch_strided_f32(p->nz, false, a, grid, s)
-            : eqk::launch_strided_f64(p->nz, false, a, grid, s);
+    if (!try_tma(p, on_z, 2, false, 1, d_in, d_out, nullptr, p->part1, s, &e))
+      e = f32 ? eqk::launch_strided_f32(p->nz, false, a, grid, s)
+              : eqk::launch_strided_f64(p->nz, false, a, grid, s);
     if (e != cudaSuccess) return fail_cuda(e, "z forward pass");
   }
   mark(1);
-  k_finalize_mean<<<1, 128, 0, s>>>(p->part1, p->g1, p->batch, double(V), p->mean, p->instats);
+  k_finalize_mean<<<1, 128, 0, s>>>(p->part1, gz_used, p->batch, double(V),
+                                    p->mean, p->instats);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "mean finalisation");
   mark(2);
   // pass 2: y forward
@@ -212,8 +283,9 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
   ay.partials = nullptr; ay.mode = 0;
   {
     dim3 grid(p->gy, p->batch * 3);
-    e = f32 ? eqk::launch_strided_f32(p->ny, false, ay, grid, s)
-            : eqk::launch_strided_f64(p->ny, false, ay, grid, s);
+    if (!try_tma(p, on_y, 1, false, 0, d_out, d_out, nullptr, nullptr, s, &e))
+      e = f32 ? eqk::launch_strided_f32(p->ny, false, ay, grid, s)
+              : eqk::launch_strided_f64(p->ny, false, ay, grid, s);
     if (e != cudaSuccess) return fail_cuda(e, "y forward pass");
   }
   mark(3);
@@ -239,8 +311,9 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
   // pass 4: y inverse
   {
     dim3 grid(p->gy, p->batch * 3);
-    e = f32 ? eqk::launch_strided_f32(p->ny, true, ay, grid, s)
-            : eqk::launch_strided_f64(p->ny, true, ay, grid, s);
+    if (!try_tma(p, on_y, 1, true, 0, d_out, d_out, nullptr, nullptr, s, &e))
+      e = f32 ? eqk::launch_strided_f32(p->ny, true, ay, grid, s)
+              : eqk::launch_strided_f64(p->ny, true, ay, grid, s);
     if (e != cudaSuccess) return fail_cuda(e, "y inverse pass");
   }
   mark(5);
@@ -251,12 +324,13 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     az.in = d_out; az.out = d_out; az.ref = linf ? d_in : nullptr;
     az.partials = p->partl; az.mode = 2;
     dim3 grid(p->gl, p->batch * 3);
-    e = f32 ? eqk::launch_strided_f32(p->nz, true, az, grid, s)
-            : eqk::launch_strided_f64(p->nz, true, az, grid, s);
+    if (!try_tma(p, on_z, 2, true, 2, d_out, d_out, linf ? d_in : nullptr, p->partl, s, &e))
+      e = f32 ? eqk::launch_strided_f32(p->nz, true, az, grid, s)
+              : eqk::launch_strided_f64(p->nz, true, az, grid, s);
     if (e != cudaSuccess) return fail_cuda(e, "z inverse pass");
   }
   mark(6);
-  k_finalize_norms<<<1, 128, 0, s>>>(p->partx, p->gx, linf ? p->partl : nullptr, p->gl, p->batch,
+  k_finalize_norms<<<1, 128, 0, s>>>(p->partx, p->gx, linf ? p->partl : nullptr, gl_used, p->batch,
                                      double(V), p->mean, p->instats, linf ? 0 : EQ_FLAG_NO_LINF,
                                      p->norms);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "norm finalisation");
@@ -436,6 +510,21 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
     p->gy = grid_for(p->info_y_f, ty, batch * 3);
     p->gx = grid_for(p->info_x, gxn, batch);
     p->gl = grid_for(p->info_z_i, tz, batch * 3);
+    // TMA path: one block per SM split over (field, component); needs whole x tiles
+    const char* no_tma = getenv("EQ_NO_TMA");
+    const bool allow = !(no_tma && no_tma[0] == '1') && encode_fn() != nullptr &&
+                       ((size_t)nx * p->esize) % 16 == 0;
+    cudaError_t te;
+    if (allow) {
+      te = dtype == EQ_F32 ? eqk::tma_info_f32(nz, &p->tz) : eqk::tma_info_f64(nz, &p->tz);
+      p->tma_z = te == cudaSuccess && nx % p->tz.cols == 0;
+      te = dtype == EQ_F32 ? eqk::tma_info_f32(ny, &p->ty) : eqk::tma_info_f64(ny, &p->ty);
+      p->tma_y = te == cudaSuccess && nx % p->ty.cols == 0;
+      cudaGetLastError();
+    }
+    const long long per = std::max(1, p->sms / (batch * 3));
+    p->gtz = (int)std::min<long long>(per, (long long)ny * (p->tma_z ? nx / p->tz.cols : 1));
+    p->gty = (int)std::min<long long>(per, (long long)nz * (p->tma_y ? nx / p->ty.cols : 1));
   }
   // tables
   std::vector<unsigned char> tw[3], xi[3];
@@ -450,9 +539,10 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
   for (int a = 0; a < 3; ++a) { o_tw[a] = off; off = align_up(off + tw[a].size(), 256); }
   for (int a = 0; a < 3; ++a) { o_xi[a] = off; off = align_up(off + xi[a].size(), 256); }
   const size_t o_pairs = off; off = align_up(off + sizeof(int) * pairs.size(), 256);
-  const size_t o_p1 = off; off = align_up(off + sizeof(double) * batch * 3 * p->g1 * 4, 256);
+  const size_t o_p1 = off; off = align_up(off + sizeof(double) * batch * 3 * std::max(p->g1, p->gtz) * 4, 256);
   const size_t o_px = off; off = align_up(off + sizeof(double) * batch * p->gx * 4, 256);
-  const size_t o_pl = off; off = align_up(off + sizeof(double) * batch * 3 * p->gl, 256);
+  const size_t o_pl = off; off = align_up(off + sizeof(double) * batch * 3 * std::max(p->gl, p->gtz), 256);
+  const size_t o_err = off; off = align_up(off + sizeof(int), 256);
   const size_t o_mean = off; off = align_up(off + sizeof(double) * batch * 6, 256);
   const size_t o_is = off; off = align_up(off + sizeof(double) * batch * 2, 256);
   const size_t o_nr = off; off = align_up(off + sizeof(eq_norms_t) * batch, 256);
@@ -479,6 +569,11 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
   p->mean = reinterpret_cast<double*>(base + o_mean);
   p->instats = reinterpret_cast<double*>(base + o_is);
   p->norms = reinterpret_cast<eq_norms_t*>(base + o_nr);
+  p->err = reinterpret_cast<int*>(base + o_err);
+  if ((e = cudaMemset(p->err, 0, sizeof(int))) != cudaSuccess) {
+    release(p);
+    return fail_cuda(e, "error flag");
+  }
   if ((e = cudaMemcpy(p->pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
     release(p);
     return fail_cuda(e, "pair table upload");
@@ -551,6 +646,15 @@ eq_status eq_norms(eq_plan* p, eq_norms_t* host_out) {
   if (!p->have_result) return fail(EQ_ERR_INVALID, "eq_norms: no projection enqueued yet");
   cudaError_t e;
   if ((e = cudaEventSynchronize(p->done)) != cudaSuccess) return fail_cuda(e, "eq_norms: wait");
+  if (p->err) {
+    int flag = 0;
+    if ((e = cudaMemcpy(&flag, p->err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return fail_cuda(e, "eq_norms: error flag");
+    if (flag) {
+      cudaMemset(p->err, 0, sizeof(int));
+      return fail(EQ_ERR_TIMEOUT, "eq_norms: a bounded wait inside a kernel ran out; results are invalid");
+    }
+  }
   const eq_norms_t* src = p->gen ? eqg::gen_norms_device(p->gen) : p->norms;
   if ((e = cudaMemcpy(host_out, src, sizeof(eq_norms_t) * p->batch, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return fail_cuda(e, "eq_norms: copy");

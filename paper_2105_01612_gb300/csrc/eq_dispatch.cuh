@@ -37,6 +37,37 @@ template <typename T, int N> struct Inst {
   }
 };
 
+template <typename T, int N> struct TmaInst {
+  static cudaError_t info(TmaInfo* out) {
+    using C = TmaCfg<T, N>;
+    if constexpr (!C::OK) {
+      return cudaErrorInvalidValue;
+    } else {
+      out->threads = C::THREADS;
+      out->cols = C::B;
+      out->box = C::BOX;
+      out->smem = C::SMEM;
+      cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_strided_tma<T, N, false>),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_strided_tma<T, N, true>),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      return e;
+    }
+  }
+  static cudaError_t launch(bool inv, const CUtensorMap& map, const TmaArgs& a, dim3 grid,
+                            cudaStream_t s) {
+    using C = TmaCfg<T, N>;
+    if constexpr (!C::OK) {
+      return cudaErrorInvalidValue;
+    } else {
+      if (inv) k_strided_tma<T, N, true><<<grid, C::THREADS, C::SMEM, s>>>(map, a);
+      else k_strided_tma<T, N, false><<<grid, C::THREADS, C::SMEM, s>>>(map, a);
+      return cudaGetLastError();
+    }
+  }
+};
+
 #define EQ_FOR_LENGTHS(X) X(1) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
 template <typename T> cudaError_t info_t(int n, PassKind kind, PassInfo* out) {
@@ -59,6 +90,25 @@ cudaError_t strided_t(int n, bool inv, const StridedArgs& a, dim3 grid, cudaStre
 template <typename T> cudaError_t xproj_t(int n, const XArgs& a, dim3 grid, cudaStream_t s) {
   switch (n) {
 #define EQ_CASE(N) case N: return Inst<T, N>::xproj(a, grid, s);
+    EQ_FOR_LENGTHS(EQ_CASE)
+#undef EQ_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T> cudaError_t tma_info_t(int n, TmaInfo* out) {
+  switch (n) {
+#define EQ_CASE(N) case N: return TmaInst<T, N>::info(out);
+    EQ_FOR_LENGTHS(EQ_CASE)
+#undef EQ_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T>
+cudaError_t tma_launch_t(int n, bool inv, const CUtensorMap& map, const TmaArgs& a, dim3 grid,
+                         cudaStream_t s) {
+  switch (n) {
+#define EQ_CASE(N) case N: return TmaInst<T, N>::launch(inv, map, a, grid, s);
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;

@@ -11,7 +11,13 @@ template <typename T> struct GenInst {
     return reinterpret_cast<const void*>(&k_gen_xproj<T>);
   }
   static cudaError_t occupancy(int kind, int threads, size_t smem, int* blocks) {
-    cudaError_t e = cudaFuncSetAttribute(fn(kind), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // one kernel serves passes with different shared-memory sizes: allow the device maximum
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess && (size_t)optin < smem) return cudaErrorInvalidValue;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn(kind), cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn(kind), threads, smem);
   }

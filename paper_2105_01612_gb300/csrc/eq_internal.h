@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "eq_kernels.cuh"
+#include "eq_tma.cuh"
 
 namespace eqk {
 
@@ -25,5 +26,17 @@ cudaError_t launch_strided_f32(int n, bool inv, const StridedArgs& a, dim3 grid,
 cudaError_t launch_strided_f64(int n, bool inv, const StridedArgs& a, dim3 grid, cudaStream_t s);
 cudaError_t launch_xproj_f32(int n, const XArgs& a, dim3 grid, cudaStream_t s);
 cudaError_t launch_xproj_f64(int n, const XArgs& a, dim3 grid, cudaStream_t s);
+
+// TMA-fed strided passes: info returns cudaErrorInvalidValue when no instance exists for n.
+struct TmaInfo {
+  int threads = 0, cols = 0, box = 0;
+  size_t smem = 0;
+};
+cudaError_t tma_info_f32(int n, TmaInfo* out);
+cudaError_t tma_info_f64(int n, TmaInfo* out);
+cudaError_t launch_tma_f32(int n, bool inv, const CUtensorMap& map, const TmaArgs& a, dim3 grid,
+                           cudaStream_t s);
+cudaError_t launch_tma_f64(int n, bool inv, const CUtensorMap& map, const TmaArgs& a, dim3 grid,
+                           cudaStream_t s);
 
 }  // namespace eqk

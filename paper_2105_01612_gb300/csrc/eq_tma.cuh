@@ -1,0 +1,211 @@
+// eq_tma.cuh - strided passes (z, y) with TMA-fed double buffering (sm_100+ bulk tensor copies).
+//
+// One block per SM walks its tiles (B consecutive x columns x all N points of one complex field).
+// Thread 0 issues cp.async.bulk.tensor loads of tile k+2 into the shared-memory stage that tile k
+// has just been read from, completing on that stage's mbarrier, so two tiles of loads are in
+// flight while the block transforms tile k (register Stockham stages, exchange buffer) and
+// stores it with plain coalesced stores.  Every mbarrier wait is bounded: if it runs out the
+// block raises the plan's error flag, waits (bounded) for its own copies in flight and leaves.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "eq_kernels.cuh"
+
+namespace eqk {
+
+constexpr long long TMA_WAIT_LIMIT = 1LL << 24;   // polls of one mbarrier phase (> 1 s)
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// true once the phase with the given parity has completed; false after TMA_WAIT_LIMIT polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_u32(bar);
+  for (long long i = 0; i < TMA_WAIT_LIMIT; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (i > 64) __nanosleep(64);
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, unsigned long long* bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <typename T, int N> struct TmaCfg {
+  static constexpr int E = 8;
+  static constexpr int TPC = N / E;
+  static constexpr int B = (sizeof(T) == 4 ? 16 : 8) * TPC <= 1024 ? (sizeof(T) == 4 ? 16 : 8)
+                                                                    : 1024 / TPC;
+  static constexpr int THREADS = B * TPC;
+  static constexpr int BOX = N < 256 ? N : 256;       // points per TMA box along the axis
+  static constexpr int NBOX = N / BOX;
+  using T2 = typename V2<T>::t;
+  static constexpr size_t STAGE_BYTES = 2 * sizeof(T) * size_t(N) * B;   // re + im planes
+  static constexpr size_t SMEM = 1024 /*align + barriers*/ + sizeof(T2) * N + 2 * STAGE_BYTES +
+                                 sizeof(T2) * size_t(N) * B;
+  static constexpr bool OK = N >= 64 && SMEM <= 227 * 1024;
+};
+
+struct TmaArgs {
+  const void* ref;         // last pass: input field for the L-inf residual (nullptr = skip)
+  void* out;               // destination field 0, plane 0
+  const void* tw;
+  double* partials;        // mode 1: [batch][3][grid][4]; mode 2: [batch][3][grid]
+  int* err;                // raised when a bounded wait runs out
+  long long field_stride, V;
+  int nx, ny, nz;
+  int axis;                // 2 = z, 1 = y
+  int mode;                // 0 middle, 1 first (statistics), 2 last
+  long long ntiles;        // tiles per (field, component)
+};
+
+template <typename T, int N, bool INV>
+__global__ void __launch_bounds__(TmaCfg<T, N>::THREADS, 1)
+k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
+  using C = TmaCfg<T, N>;
+  using T2 = typename C::T2;
+  constexpr int E = C::E, TPC = C::TPC, B = C::B, BOX = C::BOX, NBOX = C::NBOX;
+  extern __shared__ __align__(16) unsigned char smem_tma[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_tma) + 127) & ~uintptr_t(127));
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(base);
+  T* stage0 = reinterpret_cast<T*>(base + 128);
+  T* stage[2] = {stage0, stage0 + 2 * N * B};
+  T2* tw = reinterpret_cast<T2*>(stage0 + 4 * N * B);
+  T2* xbuf = tw + N;
+  __shared__ double red[32 * 4];
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x;
+  const int b = tid % B, t = tid / B;
+  const int field = blockIdx.y / 3, comp = blockIdx.y % 3;
+  const int plane_re = field * 6 + 2 * comp;
+  const long long fbase = field * a.field_stride + (2LL * comp) * a.V;
+  T* out_re = reinterpret_cast<T*>(a.out) + fbase;
+  T* out_im = out_re + a.V;
+  const T* ref_re = a.ref ? reinterpret_cast<const T*>(a.ref) + fbase : nullptr;
+  const T wa = comp == 2 ? T(2) : T(1), wb = comp == 0 ? T(1) : T(2);
+  const int tiles_x = a.nx / B;
+  const long long nstride = a.axis == 2 ? (long long)a.nx * a.ny : a.nx;
+
+  for (int i = tid; i < N; i += blockDim.x) tw[i] = reinterpret_cast<const T2*>(a.tw)[i];
+  if (tid == 0) {
+    abort_flag = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // coordinates of tile u: (x0, row) with row = y (z pass) or z (y pass)
+  int issued[2] = {0, 0};                              // loads issued per stage (thread 0)
+  auto issue = [&](long long u, int s) {
+    const int x0 = (int)(u % tiles_x) * B;
+    const int row = (int)(u / tiles_x);
+    ++issued[s];
+    mbar_expect_tx(&bar[s], (unsigned)C::STAGE_BYTES);
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int q = 0; q < NBOX; ++q) {
+        T* dst = stage[s] + p * N * B + q * BOX * B;
+        if (a.axis == 2) tma_load_4d(dst, &map, &bar[s], x0, row, q * BOX, plane_re + p);
+        else tma_load_4d(dst, &map, &bar[s], x0, q * BOX, row, plane_re + p);
+      }
+  };
+
+  const long long first = blockIdx.x, step = gridDim.x;
+  if (tid == 0) {
+    if (first < a.ntiles) issue(first, 0);
+    if (first + step < a.ntiles) issue(first + step, 1);
+  }
+
+  Kahan<T> sa, sb, sq;
+  T nonfinite = T(0), linf = T(0);
+  const IdxStrided idx{b, B};
+  int k = 0;
+  for (long long u = first; u < a.ntiles; u += step, ++k) {
+    const int s = k & 1;
+    if (!mbar_wait(&bar[s], (k >> 1) & 1)) {
+      atomicOr(a.err, 1);
+      abort_flag = 1;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    T2 x[E];
+    const T* sre = stage[s];
+    const T* sim = sre + N * B;
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = T2{sre[(t + TPC * e) * B + b], sim[(t + TPC * e) * B + b]};
+    __syncthreads();                                   // stage s is free again
+    if (tid == 0 && u + 2 * step < a.ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(u + 2 * step, s);
+    }
+    if (a.mode == 1) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        if (!isfinite(x[e].x) || !isfinite(x[e].y)) nonfinite += T(1);
+        sa.add(x[e].x);
+        sb.add(x[e].y);
+        sq.add(wa * x[e].x * x[e].x + wb * x[e].y * x[e].y);
+      }
+    }
+    fft_column<N, E, INV>(x, t, xbuf, idx, tw);
+    const int x0 = (int)(u % tiles_x) * B;
+    const long long row = u / tiles_x;
+    const long long col0 = a.axis == 2 ? row * a.nx + x0 + b : row * (long long)a.nx * a.ny + x0 + b;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const long long off = col0 + (long long)(t + TPC * e) * nstride;
+      out_re[off] = x[e].x;
+      out_im[off] = x[e].y;
+      if (ref_re) {
+        linf = fmax(linf, fabs(ref_re[off] - x[e].x));
+        linf = fmax(linf, fabs(ref_re[off + a.V] - x[e].y));
+      }
+    }
+  }
+  if (abort_flag) {
+    // leave no copy in flight: wait (bounded) for every phase this block issued
+    if (tid == 0)
+      for (int s = 0; s < 2; ++s)
+        if (issued[s] > 0) mbar_wait(&bar[s], (unsigned)((issued[s] - 1) & 1));
+    __syncthreads();
+    return;
+  }
+  if (a.mode == 1) {
+    double v[4] = {sa.value(), sb.value(), sq.value(), double(nonfinite)};
+    block_sum<4>(v, red);
+    if (tid == 0) {
+      double* p = a.partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 4;
+      p[0] = v[0]; p[1] = v[1]; p[2] = v[2]; p[3] = v[3];
+    }
+  } else if (a.mode == 2 && ref_re) {
+    double m = block_max(double(linf), red);
+    if (tid == 0) a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = m;
+  }
+}
+
+}  // namespace eqk

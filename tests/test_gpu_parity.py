@@ -112,7 +112,8 @@ def test_128cubed_beltrami_truth_plus_grain_perturbation(op, dtype):
 # ------------------------------------------------------------------ shapes, options, edge cases
 
 @pytest.mark.parametrize("shape", [(16, 16, 16), (8, 32, 16), (4, 8, 64), (32, 16, 8),
-                                   (2, 4, 128), (16, 256, 4), (8, 2, 512), (4, 4, 1024)])
+                                   (2, 4, 128), (16, 256, 4), (8, 2, 512), (4, 4, 1024),
+                                   (64, 128, 32), (256, 64, 16), (1024, 64, 16)])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_shapes(shape, dtype):
     s = field(shape, 6, 100.0, 10.0, sum(shape))
@@ -166,6 +167,22 @@ def test_batch_inplace_and_host_entry():
     plan.project_host(hin, hout)
     torch.testing.assert_close(hout, out.cpu(), rtol=0, atol=0)
     plan.close()
+
+
+def test_tma_and_plain_strided_passes_agree_bitwise(monkeypatch):
+    """The TMA-fed strided passes compute exactly what the plain-load passes compute."""
+    s = field((64, 128, 32), 9, 100.0, 10.0, 55)
+    outs = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("EQ_NO_TMA", flag)
+        for dtype in (torch.float32, torch.float64):
+            o, n = gpu_project(s, dtype)
+            outs.append((dtype, o, n))
+    for dtype in (torch.float32, torch.float64):
+        a = [o for d, o, _ in outs if d == dtype]
+        b = [n for d, _, n in outs if d == dtype]
+        assert np.array_equal(a[0], a[1])
+        assert b[0] == b[1]
 
 
 def test_deterministic_and_nonfinite_flag():
