@@ -115,6 +115,16 @@ eq_status eq_project_host(eq_plan* plan, const void* host_in, void* host_out, vo
 /* Wait for the plan's last eq_project and copy its `batch` diagnostics to host_out. */
 eq_status eq_norms(eq_plan* plan, eq_norms_t* host_out);
 
+/* Autotune the plan on the caller's buffers (d_in is only read; d_out is overwritten; work is
+ * enqueued on cuda_stream and the call waits for it).  Runtime-length plans time candidate
+ * shapes of each pass (tile columns and threads of the z and y passes, row pairs per block of the
+ * x pass) and keep the fastest; when the environment variable EQ_TUNE_CACHE names a file the
+ * choice is stored there (a JSON object keyed by sizes, dtype, options and GPU) and later plans
+ * with the same key start from it.  Power-of-two plans keep, per pass, the faster of the TMA /
+ * bulk-copy fed and the plain-load variants.  Results do not depend on the choice beyond the
+ * order of the FP64 norm reductions. */
+eq_status eq_plan_autotune(eq_plan* plan, const void* d_in, void* d_out, void* cuda_stream);
+
 /* Device bytes owned by the plan (tables, reduction buffers, host-call staging if any). */
 size_t eq_plan_workspace_bytes(const eq_plan* plan);
 

@@ -111,8 +111,7 @@ class Plan:
         self.shape = (int(batch), 6, int(nz), int(ny), int(nx))
         self.numel = _numel(self.shape)
         self.dtype = dtype
-        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
-            else torch.device(device)
+        self.device = _cuda_device(device)
         with torch.cuda.device(self.device):
             self.handle = eq_plan_create(nx, ny, nz, dtype, batch, op, h, nyq, want_linf)
 
@@ -148,6 +147,15 @@ class Plan:
         with torch.cuda.device(self.device):
             return eq_norms(self.handle, self.shape[0])
 
+    def autotune(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> None:
+        """Pick the fastest pass shapes on these buffers (out is overwritten)."""
+        self._check(x, "x")
+        self._check(out, "out")
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.load().eq_plan_autotune(self.handle, x.data_ptr(), out.data_ptr(),
+                                                    s.cuda_stream), "eq_plan_autotune")
+
     def set_timing(self, max_calls: int) -> None:
         eq_plan_set_timing(self.handle, max_calls)
 
@@ -180,8 +188,7 @@ class VarlenPlan(Plan):
         self.dtype = dtype
         self.numel = sum(6 * nx * ny * nz for nx, ny, nz in self.dims)
         self.shape = (len(self.dims), self.numel)
-        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
-            else torch.device(device)
+        self.device = _cuda_device(device)
         with torch.cuda.device(self.device):
             self.handle = eq_plan_create_varlen(self.dims, dtype, op, h, nyq, want_linf)
 
@@ -207,8 +214,7 @@ class Server:
     """Request loop (eq_server_*): single fields from host memory, admitted by HBM footprint."""
 
     def __init__(self, hbm_budget_bytes: int, max_inflight: int = 8, device=None):
-        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
-            else torch.device(device)
+        self.device = _cuda_device(device)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _lib.check(_lib.load().eq_server_create(int(hbm_budget_bytes), int(max_inflight),
@@ -264,6 +270,13 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def _cuda_device(device) -> torch.device:
+    d = torch.device("cuda") if device is None else torch.device(device)
+    if d.type != "cuda":
+        raise ValueError("plans live on a CUDA device")
+    return torch.device("cuda", torch.cuda.current_device() if d.index is None else d.index)
 
 
 def _numel(shape):

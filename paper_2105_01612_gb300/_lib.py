@@ -51,6 +51,7 @@ SIGNATURES = [
     ("eq_project_host", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("eq_norms", c_int, [c_void_p, ctypes.POINTER(EqNorms)]),
     ("eq_plan_workspace_bytes", c_size_t, [c_void_p]),
+    ("eq_plan_autotune", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("eq_plan_set_timing", c_int, [c_void_p, c_int]),
     ("eq_plan_pass_ms", c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
     ("eq_plan_destroy", None, [c_void_p]),

@@ -92,6 +92,19 @@ __global__ void k_finalize_norms(const double* __restrict__ partx, int gridx,
   }
 }
 
+namespace eqk {
+void finalize_mean(const double* part, int grid, int batch, double vol, double* mean,
+                   double* instats, cudaStream_t s) {
+  k_finalize_mean<<<1, 128, 0, s>>>(part, grid, batch, vol, mean, instats);
+}
+void finalize_norms(const double* partx, int gridx, const double* partl, int gridl, int batch,
+                    double vol, const double* mean, const double* instats, int linf_flag,
+                    eq_norms_t* out, cudaStream_t s) {
+  k_finalize_norms<<<1, 128, 0, s>>>(partx, gridx, partl, gridl, batch, vol, mean, instats,
+                                     linf_flag, out);
+}
+}  // namespace eqk
+
 // ---------------------------------------------------------------- plan
 
 struct eq_plan {
@@ -118,9 +131,10 @@ struct eq_plan {
   int g1 = 1, gy = 1, gx = 1, gl = 1;
   eqk::PassInfo info_z_f, info_y_f, info_x, info_y_i, info_z_i;
   // TMA-fed strided passes (used when an instance exists and the x extent tiles evenly)
-  eqk::TmaInfo tz, ty;
-  bool tma_z = false, tma_y = false;
-  int gtz = 1, gty = 1;
+  eqk::TmaInfo tz, ty, tx;
+  bool tma_z = false, tma_y = false, tma_x = false;
+  bool avail_z = false, avail_y = false, avail_x = false;   // instances exist for these sizes
+  int gtz = 1, gty = 1, gtx = 1;
   int* err = nullptr;          // raised by a kernel whose bounded wait ran out
   cudaEvent_t done = nullptr;
   bool have_result = false;
@@ -290,7 +304,23 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
   }
   mark(3);
   // pass 3: x forward + projector + x inverse
-  {
+  const bool on_x = p->tma_x && !(reinterpret_cast<uintptr_t>(d_out) & 15);
+  const int gx_used = on_x ? p->gtx : p->gx;
+  if (on_x) {
+    eqk::XTmaArgs x{};
+    x.data = d_out; x.tw = p->tw[0];
+    x.xi_x = p->xi[0]; x.xi_y = p->xi[1]; x.xi_z = p->xi[2];
+    x.pairs = p->pairs; x.mean = p->mean; x.partials = p->partx; x.err = p->err;
+    x.field_stride = fstride; x.V = V;
+    x.nx = p->nx; x.ny = p->ny; x.nz = p->nz;
+    x.npairs = p->npairs;
+    x.ngroups = (p->npairs + p->tx.cols - 1) / p->tx.cols;
+    x.nyq_zero = p->opts.nyq == EQ_NYQ_ZERO;
+    x.inv_v = 1.0 / double(V);
+    dim3 grid(p->gtx, p->batch);
+    e = f32 ? eqk::launch_xtma_f32(p->nx, x, grid, s) : eqk::launch_xtma_f64(p->nx, x, grid, s);
+    if (e != cudaSuccess) return fail_cuda(e, "x projection pass");
+  } else {
     eqk::XArgs x{};
     x.data = d_out; x.tw = p->tw[0];
     x.xi_x = p->xi[0]; x.xi_y = p->xi[1]; x.xi_z = p->xi[2];
@@ -330,7 +360,7 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     if (e != cudaSuccess) return fail_cuda(e, "z inverse pass");
   }
   mark(6);
-  k_finalize_norms<<<1, 128, 0, s>>>(p->partx, p->gx, linf ? p->partl : nullptr, gl_used, p->batch,
+  k_finalize_norms<<<1, 128, 0, s>>>(p->partx, gx_used, linf ? p->partl : nullptr, gl_used, p->batch,
                                      double(V), p->mean, p->instats, linf ? 0 : EQ_FLAG_NO_LINF,
                                      p->norms);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "norm finalisation");
@@ -522,6 +552,14 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
       p->tma_y = te == cudaSuccess && nx % p->ty.cols == 0;
       cudaGetLastError();
     }
+    if (allow) {
+      te = dtype == EQ_F32 ? eqk::xtma_info_f32(nx, &p->tx) : eqk::xtma_info_f64(nx, &p->tx);
+      p->tma_x = te == cudaSuccess;
+      cudaGetLastError();
+    }
+    p->gtx = (int)std::max(1LL, std::min<long long>(std::max(1, p->sms / batch),
+                                                    p->tma_x ? (p->npairs + p->tx.cols - 1) / p->tx.cols : 1));
+    p->avail_z = p->tma_z; p->avail_y = p->tma_y; p->avail_x = p->tma_x;
     const long long per = std::max(1, p->sms / (batch * 3));
     p->gtz = (int)std::min<long long>(per, (long long)ny * (p->tma_z ? nx / p->tz.cols : 1));
     p->gty = (int)std::min<long long>(per, (long long)nz * (p->tma_y ? nx / p->ty.cols : 1));
@@ -540,7 +578,7 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
   for (int a = 0; a < 3; ++a) { o_xi[a] = off; off = align_up(off + xi[a].size(), 256); }
   const size_t o_pairs = off; off = align_up(off + sizeof(int) * pairs.size(), 256);
   const size_t o_p1 = off; off = align_up(off + sizeof(double) * batch * 3 * std::max(p->g1, p->gtz) * 4, 256);
-  const size_t o_px = off; off = align_up(off + sizeof(double) * batch * p->gx * 4, 256);
+  const size_t o_px = off; off = align_up(off + sizeof(double) * batch * std::max(p->gx, p->gtx) * 4, 256);
   const size_t o_pl = off; off = align_up(off + sizeof(double) * batch * 3 * std::max(p->gl, p->gtz), 256);
   const size_t o_err = off; off = align_up(off + sizeof(int), 256);
   const size_t o_mean = off; off = align_up(off + sizeof(double) * batch * 6, 256);
@@ -694,6 +732,50 @@ eq_status eq_plan_pass_ms(eq_plan* p, double* ms_out, int* ncalls_out) {
   }
   if (ncalls_out) *ncalls_out = p->tused;
   p->tused = 0;
+  return EQ_OK;
+}
+
+eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stream) {
+  if (!p || !d_in || !d_out) return fail(EQ_ERR_INVALID, "eq_plan_autotune: NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+  if (p->gen) {
+    std::string err;
+    eq_status st = eqg::gen_autotune(p->gen, d_in, d_out, s, &err);
+    if (st != EQ_OK) return fail(st, "eq_plan_autotune: " + err);
+    return EQ_OK;
+  }
+  // power-of-two plans: per pass, keep the faster of the TMA / bulk-copy fed and the plain
+  // variant (measured with events between the passes, second of two runs)
+  cudaEvent_t ev[EQ_NUM_PASSES + 1];
+  for (auto& x : ev)
+    if ((e = cudaEventCreate(&x)) != cudaSuccess) return fail_cuda(e, "eq_plan_autotune: events");
+  float ms[2][EQ_NUM_PASSES] = {};
+  const int saved_cap = p->tcap, saved_used = p->tused;
+  for (int variant = 0; variant < 2; ++variant) {
+    p->tma_z = variant == 0 && p->avail_z;
+    p->tma_y = variant == 0 && p->avail_y;
+    p->tma_x = variant == 0 && p->avail_x;
+    for (int rep = 0; rep < 2; ++rep) {
+      // enqueue with this call's own events
+      std::vector<cudaEvent_t> keep(p->tev);
+      p->tev.assign(ev, ev + EQ_NUM_PASSES + 1);
+      p->tcap = 1; p->tused = 0;
+      eq_status st = enqueue(p, d_in, d_out, s);
+      p->tev.swap(keep);
+      if (st != EQ_OK) { p->tcap = saved_cap; p->tused = saved_used; return st; }
+      cudaEventSynchronize(ev[EQ_NUM_PASSES]);
+      for (int i = 0; i < EQ_NUM_PASSES; ++i) cudaEventElapsedTime(&ms[variant][i], ev[i], ev[i + 1]);
+    }
+  }
+  p->tcap = saved_cap; p->tused = saved_used;
+  for (auto& x : ev) cudaEventDestroy(x);
+  // pass indices: 0 z forward, 2 y forward, 3 x, 4 y inverse, 5 z inverse
+  p->tma_z = p->avail_z && ms[0][0] + ms[0][5] <= ms[1][0] + ms[1][5];
+  p->tma_y = p->avail_y && ms[0][2] + ms[0][4] <= ms[1][2] + ms[1][4];
+  p->tma_x = p->avail_x && ms[0][3] <= ms[1][3];
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "eq_plan_autotune");
   return EQ_OK;
 }
 

@@ -68,6 +68,31 @@ template <typename T, int N> struct TmaInst {
   }
 };
 
+template <typename T, int N> struct XTmaInst {
+  static cudaError_t info(TmaInfo* out) {
+    using C = XTmaCfg<T, N>;
+    if constexpr (!C::OK) {
+      return cudaErrorInvalidValue;
+    } else {
+      out->threads = C::THREADS;
+      out->cols = C::P;
+      out->box = 0;
+      out->smem = C::SMEM;
+      return cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_xproj_tma<T, N>),
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    }
+  }
+  static cudaError_t launch(const XTmaArgs& a, dim3 grid, cudaStream_t s) {
+    using C = XTmaCfg<T, N>;
+    if constexpr (!C::OK) {
+      return cudaErrorInvalidValue;
+    } else {
+      k_xproj_tma<T, N><<<grid, C::THREADS, C::SMEM, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
+};
+
 #define EQ_FOR_LENGTHS(X) X(1) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
 template <typename T> cudaError_t info_t(int n, PassKind kind, PassInfo* out) {
@@ -109,6 +134,23 @@ cudaError_t tma_launch_t(int n, bool inv, const CUtensorMap& map, const TmaArgs&
                          cudaStream_t s) {
   switch (n) {
 #define EQ_CASE(N) case N: return TmaInst<T, N>::launch(inv, map, a, grid, s);
+    EQ_FOR_LENGTHS(EQ_CASE)
+#undef EQ_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T> cudaError_t xtma_info_t(int n, TmaInfo* out) {
+  switch (n) {
+#define EQ_CASE(N) case N: return XTmaInst<T, N>::info(out);
+    EQ_FOR_LENGTHS(EQ_CASE)
+#undef EQ_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T> cudaError_t xtma_launch_t(int n, const XTmaArgs& a, dim3 grid, cudaStream_t s) {
+  switch (n) {
+#define EQ_CASE(N) case N: return XTmaInst<T, N>::launch(a, grid, s);
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;

@@ -14,4 +14,8 @@ cudaError_t launch_tma_f32(int n, bool inv, const CUtensorMap& map, const TmaArg
                            cudaStream_t s) {
   return tma_launch_t<float>(n, inv, map, a, grid, s);
 }
+cudaError_t xtma_info_f32(int n, TmaInfo* out) { return xtma_info_t<float>(n, out); }
+cudaError_t launch_xtma_f32(int n, const XTmaArgs& a, dim3 grid, cudaStream_t s) {
+  return xtma_launch_t<float>(n, a, grid, s);
+}
 }  // namespace eqk

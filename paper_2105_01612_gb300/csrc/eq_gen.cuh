@@ -93,13 +93,14 @@ __device__ __forceinline__ void dft_small(T2 (&v)[R], const T2 (&wr)[R]) {
   }
 }
 
-// one Stockham stage of radix R over C columns: src -> dst
+// one Stockham stage of radix R over C columns: src -> dst.  blockDim.x must be a multiple of C;
+// thread t works on column t % C and butterflies t / C, t / C + blockDim.x / C, ...
 template <int R, bool INV, typename T2>
 __device__ __forceinline__ void gen_stage(const T2* __restrict__ src, T2* __restrict__ dst, int m,
                                           int ns, int C, int pitch, const T2* __restrict__ tw) {
   const int nb = m / R;
-  const int total = nb * C;
   const int tstep = m / (ns * R);
+  const int col = threadIdx.x % C, jstep = blockDim.x / C;
   T2 wr[R];
 #pragma unroll
   for (int q = 0; q < R; ++q) {
@@ -107,8 +108,7 @@ __device__ __forceinline__ void gen_stage(const T2* __restrict__ src, T2* __rest
     if (INV) w.y = -w.y;
     wr[q] = w;
   }
-  for (int w = threadIdx.x; w < total; w += blockDim.x) {
-    const int col = w % C, j = w / C;
+  for (int j = threadIdx.x / C; j < nb; j += jstep) {
     T2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * pitch + col];
@@ -152,36 +152,45 @@ __device__ T2* gen_fft(T2* a, T2* b, const AxisPlan& ap, int C, int pitch, const
   return a;
 }
 
-// Full axis transform of the C columns held in `a` (n valid elements each, element-major).
-// For Bluestein the caller has already multiplied by the chirp and zero-filled [n, m).
-// Returns the buffer with the n outputs (before the Bluestein post-chirp, see blue_post).
+// Per-item copy of an axis plan's tables into shared memory: twiddles (m), chirp (n), chirp
+// transform (m).
 template <typename T2>
-__device__ T2* axis_transform(T2* a, T2* b, const AxisPlan& ap, int C, int pitch,
-                              const T2* __restrict__ cpool, bool inv) {
-  const T2* tw = cpool + ap.tw;
-  if (!ap.blue) return inv ? gen_fft<true>(a, b, ap, C, pitch, tw) : gen_fft<false>(a, b, ap, C, pitch, tw);
-  T2* r = gen_fft<false>(a, b, ap, C, pitch, tw);
-  T2* o = (r == a) ? b : a;
-  const T2* bh = cpool + ap.bhat;
-  for (int w = threadIdx.x; w < ap.m * C; w += blockDim.x) {
-    const int col = w % C, k = w / C;
-    r[k * pitch + col] = cmul(r[k * pitch + col], bh[k]);
+__device__ __forceinline__ void load_tables(const AxisPlan& ap, const T2* __restrict__ cpool,
+                                            T2* tws, T2* chs, T2* bhs) {
+  for (int i = threadIdx.x; i < ap.m; i += blockDim.x) {
+    tws[i] = cpool[ap.tw + i];
+    if (ap.blue) bhs[i] = cpool[ap.bhat + i];
   }
+  if (ap.blue)
+    for (int i = threadIdx.x; i < ap.n; i += blockDim.x) chs[i] = cpool[ap.chirp + i];
+}
+
+// Full axis transform of the C columns held in `a` (element-major, pitch `pitch`).  For Bluestein
+// the caller has already multiplied by the chirp and zero-filled [n, m).  Returns the buffer with
+// the outputs (before the Bluestein post-chirp, see post()).
+template <typename T2>
+__device__ T2* axis_transform(T2* a, T2* b, const AxisPlan& ap, int C, int pitch, const T2* tws,
+                              const T2* bhs, bool inv) {
+  if (!ap.blue) return inv ? gen_fft<true>(a, b, ap, C, pitch, tws) : gen_fft<false>(a, b, ap, C, pitch, tws);
+  T2* r = gen_fft<false>(a, b, ap, C, pitch, tws);
+  T2* o = (r == a) ? b : a;
+  const int col = threadIdx.x % C, jstep = blockDim.x / C;
+  for (int k = threadIdx.x / C; k < ap.m; k += jstep) r[k * pitch + col] = cmul(r[k * pitch + col], bhs[k]);
   __syncthreads();
-  return gen_fft<true>(r, o, ap, C, pitch, tw);
+  return gen_fft<true>(r, o, ap, C, pitch, tws);
 }
 
 // value to place in the work buffer for input element j of a transform (pre-chirp, conj trick)
 template <typename T2>
-__device__ __forceinline__ T2 pre(T2 x, int j, const AxisPlan& ap, const T2* cpool, bool inv) {
+__device__ __forceinline__ T2 pre(T2 x, int j, const AxisPlan& ap, const T2* chs, bool inv) {
   if (!ap.blue) return x;
   if (inv) x.y = -x.y;
-  return cmul(x, cpool[ap.chirp + j]);
+  return cmul(x, chs[j]);
 }
 template <typename T2>
-__device__ __forceinline__ T2 post(T2 y, int k, const AxisPlan& ap, const T2* cpool, bool inv) {
+__device__ __forceinline__ T2 post(T2 y, int k, const AxisPlan& ap, const T2* chs, bool inv) {
   if (!ap.blue) return y;
-  T2 r = cmul(y, cpool[ap.chirp + k]);
+  T2 r = cmul(y, chs[k]);
   if (inv) r.y = -r.y;
   return r;
 }
@@ -206,23 +215,45 @@ __device__ __forceinline__ void warp_partials(double (&v)[K], double* dst) {
     for (int k = 0; k < K; ++k) dst[(threadIdx.x >> 5) * K + k] = v[k];
 }
 
+// Shared memory of the runtime-length kernels: two work buffers of mmax x pitch, then the
+// per-item tables (twiddles, chirp, chirp transform: mmax entries each).
+template <typename T2> struct GenSmem {
+  T2 *a, *b, *tw, *ch, *bh;
+  __device__ GenSmem(unsigned char* raw, int mmax, int pitch) {
+    a = reinterpret_cast<T2*>(raw);
+    b = a + (size_t)mmax * pitch;
+    tw = b + (size_t)mmax * pitch;
+    ch = tw + mmax;
+    bh = ch + mmax;
+  }
+};
+
 // Strided pass (axis y or z) over a list of fields, any lengths.
 // Item = (field, component, chunk of tiles_per_item tiles of C consecutive columns).
+// blockDim.x must be a multiple of C.
 template <typename T, bool INV>
 __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
   using T2 = typename eqk::V2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2* bufA = reinterpret_cast<T2*>(smem_raw);
-  T2* bufB = bufA + (size_t)a.mmax * a.pitch;
+  const GenSmem<T2> sm(smem_raw, a.mmax, a.pitch);
   const T2* cpool = reinterpret_cast<const T2*>(a.cpool);
   const int C = a.cols, pitch = a.pitch;
   const int nw = blockDim.x >> 5;
+  const int col = threadIdx.x % C, j0 = threadIdx.x / C, jstep = blockDim.x / C;
+  int cur_ax = -1;
 
   for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
     const int f = find_field(a.item0, a.nfields, item);
     const FieldDesc fd = a.fields[f];
-    const AxisPlan& ap = a.axes[fd.ax[a.axis]];
-    const int n = ap.n;
+    const int axi = fd.ax[a.axis];
+    const AxisPlan& ap = a.axes[axi];
+    if (axi != cur_ax) {                       // tables of this axis length into shared memory
+      __syncthreads();
+      load_tables(ap, cpool, sm.tw, sm.ch, sm.bh);
+      __syncthreads();
+      cur_ax = axi;
+    }
+    const int n = ap.n, m = ap.m;
     long long inner, nstride, outer_stride, ncols;
     if (a.axis == 2) { inner = (long long)fd.nx * fd.ny; nstride = inner; outer_stride = 0; ncols = inner; }
     else { inner = fd.nx; nstride = fd.nx; outer_stride = (long long)fd.nx * fd.ny; ncols = (long long)fd.nz * fd.nx; }
@@ -242,14 +273,14 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
     const bool inv = INV;
     for (long long tile = chunk * a.tiles_per_item;
          tile < ntiles && tile < (chunk + 1) * a.tiles_per_item; ++tile) {
-      // load: element j of column col -> bufA[j][col]
-      for (int w = threadIdx.x; w < ap.m * C; w += blockDim.x) {
-        const int col = w % C, j = w / C;
-        const long long c = tile * C + col;
+      const long long c = tile * C + col;
+      const bool valid = c < ncols;
+      const long long o = valid ? c / inner : 0;
+      const long long base = o * outer_stride + (valid ? c - o * inner : 0);
+      for (int j = j0; j < m; j += jstep) {
         T2 x = {T(0), T(0)};
-        if (j < n && c < ncols) {
-          const long long o = c / inner, ii = c - o * inner;
-          const long long off = o * outer_stride + ii + (long long)j * nstride;
+        if (j < n && valid) {
+          const long long off = base + (long long)j * nstride;
           x = T2{in_re[off], in_im[off]};
           if (a.mode == 1) {
             if (!isfinite(x.x) || !isfinite(x.y)) nonfinite += T(1);
@@ -257,19 +288,16 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
             sb.add(x.y);
             sq.add(wa * x.x * x.x + wb * x.y * x.y);
           }
-          x = pre(x, j, ap, cpool, inv);
+          x = pre(x, j, ap, sm.ch, inv);
         }
-        bufA[j * pitch + col] = x;
+        sm.a[j * pitch + col] = x;
       }
       __syncthreads();
-      T2* r = axis_transform(bufA, bufB, ap, C, pitch, cpool, inv);
-      for (int w = threadIdx.x; w < n * C; w += blockDim.x) {
-        const int col = w % C, k = w / C;
-        const long long c = tile * C + col;
-        if (c < ncols) {
-          const long long o = c / inner, ii = c - o * inner;
-          const long long off = o * outer_stride + ii + (long long)k * nstride;
-          const T2 y = post(r[k * pitch + col], k, ap, cpool, inv);
+      T2* r = axis_transform(sm.a, sm.b, ap, C, pitch, sm.tw, sm.bh, inv);
+      if (valid) {
+        for (int k = j0; k < n; k += jstep) {
+          const long long off = base + (long long)k * nstride;
+          const T2 y = post(r[k * pitch + col], k, ap, sm.ch, inv);
           out_re[off] = y.x;
           out_im[off] = y.y;
           if (ref_re) {
@@ -286,10 +314,10 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
       for (int k = nw * 4 + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
         a.partials[item * WARPS_MAX * 4 + k] = 0.0;
     } else if (a.mode == 2) {
-      double v[1] = {double(linf)};
+      double v = double(linf);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v[0] = fmax(v[0], __shfl_down_sync(0xffffffffu, v[0], o));
-      if ((threadIdx.x & 31) == 0) a.partials[item * WARPS_MAX * 4 + (threadIdx.x >> 5)] = v[0];
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+      if ((threadIdx.x & 31) == 0) a.partials[item * WARPS_MAX * 4 + (threadIdx.x >> 5)] = v;
       for (int k = nw + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
         a.partials[item * WARPS_MAX * 4 + k] = 0.0;
     }
@@ -297,23 +325,30 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
 }
 
 // Fused x pass over a list of fields, any lengths.  Item = (field, tiles_per_item groups of P
-// row pairs); C = 6 P columns.
+// row pairs); C = 6 P columns; blockDim.x = 32 C (one warp per row for the global loads).
 template <typename T>
 __global__ void __launch_bounds__(512) k_gen_xproj(const GenArgs a) {
   using T2 = typename eqk::V2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2* bufA = reinterpret_cast<T2*>(smem_raw);
-  T2* bufB = bufA + (size_t)a.mmax * a.pitch;
+  const GenSmem<T2> sm(smem_raw, a.mmax, a.pitch);
   const T2* cpool = reinterpret_cast<const T2*>(a.cpool);
   const T* xipool = reinterpret_cast<const T*>(a.xipool);
   const int C = a.cols, pitch = a.pitch, P = C / 6;
   const int nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;       // one warp per row
+  int cur_ax = -1;
 
   for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
     const int f = find_field(a.item0, a.nfields, item);
     const FieldDesc fd = a.fields[f];
     const AxisPlan& ap = a.axes[fd.ax[0]];
-    const int nx = fd.nx, ny = fd.ny, nz = fd.nz;
+    if (fd.ax[0] != cur_ax) {
+      __syncthreads();
+      load_tables(ap, cpool, sm.tw, sm.ch, sm.bh);
+      __syncthreads();
+      cur_ax = fd.ax[0];
+    }
+    const int nx = fd.nx, ny = fd.ny, nz = fd.nz, m = ap.m;
     const long long local = item - a.item0[f];
     const int* pairs = a.pairpool + fd.pairs;
     T* base = reinterpret_cast<T*>(a.out) + fd.out_off;
@@ -325,32 +360,29 @@ __global__ void __launch_bounds__(512) k_gen_xproj(const GenArgs a) {
     const double vol = double(fd.V);
     Kahan<T> r2, di2, do2, o2;
     const int ngroups = (fd.npairs + P - 1) / P;
+    // row handled by this warp: column wrow = slot * 6 + side * 3 + comp
+    const int slot = wrow / 6, side = (wrow % 6) / 3, comp = wrow % 3;
     for (int g = (int)(local * a.tiles_per_item);
          g < ngroups && g < (local + 1) * a.tiles_per_item; ++g) {
-      // load the 6 P rows: column col = slot * 6 + side * 3 + comp
-      for (int w = threadIdx.x; w < ap.m * C; w += blockDim.x) {
-        const int col = w / ap.m, j = w - col * ap.m;      // consecutive threads along a row
-        const int slot = col / 6, side = (col % 6) / 3, comp = col % 3;
-        const int p = g * P + slot;
+      const int p = g * P + slot;
+      long long roff = -1;
+      if (p < fd.npairs) {
+        const int rA = pairs[p];
+        const int kz = rA / ny, ky = rA - kz * ny;
+        const int rB = (kz == 0 ? 0 : nz - kz) * ny + (ky == 0 ? 0 : ny - ky);
+        if (!(side == 1 && rA == rB)) roff = (long long)(side == 0 ? rA : rB) * nx + 2LL * comp * fd.V;
+      }
+      for (int j = lane; j < m; j += 32) {
         T2 x = {T(0), T(0)};
-        if (j < nx && p < fd.npairs) {
-          const int rA = pairs[p];
-          const int kz = rA / ny, ky = rA - kz * ny;
-          const int rB = (kz == 0 ? 0 : nz - kz) * ny + (ky == 0 ? 0 : ny - ky);
-          if (!(side == 1 && rA == rB)) {
-            const long long off = (long long)(side == 0 ? rA : rB) * nx + j + 2LL * comp * fd.V;
-            x = pre(T2{base[off], base[off + fd.V]}, j, ap, cpool, false);
-          }
-        }
-        bufA[j * pitch + col] = x;
+        if (j < nx && roff >= 0) x = pre(T2{base[roff + j], base[roff + j + fd.V]}, j, ap, sm.ch, false);
+        sm.a[j * pitch + wrow] = x;
       }
       __syncthreads();
-      T2* r = axis_transform(bufA, bufB, ap, C, pitch, cpool, false);
+      T2* r = axis_transform(sm.a, sm.b, ap, C, pitch, sm.tw, sm.bh, false);
       if (ap.blue) {
-        for (int w = threadIdx.x; w < nx * C; w += blockDim.x) {
-          const int col = w % C, k = w / C;
-          r[k * pitch + col] = post(r[k * pitch + col], k, ap, cpool, false);
-        }
+        const int col = threadIdx.x % C, jstep = blockDim.x / C;
+        for (int k = threadIdx.x / C; k < nx; k += jstep)
+          r[k * pitch + col] = post(r[k * pitch + col], k, ap, sm.ch, false);
         __syncthreads();
       }
       for (int it = threadIdx.x; it < P * nx; it += blockDim.x) {
@@ -379,30 +411,21 @@ __global__ void __launch_bounds__(512) k_gen_xproj(const GenArgs a) {
         }
       }
       __syncthreads();
-      // inverse: move to bufA (pre-chirp for Bluestein), transform, store
-      T2* other = (r == bufA) ? bufB : bufA;
-      for (int w = threadIdx.x; w < ap.m * C; w += blockDim.x) {
-        const int j = w / C, col = w % C;
-        T2 x = {T(0), T(0)};
-        if (j < nx) x = pre(r[j * pitch + col], j, ap, cpool, true);
-        other[j * pitch + col] = x;
+      // inverse: move to the other buffer (pre-chirp for Bluestein), transform, store
+      T2* other = (r == sm.a) ? sm.b : sm.a;
+      {
+        const int col = threadIdx.x % C, jstep = blockDim.x / C;
+        for (int j = threadIdx.x / C; j < m; j += jstep)
+          other[j * pitch + col] = j < nx ? pre(r[j * pitch + col], j, ap, sm.ch, true) : T2{T(0), T(0)};
       }
       __syncthreads();
-      T2* q = axis_transform(other, r, ap, C, pitch, cpool, true);
-      for (int w = threadIdx.x; w < nx * C; w += blockDim.x) {
-        const int col = w / nx, j = w - col * nx;
-        const int slot = col / 6, side = (col % 6) / 3, comp = col % 3;
-        const int p = g * P + slot;
-        if (p >= fd.npairs) continue;
-        const int rA = pairs[p];
-        const int kz = rA / ny, ky = rA - kz * ny;
-        const int rB = (kz == 0 ? 0 : nz - kz) * ny + (ky == 0 ? 0 : ny - ky);
-        if (side == 1 && rA == rB) continue;
-        const long long off = (long long)(side == 0 ? rA : rB) * nx + j + 2LL * comp * fd.V;
-        const T2 y = post(q[j * pitch + col], j, ap, cpool, true);
-        base[off] = y.x;
-        base[off + fd.V] = y.y;
-      }
+      T2* q = axis_transform(other, r, ap, C, pitch, sm.tw, sm.bh, true);
+      if (roff >= 0)
+        for (int j = lane; j < nx; j += 32) {
+          const T2 y = post(q[j * pitch + wrow], j, ap, sm.ch, true);
+          base[roff + j] = y.x;
+          base[roff + j + fd.V] = y.y;
+        }
       __syncthreads();
     }
     double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};

@@ -2,6 +2,10 @@
 // descriptors, work-item prefix sums, launches.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <sstream>
 #include <complex>
 #include <map>
 #include <new>
@@ -126,6 +130,11 @@ struct GenPlan {
   PassShape z, y, x;
   std::vector<FieldDesc> fh;
   std::vector<AxisPlan> ah;
+  int mx[3] = {1, 1, 1};       // largest transform length per axis (x, y, z)
+  void* wmem = nullptr;        // work allocation: item prefix sums and partials
+  size_t wbytes = 0;
+  GenTune tune;
+  std::string key;             // tuning-cache key
 };
 
 namespace {
@@ -287,90 +296,33 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
     g->fh.push_back(fd);
   }
   g->total_elems = off;
-  // pass shapes
-  const size_t budget = 200 * 1024;
-  auto strided_cols = [&](int m) {
-    int C = es == 4 ? 16 : 8;
-    while (C > 1 && 2 * (size_t)m * C * cs > budget) C /= 2;
-    return C;
-  };
-  PassShape* ps[3] = {&g->z, &g->y, &g->x};
-  g->z.kind = 0; g->z.mmax = mx[2];
-  g->y.kind = 0; g->y.mmax = mx[1];
-  g->x.kind = 2; g->x.mmax = mx[0];
-  for (PassShape* p : {&g->z, &g->y}) {
-    p->cols = strided_cols(p->mmax);
-    p->pitch = p->cols;
-    p->threads = 256;
-    p->smem = 2 * (size_t)p->mmax * p->pitch * cs;
-  }
+  g->mx[0] = mx[0]; g->mx[1] = mx[1]; g->mx[2] = mx[2];
   {
-    int P = 2;
-    while (P > 1 && 2 * (size_t)g->x.mmax * (6 * P + 1) * cs > budget) --P;
-    g->x.cols = 6 * P;
-    g->x.pitch = 6 * P + 1;
-    g->x.threads = 256;
-    g->x.smem = 2 * (size_t)g->x.mmax * g->x.pitch * cs;
-    if (g->x.smem > 227 * 1024) {
-      *err = "x length too large for the runtime-length path";
-      delete g;
-      return EQ_ERR_INVALID;
+    // tuning-cache key: sizes (FNV-1a of the dims list), dtype, options, GPU
+    unsigned long long h = 1469598103934665603ULL;
+    for (int i = 0; i < 3 * count; ++i) {
+      h ^= (unsigned long long)dims[i];
+      h *= 1099511628211ULL;
     }
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::string gpu = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "gpu";
+    for (char& c : gpu) if (c == '"' || c == '\\') c = '_';
+    char buf[512];
+    snprintf(buf, sizeof(buf), "gen|%s|op%d|nyq%d|%.6g,%.6g,%.6g|n%d|%016llx|%s|%d",
+             dtype == EQ_F32 ? "f32" : "f64", (int)o.op, (int)o.nyq, o.hx, o.hy, o.hz, count, h,
+             gpu.c_str(), sms);
+    g->key = buf;
   }
-  // work items per field and pass; tiles per item chosen for about 8 items per resident block
-  std::vector<long long> iz(count + 1), iy(count + 1), ix(count + 1);
-  for (int pi = 0; pi < 3; ++pi) {
-    PassShape* p = ps[pi];
-    int blocks = 0;
-    cudaError_t e = occupancy(dtype, pi == 2 ? 2 : 0, p->threads, p->smem, &blocks);
-    if (e == cudaSuccess) e = occupancy(dtype, pi == 2 ? 2 : 1, p->threads, p->smem, &blocks);
-    if (e != cudaSuccess || blocks < 1) {
-      *err = std::string("occupancy: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "0 blocks");
-      delete g;
-      return EQ_ERR_CUDA;
-    }
-    const long long resident = (long long)sms * blocks;
-    long long total_tiles = 0;
-    for (const FieldDesc& fd : g->fh) {
-      if (pi == 2) total_tiles += (fd.npairs + (p->cols / 6) - 1) / (p->cols / 6);
-      else {
-        const long long ncols = pi == 0 ? (long long)fd.nx * fd.ny : (long long)fd.nz * fd.nx;
-        total_tiles += 3 * ((ncols + p->cols - 1) / p->cols);
-      }
-    }
-    p->tpi = (int)std::max(1LL, total_tiles / (8 * resident));
-    std::vector<long long>& pre = pi == 0 ? iz : (pi == 1 ? iy : ix);
-    pre[0] = 0;
-    for (int f = 0; f < count; ++f) {
-      const FieldDesc& fd = g->fh[f];
-      long long items;
-      if (pi == 2) {
-        const long long groups = (fd.npairs + (p->cols / 6) - 1) / (p->cols / 6);
-        items = (groups + p->tpi - 1) / p->tpi;
-      } else {
-        const long long ncols = pi == 0 ? (long long)fd.nx * fd.ny : (long long)fd.nz * fd.nx;
-        const long long ntiles = (ncols + p->cols - 1) / p->cols;
-        items = 3 * ((ntiles + p->tpi - 1) / p->tpi);
-      }
-      pre[f + 1] = pre[f] + items;
-    }
-    p->nitems = pre[count];
-    p->grid = (int)std::max(1LL, std::min(resident, p->nitems));
-  }
-  // one device allocation for everything
-  size_t o_f = 0, cur = 0;
+  // tables: one device allocation
+  size_t cur = 0;
   auto take = [&](size_t bytes) { size_t at = cur; cur = align_up(cur + bytes, 256); return at; };
-  o_f = take(sizeof(FieldDesc) * count);
+  const size_t o_f = take(sizeof(FieldDesc) * count);
   const size_t o_a = take(sizeof(AxisPlan) * g->ah.size());
   const size_t o_c = take(cpool.size());
   const size_t o_xi = take(xipool.size());
   const size_t o_pp = take(sizeof(int) * std::max<size_t>(1, pairpool.size()));
-  const size_t o_iz = take(sizeof(long long) * (count + 1));
-  const size_t o_iy = take(sizeof(long long) * (count + 1));
-  const size_t o_ix = take(sizeof(long long) * (count + 1));
-  const size_t o_pf = take(sizeof(double) * g->z.nitems * WARPS_MAX * 4);
-  const size_t o_px = take(sizeof(double) * g->x.nitems * WARPS_MAX * 4);
-  const size_t o_pl = take(sizeof(double) * g->z.nitems * WARPS_MAX * 4);
   const size_t o_m = take(sizeof(double) * 6 * count);
   const size_t o_is = take(sizeof(double) * 2 * count);
   const size_t o_n = take(sizeof(eq_norms_t) * count);
@@ -388,12 +340,6 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
   g->cpool = b + o_c;
   g->xipool = b + o_xi;
   g->pairpool = reinterpret_cast<int*>(b + o_pp);
-  g->z.item0 = reinterpret_cast<long long*>(b + o_iz);
-  g->y.item0 = reinterpret_cast<long long*>(b + o_iy);
-  g->x.item0 = reinterpret_cast<long long*>(b + o_ix);
-  g->part_first = reinterpret_cast<double*>(b + o_pf);
-  g->part_x = reinterpret_cast<double*>(b + o_px);
-  g->part_last = reinterpret_cast<double*>(b + o_pl);
   g->mean = reinterpret_cast<double*>(b + o_m);
   g->instats = reinterpret_cast<double*>(b + o_is);
   g->norms = reinterpret_cast<eq_norms_t*>(b + o_n);
@@ -402,10 +348,7 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
       {g->axes, g->ah.data(), sizeof(AxisPlan) * g->ah.size()},
       {g->cpool, cpool.data(), cpool.size()},
       {g->xipool, xipool.data(), xipool.size()},
-      {g->pairpool, pairpool.data(), sizeof(int) * pairpool.size()},
-      {g->z.item0, iz.data(), sizeof(long long) * (count + 1)},
-      {g->y.item0, iy.data(), sizeof(long long) * (count + 1)},
-      {g->x.item0, ix.data(), sizeof(long long) * (count + 1)}};
+      {g->pairpool, pairpool.data(), sizeof(int) * pairpool.size()}};
   for (const Up& u : ups) {
     if (u.n == 0) continue;
     if ((e = cudaMemcpy(u.d, u.h, u.n, cudaMemcpyHostToDevice)) != cudaSuccess) {
@@ -414,7 +357,121 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
       return EQ_ERR_CUDA;
     }
   }
+  // pass shapes: the tuning cache if it knows this plan, else the defaults
+  GenTune t = gen_default_tune(g);
+  gen_cache_lookup(g, &t);
+  eq_status st = gen_configure(g, t, err);
+  if (st != EQ_OK) {
+    gen_destroy(g);
+    return st;
+  }
   *out = g;
+  return EQ_OK;
+}
+
+GenTune gen_default_tune(const GenPlan* g) {
+  const size_t es = g->dtype == EQ_F32 ? 4 : 8;
+  GenTune t;
+  t.zc = es == 4 ? (g->mx[2] > 256 ? 8 : 16) : (g->mx[2] > 256 ? 4 : 8);
+  t.yc = es == 4 ? (g->mx[1] > 256 ? 8 : 16) : (g->mx[1] > 256 ? 4 : 8);
+  t.zt = t.yt = 256;
+  t.xp = g->mx[0] > 256 ? 1 : 2;
+  return t;
+}
+
+// Set the pass shapes (tile columns, threads, row pairs) and rebuild the work-item tables and
+// the partial buffers for them.
+eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
+  const size_t cs = g->dtype == EQ_F32 ? 8 : 16;
+  const size_t limit = 227 * 1024;
+  PassShape z = g->z, y = g->y, x = g->x;
+  z.kind = 0; z.mmax = g->mx[2]; z.cols = t.zc; z.pitch = t.zc; z.threads = t.zt;
+  y.kind = 0; y.mmax = g->mx[1]; y.cols = t.yc; y.pitch = t.yc; y.threads = t.yt;
+  x.kind = 2; x.mmax = g->mx[0]; x.cols = 6 * t.xp; x.pitch = 6 * t.xp + 1; x.threads = 32 * x.cols;
+  PassShape* ps[3] = {&z, &y, &x};
+  for (PassShape* p : ps) {
+    p->smem = (2 * (size_t)p->mmax * p->pitch + 3 * (size_t)p->mmax) * cs;
+    if (p->smem > limit || p->threads > 512 || p->threads % p->cols != 0 || p->cols < 1) {
+      *err = "pass shape does not fit (tile columns, threads or shared memory)";
+      return EQ_ERR_INVALID;
+    }
+  }
+  const int count = g->F;
+  std::vector<long long> pre[3];
+  for (int pi = 0; pi < 3; ++pi) {
+    PassShape* p = ps[pi];
+    int blocks = 0;
+    cudaError_t e = occupancy(g->dtype, pi == 2 ? 2 : 0, p->threads, p->smem, &blocks);
+    if (e == cudaSuccess) e = occupancy(g->dtype, pi == 2 ? 2 : 1, p->threads, p->smem, &blocks);
+    if (e != cudaSuccess || blocks < 1) {
+      cudaGetLastError();
+      *err = std::string("occupancy: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "0 blocks");
+      return EQ_ERR_INVALID;
+    }
+    const long long resident = (long long)g->sms * blocks;
+    long long total_tiles = 0;
+    for (const FieldDesc& fd : g->fh) {
+      if (pi == 2) total_tiles += (fd.npairs + (p->cols / 6) - 1) / (p->cols / 6);
+      else {
+        const long long ncols = pi == 0 ? (long long)fd.nx * fd.ny : (long long)fd.nz * fd.nx;
+        total_tiles += 3 * ((ncols + p->cols - 1) / p->cols);
+      }
+    }
+    p->tpi = (int)std::max(1LL, total_tiles / (8 * resident));
+    pre[pi].assign(count + 1, 0);
+    for (int f = 0; f < count; ++f) {
+      const FieldDesc& fd = g->fh[f];
+      long long items;
+      if (pi == 2) {
+        const long long groups = (fd.npairs + (p->cols / 6) - 1) / (p->cols / 6);
+        items = (groups + p->tpi - 1) / p->tpi;
+      } else {
+        const long long ncols = pi == 0 ? (long long)fd.nx * fd.ny : (long long)fd.nz * fd.nx;
+        const long long ntiles = (ncols + p->cols - 1) / p->cols;
+        items = 3 * ((ntiles + p->tpi - 1) / p->tpi);
+      }
+      pre[pi][f + 1] = pre[pi][f] + items;
+    }
+    p->nitems = pre[pi][count];
+    p->grid = (int)std::max(1LL, std::min(resident, p->nitems));
+  }
+  // work allocation: item prefix sums and per-warp partial records
+  size_t cur = 0;
+  auto take = [&](size_t bytes) { size_t at = cur; cur = align_up(cur + bytes, 256); return at; };
+  const size_t o_iz = take(sizeof(long long) * (count + 1));
+  const size_t o_iy = take(sizeof(long long) * (count + 1));
+  const size_t o_ix = take(sizeof(long long) * (count + 1));
+  const size_t o_pf = take(sizeof(double) * z.nitems * WARPS_MAX * 4);
+  const size_t o_px = take(sizeof(double) * x.nitems * WARPS_MAX * 4);
+  const size_t o_pl = take(sizeof(double) * z.nitems * WARPS_MAX * 4);
+  if (cur > g->wbytes) {
+    void* w = nullptr;
+    cudaError_t e = cudaMalloc(&w, cur);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+      return EQ_ERR_OOM;
+    }
+    if (g->wmem) cudaFree(g->wmem);
+    g->wmem = w;
+    g->wbytes = cur;
+  }
+  unsigned char* b = static_cast<unsigned char*>(g->wmem);
+  z.item0 = reinterpret_cast<long long*>(b + o_iz);
+  y.item0 = reinterpret_cast<long long*>(b + o_iy);
+  x.item0 = reinterpret_cast<long long*>(b + o_ix);
+  cudaError_t e;
+  if ((e = cudaMemcpy(z.item0, pre[0].data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(y.item0, pre[1].data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(x.item0, pre[2].data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    *err = std::string("item tables: ") + cudaGetErrorString(e);
+    return EQ_ERR_CUDA;
+  }
+  g->part_first = reinterpret_cast<double*>(b + o_pf);
+  g->part_x = reinterpret_cast<double*>(b + o_px);
+  g->part_last = reinterpret_cast<double*>(b + o_pl);
+  g->z = z; g->y = y; g->x = x;
+  g->tune = t;
   return EQ_OK;
 }
 
@@ -471,13 +528,159 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
 }
 
 const eq_norms_t* gen_norms_device(const GenPlan* g) { return g->norms; }
-size_t gen_device_bytes(const GenPlan* g) { return g->dbytes; }
+GenTune gen_current_tune(const GenPlan* g) { return g->tune; }
+
+// ---- tuning cache: a JSON object {"key": [zc, zt, yc, yt, xp], ...} in the file $EQ_TUNE_CACHE
+
+namespace {
+
+std::string read_file(const char* path) {
+  std::ifstream f(path);
+  if (!f) return "";
+  std::stringstream ss;
+  ss << f.rdbuf();
+  return ss.str();
+}
+
+// entries of the cache file as (key, values) pairs
+std::vector<std::pair<std::string, std::vector<int>>> parse_cache(const std::string& txt) {
+  std::vector<std::pair<std::string, std::vector<int>>> out;
+  size_t pos = 0;
+  while (true) {
+    const size_t q0 = txt.find('"', pos);
+    if (q0 == std::string::npos) break;
+    const size_t q1 = txt.find('"', q0 + 1);
+    if (q1 == std::string::npos) break;
+    const size_t b0 = txt.find('[', q1);
+    const size_t b1 = txt.find(']', b0 == std::string::npos ? q1 : b0);
+    if (b0 == std::string::npos || b1 == std::string::npos) break;
+    std::vector<int> vals;
+    std::stringstream ss(txt.substr(b0 + 1, b1 - b0 - 1));
+    std::string tok;
+    while (std::getline(ss, tok, ',')) vals.push_back(std::atoi(tok.c_str()));
+    out.emplace_back(txt.substr(q0 + 1, q1 - q0 - 1), vals);
+    pos = b1 + 1;
+  }
+  return out;
+}
+
+void cache_store(const GenPlan* g) {
+  const char* path = getenv("EQ_TUNE_CACHE");
+  if (!path || !*path) return;
+  auto entries = parse_cache(read_file(path));
+  const std::vector<int> v = {g->tune.zc, g->tune.zt, g->tune.yc, g->tune.yt, g->tune.xp};
+  bool found = false;
+  for (auto& e : entries)
+    if (e.first == g->key) { e.second = v; found = true; }
+  if (!found) entries.emplace_back(g->key, v);
+  const std::string tmp = std::string(path) + ".tmp";
+  {
+    std::ofstream f(tmp);
+    f << "{\n";
+    for (size_t i = 0; i < entries.size(); ++i) {
+      f << "  \"" << entries[i].first << "\": [";
+      for (size_t k = 0; k < entries[i].second.size(); ++k) f << (k ? ", " : "") << entries[i].second[k];
+      f << "]" << (i + 1 < entries.size() ? "," : "") << "\n";
+    }
+    f << "}\n";
+  }
+  std::rename(tmp.c_str(), path);
+}
+
+}  // namespace
+
+bool gen_cache_lookup(const GenPlan* g, GenTune* t) {
+  const char* path = getenv("EQ_TUNE_CACHE");
+  if (!path || !*path) return false;
+  for (const auto& e : parse_cache(read_file(path)))
+    if (e.first == g->key && e.second.size() == 5) {
+      t->zc = e.second[0]; t->zt = e.second[1]; t->yc = e.second[2]; t->yt = e.second[3];
+      t->xp = e.second[4];
+      return true;
+    }
+  return false;
+}
+
+// time one pass (z forward, y forward or x) with the current shapes; median of 3 runs, ms
+static float time_pass(GenPlan* g, int which, const void* d_in, void* d_out, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  GenArgs a{};
+  a.fields = g->fields; a.axes = g->axes; a.cpool = g->cpool; a.xipool = g->xipool;
+  a.pairpool = g->pairpool; a.mean = g->mean; a.nfields = g->F;
+  a.nyq_zero = g->opts.nyq == EQ_NYQ_ZERO;
+  const PassShape& p = which == 0 ? g->z : (which == 1 ? g->y : g->x);
+  a.item0 = p.item0; a.nitems = p.nitems; a.tiles_per_item = p.tpi; a.cols = p.cols;
+  a.pitch = p.pitch; a.mmax = p.mmax;
+  a.in = which == 0 ? d_in : d_out;
+  a.out = d_out;
+  a.axis = which == 0 ? 2 : 1;
+  a.mode = which == 0 ? 1 : 0;
+  a.partials = which == 0 ? g->part_first : (which == 2 ? g->part_x : nullptr);
+  const int kind = which == 2 ? 2 : 0;
+  float best[3];
+  for (int r = 0; r < 4; ++r) {
+    cudaEventRecord(e0, s);
+    if (g->dtype == EQ_F32) gen_launch_f32(kind, a, p.grid, p.threads, p.smem, s);
+    else gen_launch_f64(kind, a, p.grid, p.threads, p.smem, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0) best[r - 1] = ms;              // first run warms up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::sort(best, best + 3);
+  return best[1];
+}
+
+eq_status gen_autotune(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s, std::string* err) {
+  GenTune best = g->tune;
+  const bool f32 = g->dtype == EQ_F32;
+  const int cols[4] = {f32 ? 4 : 2, f32 ? 8 : 4, f32 ? 16 : 8, f32 ? 32 : 16};
+  const int threads[3] = {128, 256, 512};
+  for (int which = 0; which < 3; ++which) {
+    float best_ms = 1e30f;
+    GenTune keep = best;
+    std::vector<GenTune> cands;
+    if (which < 2) {
+      for (int c : cols)
+        for (int t : threads) {
+          GenTune u = best;
+          if (which == 0) { u.zc = c; u.zt = t; } else { u.yc = c; u.yt = t; }
+          cands.push_back(u);
+        }
+    } else {
+      for (int xp : {1, 2, 3}) {
+        GenTune u = best;
+        u.xp = xp;
+        cands.push_back(u);
+      }
+    }
+    for (const GenTune& u : cands) {
+      std::string e2;
+      if (gen_configure(g, u, &e2) != EQ_OK) continue;     // shape does not fit: skip
+      const float ms = time_pass(g, which, d_in, d_out, s);
+      if (cudaGetLastError() != cudaSuccess) continue;
+      if (ms < best_ms) { best_ms = ms; keep = u; }
+    }
+    best = keep;
+  }
+  eq_status st = gen_configure(g, best, err);
+  if (st != EQ_OK) return st;
+  cache_store(g);
+  return EQ_OK;
+}
+size_t gen_device_bytes(const GenPlan* g) { return g->dbytes + g->wbytes; }
 long long gen_total_elems(const GenPlan* g) { return g->total_elems; }
 int gen_count(const GenPlan* g) { return g->F; }
 
 void gen_destroy(GenPlan* g) {
   if (!g) return;
   if (g->dmem) cudaFree(g->dmem);
+  if (g->wmem) cudaFree(g->wmem);
   delete g;
 }
 

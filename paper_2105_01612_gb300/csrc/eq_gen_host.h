@@ -16,6 +16,13 @@ cudaError_t gen_launch_f64(int kind, const GenArgs& a, int grid, int threads, si
 
 struct GenPlan;
 
+// Tunable pass shapes of the runtime-length path.
+struct GenTune {
+  int zc = 16, zt = 256;   // z pass: tile columns, threads per block
+  int yc = 16, yt = 256;   // y pass
+  int xp = 2;              // x pass: row pairs per block (6 xp transforms, 32 threads each)
+};
+
 // Largest supported axis length and the rule for it (for error messages).
 bool gen_length_supported(int n);
 
@@ -26,6 +33,13 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
 eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s, cudaEvent_t* ev,
                       std::string* err);
 const eq_norms_t* gen_norms_device(const GenPlan* g);
+GenTune gen_default_tune(const GenPlan* g);
+eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err);
+// Time candidate shapes of each pass on these buffers and keep the fastest (stored in the
+// tuning cache when EQ_TUNE_CACHE names a file).
+eq_status gen_autotune(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s, std::string* err);
+bool gen_cache_lookup(const GenPlan* g, GenTune* t);
+GenTune gen_current_tune(const GenPlan* g);
 size_t gen_device_bytes(const GenPlan* g);
 long long gen_total_elems(const GenPlan* g);   // 6 * sum of voxels
 int gen_count(const GenPlan* g);

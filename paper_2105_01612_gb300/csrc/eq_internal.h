@@ -2,6 +2,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <string>
+
+#include "../../include/eq.h"
 #include "eq_kernels.cuh"
 #include "eq_tma.cuh"
 
@@ -38,5 +41,18 @@ cudaError_t launch_tma_f32(int n, bool inv, const CUtensorMap& map, const TmaArg
                            cudaStream_t s);
 cudaError_t launch_tma_f64(int n, bool inv, const CUtensorMap& map, const TmaArgs& a, dim3 grid,
                            cudaStream_t s);
+// bulk-copy fused x pass: info fails when no instance exists for n
+cudaError_t xtma_info_f32(int n, TmaInfo* out);
+cudaError_t xtma_info_f64(int n, TmaInfo* out);
+cudaError_t launch_xtma_f32(int n, const XTmaArgs& a, dim3 grid, cudaStream_t s);
+cudaError_t launch_xtma_f64(int n, const XTmaArgs& a, dim3 grid, cudaStream_t s);
+
+// Finalisation kernels of the power-of-two path (fixed-order FP64 reductions of block partials).
+void finalize_mean(const double* part, int grid, int batch, double vol, double* mean,
+                   double* instats, cudaStream_t s);
+void finalize_norms(const double* partx, int gridx, const double* partl, int gridl, int batch,
+                    double vol, const double* mean, const double* instats, int linf_flag,
+                    eq_norms_t* out, cudaStream_t s);
+void set_last_error(const std::string& msg);
 
 }  // namespace eqk

@@ -52,6 +52,15 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 template <typename T, int N> struct TmaCfg {
   static constexpr int E = 8;
   static constexpr int TPC = N / E;
@@ -205,6 +214,220 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
   } else if (a.mode == 2 && ref_re) {
     double m = block_max(double(linf), red);
     if (tid == 0) a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = m;
+  }
+}
+
+// ---- fused x pass with bulk-copy double buffering --------------------------------------
+//
+// Same work as k_xproj (forward x transform of P row pairs, projector per mode pair, inverse x
+// transform), but the rows of group g + 2 stream into shared memory with cp.async.bulk (one 1-D
+// copy per row and plane) while the block works on group g.
+
+template <typename T, int N> struct XTmaCfg {
+  static constexpr int E = 8;
+  static constexpr int TPC = N / E;
+  static constexpr int P = (sizeof(T) == 4 && N <= 512) ? 2 : 1;
+  static constexpr int XCOLS = 6 * P;
+  static constexpr int THREADS = XCOLS * TPC;
+  static constexpr int PITCH = N + (N >> 3);
+  using T2 = typename V2<T>::t;
+  static constexpr size_t STAGE_BYTES = 2 * sizeof(T) * size_t(N) * XCOLS;   // re + im rows
+  static constexpr size_t SMEM = 1024 + 2 * STAGE_BYTES + sizeof(T2) * size_t(XCOLS) * PITCH +
+                                 sizeof(T2) * N + sizeof(T) * N;
+  static constexpr bool OK = N >= 64 && THREADS <= 1024 && SMEM <= 227 * 1024;
+};
+
+struct XTmaArgs {
+  void* data;
+  const void* tw;
+  const void* xi_x;
+  const void* xi_y;
+  const void* xi_z;
+  const int* pairs;
+  const double* mean;
+  double* partials;        // [batch][grid][4]
+  int* err;
+  long long field_stride, V;
+  int nx, ny, nz;
+  int npairs, ngroups;
+  int nyq_zero;
+  double inv_v;
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(XTmaCfg<T, N>::THREADS, 1)
+k_xproj_tma(const XTmaArgs a) {
+  using C = XTmaCfg<T, N>;
+  using T2 = typename C::T2;
+  constexpr int E = C::E, TPC = C::TPC, P = C::P, PITCH = C::PITCH, XCOLS = C::XCOLS;
+  extern __shared__ __align__(16) unsigned char smem_xt[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_xt) + 127) & ~uintptr_t(127));
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(base);
+  T* stage0 = reinterpret_cast<T*>(base + 128);
+  T* stage[2] = {stage0, stage0 + 2 * N * XCOLS};
+  T2* buf = reinterpret_cast<T2*>(stage0 + 4 * N * XCOLS);
+  T2* tw = buf + XCOLS * PITCH;
+  T* xix = reinterpret_cast<T*>(tw + N);
+  __shared__ double red[32 * 4];
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x;
+  for (int i = tid; i < N; i += blockDim.x) {
+    tw[i] = reinterpret_cast<const T2*>(a.tw)[i];
+    xix[i] = reinterpret_cast<const T*>(a.xi_x)[i];
+  }
+  if (tid == 0) {
+    abort_flag = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const T* xiy = reinterpret_cast<const T*>(a.xi_y);
+  const T* xiz = reinterpret_cast<const T*>(a.xi_z);
+  const int col = tid / TPC, t = tid % TPC;
+  const int slot = col / 6, side = (col % 6) / 3, comp = col % 3;
+  const int field = blockIdx.y;
+  T* fdata = reinterpret_cast<T*>(a.data) + field * a.field_stride;
+  T* pre = fdata + (2LL * comp) * a.V;
+  T* pim = pre + a.V;
+  const double* mean = a.mean ? a.mean + field * 6 : nullptr;
+  const IdxRow idx{col * PITCH};
+  const T inv_v = T(a.inv_v);
+  const double vol = 1.0 / a.inv_v;
+
+  auto mirror = [&](int r) {
+    const int kz = r / a.ny, ky = r - kz * a.ny;
+    return (kz == 0 ? 0 : a.nz - kz) * a.ny + (ky == 0 ? 0 : a.ny - ky);
+  };
+  int issued[2] = {0, 0};
+  // thread 0: stream the rows of group g into stage s (skipping absent and mirror-of-self rows)
+  auto issue = [&](int g, int s) {
+    unsigned bytes = 0;
+    int rows[2 * P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int p = g * P + q;
+      rows[2 * q] = rows[2 * q + 1] = -1;
+      if (p < a.npairs) {
+        const int rA = a.pairs[p], rB = mirror(rA);
+        rows[2 * q] = rA;
+        rows[2 * q + 1] = rB == rA ? -1 : rB;
+      }
+      bytes += (rows[2 * q] >= 0 ? 6u : 0u) * N * sizeof(T) + (rows[2 * q + 1] >= 0 ? 6u : 0u) * N * sizeof(T);
+    }
+    ++issued[s];
+    mbar_expect_tx(&bar[s], bytes);
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int r = rows[2 * q + sd];
+        if (r < 0) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int pl = 0; pl < 2; ++pl) {
+            const int cc = q * 6 + sd * 3 + c;
+            T* dst = stage[s] + (2 * cc + pl) * N;
+            const T* src = fdata + (2LL * c + pl) * a.V + (long long)r * N;
+            bulk_load(dst, src, N * sizeof(T), &bar[s]);
+          }
+      }
+  };
+  const int first = blockIdx.x, step = gridDim.x;
+  if (tid == 0) {
+    if (first < a.ngroups) issue(first, 0);
+    if (first + step < a.ngroups) issue(first + step, 1);
+  }
+
+  Kahan<T> r2, di2, do2, o2;
+  int k = 0;
+  for (int g = first; g < a.ngroups; g += step, ++k) {
+    const int s = k & 1;
+    if (!mbar_wait(&bar[s], (k >> 1) & 1)) {
+      atomicOr(a.err, 1);
+      abort_flag = 1;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    const int p = g * P + slot;
+    const bool valid = p < a.npairs;
+    int rowA = 0, rowB = 0;
+    if (valid) {
+      rowA = a.pairs[p];
+      rowB = mirror(rowA);
+    }
+    const bool active = valid && !(side == 1 && rowA == rowB);
+    T2 x[E];
+    {
+      const T* sre = stage[s] + (2 * col) * N;
+      const T* sim = sre + N;
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        x[e] = active ? T2{sre[t + TPC * e], sim[t + TPC * e]} : T2{T(0), T(0)};
+    }
+    __syncthreads();                                   // stage s is free again
+    if (tid == 0 && g + 2 * step < a.ngroups) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(g + 2 * step, s);
+    }
+    fft_column<N, E, false>(x, t, buf, idx, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) buf[idx(t + TPC * e)] = x[e];
+    __syncthreads();
+    for (int item = tid; item < P * N; item += blockDim.x) {
+      const int s2 = item / N, kx = item - s2 * N;
+      const int p2 = g * P + s2;
+      if (p2 >= a.npairs) continue;
+      const int rA = a.pairs[p2];
+      const int kz = rA / a.ny, ky = rA - kz * a.ny;
+      const bool self2 = mirror(rA) == rA;
+      const int kxm = kx == 0 ? 0 : N - kx;
+      if (self2 && kx > kxm) continue;
+      const int colA = s2 * 6, colB = self2 ? s2 * 6 : s2 * 6 + 3;
+      T2 av[3], bv[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        av[c] = buf[(colA + c) * PITCH + kx + (kx >> 3)];
+        bv[c] = buf[(colB + c) * PITCH + kxm + (kxm >> 3)];
+      }
+      const bool selfmode = self2 && kx == kxm;
+      project_pair<T>(av, bv, xix[kx], xiy[ky], xiz[kz], rA == 0 && kx == 0, mean, vol,
+                      a.nyq_zero != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        buf[(colA + c) * PITCH + kx + (kx >> 3)] = av[c];
+        if (!selfmode) buf[(colB + c) * PITCH + kxm + (kxm >> 3)] = bv[c];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = buf[idx(t + TPC * e)];
+    __syncthreads();
+    fft_column<N, E, true>(x, t, buf, idx, tw);
+    if (active) {
+      const long long roff = (long long)(side == 0 ? rowA : rowB) * N;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        pre[roff + t + TPC * e] = x[e].x;
+        pim[roff + t + TPC * e] = x[e].y;
+      }
+    }
+  }
+  if (abort_flag) {
+    if (tid == 0)
+      for (int s = 0; s < 2; ++s)
+        if (issued[s] > 0) mbar_wait(&bar[s], (unsigned)((issued[s] - 1) & 1));
+    __syncthreads();
+    return;
+  }
+  double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
+  block_sum<4>(v, red);
+  if (tid == 0) {
+    double* q = a.partials + ((long long)field * gridDim.x + blockIdx.x) * 4;
+    q[0] = v[0]; q[1] = v[1]; q[2] = v[2]; q[3] = v[3];
   }
 }
 

@@ -101,3 +101,33 @@ def test_batch_of_64_uneven_fields_config_sizes_sampled():
         assert abs(n["norm_in"] ** 2 - n["norm_out"] ** 2 - n["resid_l2"] ** 2) <= 1e-5 * n["norm_in"] ** 2
         assert n["div_out_l2"] <= 1e-5 * n["div_in_l2"]
     plan.close()
+
+
+def test_autotune_keeps_results_and_writes_the_cache(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("EQ_TUNE_CACHE", str(cache))
+    dims = [(24, 20, 18), (33, 16, 40), (64, 12, 10)]
+    fields, ref_outs, _ = _varlen_run(dims, torch.float32, 6000)
+    plan = eq.VarlenPlan(dims, torch.float32, "ddo")
+    flat = plan.pack([torch.as_tensor(f) for f in fields])
+    out = torch.empty_like(flat)
+    plan.autotune(flat, out)
+    plan.project(flat, out)
+    for o, r in zip(plan.unpack(out), ref_outs):
+        assert rel(o.double().cpu().numpy(), r) <= 2e-6
+    plan.close()
+    txt = cache.read_text()
+    assert txt.strip().startswith("{") and "gen|f32" in txt
+    # a new plan with the same key starts from the cached shapes and still matches
+    _, again, _ = _varlen_run(dims, torch.float32, 6000)
+    for a, r in zip(again, ref_outs):
+        assert rel(a, r) <= 2e-6
+    # power-of-two plan: TMA / plain choice per pass
+    s = voronoi_stress_field((64, 64, 64), 9, 100.0, 5.0, 61).numpy()
+    x = torch.as_tensor(s).float().cuda().unsqueeze(0)
+    p2 = eq.Plan(64, 64, 64, torch.float32)
+    y = torch.empty_like(x)
+    p2.autotune(x, y)
+    p2.project(x, y)
+    assert rel(y[0].double().cpu().numpy(), oracle.project(x[0].double().cpu().numpy(), "ddo")) <= 2e-6
+    p2.close()

@@ -169,9 +169,9 @@ def test_batch_inplace_and_host_entry():
     plan.close()
 
 
-def test_tma_and_plain_strided_passes_agree_bitwise(monkeypatch):
-    """The TMA-fed strided passes compute exactly what the plain-load passes compute."""
-    s = field((64, 128, 32), 9, 100.0, 10.0, 55)
+def test_tma_and_plain_passes_agree(monkeypatch):
+    """The TMA / bulk-copy fed passes compute what the plain-load passes compute."""
+    s = field((64, 128, 64), 9, 100.0, 10.0, 55)
     outs = []
     for flag in ("0", "1"):
         monkeypatch.setenv("EQ_NO_TMA", flag)
@@ -181,8 +181,14 @@ def test_tma_and_plain_strided_passes_agree_bitwise(monkeypatch):
     for dtype in (torch.float32, torch.float64):
         a = [o for d, o, _ in outs if d == dtype]
         b = [n for d, _, n in outs if d == dtype]
-        assert np.array_equal(a[0], a[1])
-        assert b[0] == b[1]
+        # identical transforms; only the FP64 mean substituted at k = 0 can differ in its last
+        # bit, because the two first passes reduce it over different block grids
+        assert rel(a[0], a[1]) <= 4 * EPS[dtype]
+        # the two paths split the FP64 reductions over different block grids
+        # (FP32 partials are Kahan-compensated FP32 sums, FP64 ones plain FP64 sums)
+        tol = 1e-7 if dtype == torch.float32 else 1e-12
+        for k in ("norm_in", "norm_out", "resid_l2", "resid_linf", "div_in_l2"):
+            assert b[0][0][k] == pytest.approx(b[1][0][k], rel=tol), k
 
 
 def test_deterministic_and_nonfinite_flag():
