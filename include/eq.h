@@ -142,6 +142,25 @@ eq_status eq_plan_set_timing(eq_plan* plan, int max_calls);
  * them (ms_out: EQ_NUM_PASSES entries) and their number; then reset the counters. */
 eq_status eq_plan_pass_ms(eq_plan* plan, double* ms_out, int* ncalls_out);
 
+/* ---- projection without any allocation ------------------------------------------------
+ * For callers that cannot allocate device memory when they project: code that runs under a
+ * fixed memory budget or a caller-owned allocator, or a loop in which CUDA allocation calls are
+ * not allowed.  The paper has no counterpart; this is a library facility.
+ * One FP32 field, power-of-two axis lengths 1..EQ_STATIC_MAX_N.  The caller passes d_in, d_out
+ * (6 nx ny nz floats each; equal or disjoint) and optionally d_norms (device memory for one
+ * eq_norms_t; NULL = do not report).  Tables and reduction partials live in a fixed
+ * EQ_STATIC_SCRATCH_BYTES array in device memory that the library declares; every GPU that loads
+ * the library holds it until the process exits.  The call makes no cudaMalloc/cudaFree and calls
+ * no allocating library routine; it enqueues work on cuda_stream and returns.  The first call on
+ * each device (with that device current) looks up the array's device address; make that first
+ * call before any stream capture.  All calls share the array: calls whose work overlaps on the
+ * GPU race on it, so order them (one stream, or synchronise).  Grids whose scratch would not fit
+ * are rejected with EQ_ERR_INVALID.  Results equal eq_project's for the same field. */
+#define EQ_STATIC_SCRATCH_BYTES (1u << 20)
+#define EQ_STATIC_MAX_N 512
+eq_status eq_project_static(int nx, int ny, int nz, const eq_plan_opts* opts, const float* d_in,
+                            float* d_out, eq_norms_t* d_norms, void* cuda_stream);
+
 /* ---- serving ------------------------------------------------------------------------
  * A request loop for single fields arriving over time.  A scheduler thread admits queued
  * requests in arrival order as soon as one of `max_inflight` slots (CUDA streams) is free and the

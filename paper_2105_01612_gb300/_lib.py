@@ -55,6 +55,8 @@ SIGNATURES = [
     ("eq_plan_set_timing", c_int, [c_void_p, c_int]),
     ("eq_plan_pass_ms", c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
     ("eq_plan_destroy", None, [c_void_p]),
+    ("eq_project_static", c_int, [c_int, c_int, c_int, ctypes.POINTER(EqPlanOpts), c_void_p,
+                                  c_void_p, c_void_p, c_void_p]),
     ("eq_server_create", c_int, [c_size_t, c_int, ctypes.POINTER(c_void_p)]),
     ("eq_serve_submit", c_int, [c_void_p, c_int, c_int, c_int, c_int, ctypes.POINTER(EqPlanOpts),
                                 c_void_p, c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]),
