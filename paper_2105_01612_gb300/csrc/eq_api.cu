@@ -120,6 +120,7 @@ struct eq_plan {
   size_t dbytes = 0;
   void* tw[3] = {nullptr, nullptr, nullptr};   // x, y, z twiddles
   void* xi[3] = {nullptr, nullptr, nullptr};   // x, y, z operator symbols
+  void* twst = nullptr;                        // per-stage x twiddles (cos table, sin table)
   int* pairs = nullptr;
   int npairs = 0;
   double* part1 = nullptr;     // [batch][3][g1][4]
@@ -132,9 +133,11 @@ struct eq_plan {
   eqk::PassInfo info_z_f, info_y_f, info_x, info_y_i, info_z_i;
   // TMA-fed strided passes (used when an instance exists and the x extent tiles evenly)
   eqk::TmaInfo tz, ty, tx;
+  bool tma_allow = false;
   bool tma_z = false, tma_y = false, tma_x = false;
   bool avail_z = false, avail_y = false, avail_x = false;   // instances exist for these sizes
-  int gtz = 1, gty = 1, gtx = 1;
+  int vz = 0, vy = 0, vx = 0;                               // shape variants in use
+  int gtz = 1, gty = 1, gtx = 1, gtz_max = 1, gtx_max = 1;
   int* err = nullptr;          // raised by a kernel whose bounded wait ran out
   cudaEvent_t done = nullptr;
   bool have_result = false;
@@ -184,6 +187,32 @@ template <typename T> void fill_tables(int n, double h, eq_op op, std::vector<un
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Per-stage twiddles W_{Ns R}^{r k} (k < Ns, r = 1..R-1) of the power-of-two schedule of
+// length n, stages with Ns > 1 in order, as a cos table followed by a sin table.
+template <typename T> void staged_twiddles(int n, std::vector<unsigned char>& out) {
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<double> c, sn;
+  int ns = 1, st = 0;
+  while (ns < n) {
+    const int R = eqk::stage_radix(n, st);
+    if (ns > 1)
+      for (int k = 0; k < ns; ++k)
+        for (int r = 1; r < R; ++r) {
+          const double ang = -two_pi * double(r * k) / double(ns * R);
+          c.push_back(std::cos(ang));
+          sn.push_back(std::sin(ang));
+        }
+    ns *= R;
+    ++st;
+  }
+  out.resize(sizeof(T) * 2 * std::max<size_t>(1, c.size()));
+  T* o = reinterpret_cast<T*>(out.data());
+  for (size_t i = 0; i < c.size(); ++i) {
+    o[i] = T(c[i]);
+    o[c.size() + i] = T(sn[i]);
+  }
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -219,6 +248,34 @@ bool make_map(CUtensorMap* m, const void* base, const eq_plan* p, int axis, int 
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Select shape variants for the TMA / bulk-copy passes and compute their grids (occupancy x SMs,
+// split over fields and components, capped by the work).
+void tma_setup(eq_plan* p, int vz, int vy, int vx) {
+  p->vz = vz; p->vy = vy; p->vx = vx;
+  p->tma_z = p->tma_y = p->tma_x = false;
+  if (p->tma_allow) {
+    const bool f32 = p->dtype == EQ_F32;
+    cudaError_t te = f32 ? eqk::tma_info_f32(p->nz, vz, &p->tz) : eqk::tma_info_f64(p->nz, vz, &p->tz);
+    p->tma_z = te == cudaSuccess && p->tz.cols > 0 && p->nx % p->tz.cols == 0 && p->tz.blocks_per_sm > 0;
+    te = f32 ? eqk::tma_info_f32(p->ny, vy, &p->ty) : eqk::tma_info_f64(p->ny, vy, &p->ty);
+    p->tma_y = te == cudaSuccess && p->ty.cols > 0 && p->nx % p->ty.cols == 0 && p->ty.blocks_per_sm > 0;
+    te = f32 ? eqk::xtma_info_f32(p->nx, vx, &p->tx) : eqk::xtma_info_f64(p->nx, vx, &p->tx);
+    p->tma_x = te == cudaSuccess && p->tx.blocks_per_sm > 0;
+    cudaGetLastError();
+  }
+  const long long b3 = 3LL * p->batch;
+  p->gtz = p->tma_z ? (int)std::max(1LL, std::min<long long>((long long)p->sms * p->tz.blocks_per_sm / b3,
+                                                             (long long)p->ny * (p->nx / p->tz.cols)))
+                    : 1;
+  p->gty = p->tma_y ? (int)std::max(1LL, std::min<long long>((long long)p->sms * p->ty.blocks_per_sm / b3,
+                                                             (long long)p->nz * (p->nx / p->ty.cols)))
+                    : 1;
+  p->gtx = p->tma_x ? (int)std::max(1LL, std::min<long long>((long long)p->sms * p->tx.blocks_per_sm / p->batch,
+                                                             (p->npairs + p->tx.cols - 1) / p->tx.cols))
+                    : 1;
+  p->avail_z = p->tma_z; p->avail_y = p->tma_y; p->avail_x = p->tma_x;
+}
+
 // Strided pass along `axis` through the TMA kernel; false if not applicable for these buffers.
 bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src, void* dst,
              const void* ref, double* partials, cudaStream_t s, cudaError_t* e) {
@@ -237,8 +294,9 @@ bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src,
   t.ntiles = (axis == 2 ? (long long)p->ny : (long long)p->nz) * (p->nx / ti.cols);
   dim3 grid(axis == 2 ? p->gtz : p->gty, p->batch * 3);
   const int n = axis == 2 ? p->nz : p->ny;
-  *e = p->dtype == EQ_F32 ? eqk::launch_tma_f32(n, inv, map, t, grid, s)
-                          : eqk::launch_tma_f64(n, inv, map, t, grid, s);
+  const int v = axis == 2 ? p->vz : p->vy;
+  *e = p->dtype == EQ_F32 ? eqk::launch_tma_f32(n, v, inv, map, t, grid, s)
+                          : eqk::launch_tma_f64(n, v, inv, map, t, grid, s);
   return true;
 }
 
@@ -308,7 +366,7 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
   const int gx_used = on_x ? p->gtx : p->gx;
   if (on_x) {
     eqk::XTmaArgs x{};
-    x.data = d_out; x.tw = p->tw[0];
+    x.data = d_out; x.tws = p->twst;
     x.xi_x = p->xi[0]; x.xi_y = p->xi[1]; x.xi_z = p->xi[2];
     x.pairs = p->pairs; x.mean = p->mean; x.partials = p->partx; x.err = p->err;
     x.field_stride = fstride; x.V = V;
@@ -318,7 +376,7 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     x.nyq_zero = p->opts.nyq == EQ_NYQ_ZERO;
     x.inv_v = 1.0 / double(V);
     dim3 grid(p->gtx, p->batch);
-    e = f32 ? eqk::launch_xtma_f32(p->nx, x, grid, s) : eqk::launch_xtma_f64(p->nx, x, grid, s);
+    e = f32 ? eqk::launch_xtma_f32(p->nx, p->vx, x, grid, s) : eqk::launch_xtma_f64(p->nx, p->vx, x, grid, s);
     if (e != cudaSuccess) return fail_cuda(e, "x projection pass");
   } else {
     eqk::XArgs x{};
@@ -540,29 +598,23 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
     p->gy = grid_for(p->info_y_f, ty, batch * 3);
     p->gx = grid_for(p->info_x, gxn, batch);
     p->gl = grid_for(p->info_z_i, tz, batch * 3);
-    // TMA path: one block per SM split over (field, component); needs whole x tiles
+    // TMA / bulk-copy passes: shape variant 0 (wide tiles) unless overridden; grids sized for
+    // both variants so that the autotuner can switch between them later
     const char* no_tma = getenv("EQ_NO_TMA");
-    const bool allow = !(no_tma && no_tma[0] == '1') && encode_fn() != nullptr &&
-                       ((size_t)nx * p->esize) % 16 == 0;
-    cudaError_t te;
-    if (allow) {
-      te = dtype == EQ_F32 ? eqk::tma_info_f32(nz, &p->tz) : eqk::tma_info_f64(nz, &p->tz);
-      p->tma_z = te == cudaSuccess && nx % p->tz.cols == 0;
-      te = dtype == EQ_F32 ? eqk::tma_info_f32(ny, &p->ty) : eqk::tma_info_f64(ny, &p->ty);
-      p->tma_y = te == cudaSuccess && nx % p->ty.cols == 0;
-      cudaGetLastError();
+    p->tma_allow = !(no_tma && no_tma[0] == '1') && encode_fn() != nullptr &&
+                   ((size_t)nx * p->esize) % 16 == 0;
+    int gmax_z = 1, gmax_x = 1;
+    for (int v = 1; v >= 0; --v) {
+      tma_setup(p, v, v, v);
+      gmax_z = std::max(gmax_z, std::max(p->gtz, p->gty));
+      gmax_x = std::max(gmax_x, p->gtx);
     }
-    if (allow) {
-      te = dtype == EQ_F32 ? eqk::xtma_info_f32(nx, &p->tx) : eqk::xtma_info_f64(nx, &p->tx);
-      p->tma_x = te == cudaSuccess;
-      cudaGetLastError();
-    }
-    p->gtx = (int)std::max(1LL, std::min<long long>(std::max(1, p->sms / batch),
-                                                    p->tma_x ? (p->npairs + p->tx.cols - 1) / p->tx.cols : 1));
-    p->avail_z = p->tma_z; p->avail_y = p->tma_y; p->avail_x = p->tma_x;
-    const long long per = std::max(1, p->sms / (batch * 3));
-    p->gtz = (int)std::min<long long>(per, (long long)ny * (p->tma_z ? nx / p->tz.cols : 1));
-    p->gty = (int)std::min<long long>(per, (long long)nz * (p->tma_y ? nx / p->ty.cols : 1));
+    const char* vs = getenv("EQ_TMA_VARIANT");
+    const char* vxs = getenv("EQ_X_VARIANT");
+    const int v0 = (vs && vs[0] == '1') ? 1 : 0, vx0 = (vxs && vxs[0] == '1') ? 1 : 0;
+    tma_setup(p, v0, v0, vx0);
+    p->gtz_max = gmax_z;
+    p->gtx_max = gmax_x;
   }
   // tables
   std::vector<unsigned char> tw[3], xi[3];
@@ -572,14 +624,18 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
     if (dtype == EQ_F32) fill_tables<float>(lens[a], hs[a], o.op, tw[a], xi[a]);
     else fill_tables<double>(lens[a], hs[a], o.op, tw[a], xi[a]);
   }
+  std::vector<unsigned char> twst;
+  if (dtype == EQ_F32) staged_twiddles<float>(nx, twst);
+  else staged_twiddles<double>(nx, twst);
   size_t off = 0;
   size_t o_tw[3], o_xi[3];
+  const size_t o_twst = off; off = align_up(off + twst.size(), 256);
   for (int a = 0; a < 3; ++a) { o_tw[a] = off; off = align_up(off + tw[a].size(), 256); }
   for (int a = 0; a < 3; ++a) { o_xi[a] = off; off = align_up(off + xi[a].size(), 256); }
   const size_t o_pairs = off; off = align_up(off + sizeof(int) * pairs.size(), 256);
-  const size_t o_p1 = off; off = align_up(off + sizeof(double) * batch * 3 * std::max(p->g1, p->gtz) * 4, 256);
-  const size_t o_px = off; off = align_up(off + sizeof(double) * batch * std::max(p->gx, p->gtx) * 4, 256);
-  const size_t o_pl = off; off = align_up(off + sizeof(double) * batch * 3 * std::max(p->gl, p->gtz), 256);
+  const size_t o_p1 = off; off = align_up(off + sizeof(double) * batch * 3 * std::max(p->g1, p->gtz_max) * 4, 256);
+  const size_t o_px = off; off = align_up(off + sizeof(double) * batch * std::max(p->gx, p->gtx_max) * 4, 256);
+  const size_t o_pl = off; off = align_up(off + sizeof(double) * batch * 3 * std::max(p->gl, p->gtz_max), 256);
   const size_t o_err = off; off = align_up(off + sizeof(int), 256);
   const size_t o_mean = off; off = align_up(off + sizeof(double) * batch * 6, 256);
   const size_t o_is = off; off = align_up(off + sizeof(double) * batch * 2, 256);
@@ -599,6 +655,11 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
       release(p);
       return fail_cuda(e, "table upload");
     }
+  }
+  p->twst = base + o_twst;
+  if ((e = cudaMemcpy(p->twst, twst.data(), twst.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    release(p);
+    return fail_cuda(e, "twiddle upload");
   }
   p->pairs = reinterpret_cast<int*>(base + o_pairs);
   p->part1 = reinterpret_cast<double*>(base + o_p1);
@@ -746,19 +807,21 @@ eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stre
     if (st != EQ_OK) return fail(st, "eq_plan_autotune: " + err);
     return EQ_OK;
   }
-  // power-of-two plans: per pass, keep the faster of the TMA / bulk-copy fed and the plain
-  // variant (measured with events between the passes, second of two runs)
+  // power-of-two plans: per pass, keep the fastest of the wide-tile TMA / bulk-copy variant, the
+  // narrow-tile variant and the plain-load kernels (events between the passes, second of two runs)
   cudaEvent_t ev[EQ_NUM_PASSES + 1];
   for (auto& x : ev)
     if ((e = cudaEventCreate(&x)) != cudaSuccess) return fail_cuda(e, "eq_plan_autotune: events");
-  float ms[2][EQ_NUM_PASSES] = {};
+  float ms[3][EQ_NUM_PASSES] = {};
+  bool ok[3][3] = {};                                   // [config][axis z, y, x] available
   const int saved_cap = p->tcap, saved_used = p->tused;
-  for (int variant = 0; variant < 2; ++variant) {
-    p->tma_z = variant == 0 && p->avail_z;
-    p->tma_y = variant == 0 && p->avail_y;
-    p->tma_x = variant == 0 && p->avail_x;
+  for (int cfg = 0; cfg < 3; ++cfg) {
+    tma_setup(p, cfg == 1, cfg == 1, cfg == 1);
+    if (cfg == 2) p->tma_z = p->tma_y = p->tma_x = false;
+    ok[cfg][0] = cfg == 2 || p->tma_z;
+    ok[cfg][1] = cfg == 2 || p->tma_y;
+    ok[cfg][2] = cfg == 2 || p->tma_x;
     for (int rep = 0; rep < 2; ++rep) {
-      // enqueue with this call's own events
       std::vector<cudaEvent_t> keep(p->tev);
       p->tev.assign(ev, ev + EQ_NUM_PASSES + 1);
       p->tcap = 1; p->tused = 0;
@@ -766,15 +829,25 @@ eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stre
       p->tev.swap(keep);
       if (st != EQ_OK) { p->tcap = saved_cap; p->tused = saved_used; return st; }
       cudaEventSynchronize(ev[EQ_NUM_PASSES]);
-      for (int i = 0; i < EQ_NUM_PASSES; ++i) cudaEventElapsedTime(&ms[variant][i], ev[i], ev[i + 1]);
+      for (int i = 0; i < EQ_NUM_PASSES; ++i) cudaEventElapsedTime(&ms[cfg][i], ev[i], ev[i + 1]);
     }
   }
   p->tcap = saved_cap; p->tused = saved_used;
   for (auto& x : ev) cudaEventDestroy(x);
   // pass indices: 0 z forward, 2 y forward, 3 x, 4 y inverse, 5 z inverse
-  p->tma_z = p->avail_z && ms[0][0] + ms[0][5] <= ms[1][0] + ms[1][5];
-  p->tma_y = p->avail_y && ms[0][2] + ms[0][4] <= ms[1][2] + ms[1][4];
-  p->tma_x = p->avail_x && ms[0][3] <= ms[1][3];
+  auto pick = [&](int axis, float (*cost)(const float*)) {
+    int best = 2;
+    for (int c = 0; c < 2; ++c)
+      if (ok[c][axis] && cost(ms[c]) < cost(ms[best])) best = c;
+    return best;
+  };
+  const int bz = pick(0, [](const float* m) { return m[0] + m[5]; });
+  const int by = pick(1, [](const float* m) { return m[2] + m[4]; });
+  const int bx = pick(2, [](const float* m) { return m[3]; });
+  tma_setup(p, bz == 1, by == 1, bx == 1);
+  if (bz == 2) p->tma_z = false;
+  if (by == 2) p->tma_y = false;
+  if (bx == 2) p->tma_x = false;
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "eq_plan_autotune");
   return EQ_OK;
 }

@@ -37,9 +37,9 @@ template <typename T, int N> struct Inst {
   }
 };
 
-template <typename T, int N> struct TmaInst {
+template <typename T, int N, int V> struct TmaInst {
   static cudaError_t info(TmaInfo* out) {
-    using C = TmaCfg<T, N>;
+    using C = TmaCfg<T, N, V>;
     if constexpr (!C::OK) {
       return cudaErrorInvalidValue;
     } else {
@@ -47,30 +47,38 @@ template <typename T, int N> struct TmaInst {
       out->cols = C::B;
       out->box = C::BOX;
       out->smem = C::SMEM;
-      cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_strided_tma<T, N, false>),
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_strided_tma<T, N, true>),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      const void* fns[4] = {reinterpret_cast<const void*>(&k_strided_tma<T, N, false, 1, V>),
+                            reinterpret_cast<const void*>(&k_strided_tma<T, N, false, 0, V>),
+                            reinterpret_cast<const void*>(&k_strided_tma<T, N, true, 0, V>),
+                            reinterpret_cast<const void*>(&k_strided_tma<T, N, true, 2, V>)};
+      cudaError_t e = cudaSuccess;
+      for (const void* f : fns)
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      int bl = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, fns[0], C::THREADS, C::SMEM);
+      out->blocks_per_sm = bl;
       return e;
     }
   }
   static cudaError_t launch(bool inv, const CUtensorMap& map, const TmaArgs& a, dim3 grid,
                             cudaStream_t s) {
-    using C = TmaCfg<T, N>;
+    using C = TmaCfg<T, N, V>;
     if constexpr (!C::OK) {
       return cudaErrorInvalidValue;
     } else {
-      if (inv) k_strided_tma<T, N, true><<<grid, C::THREADS, C::SMEM, s>>>(map, a);
-      else k_strided_tma<T, N, false><<<grid, C::THREADS, C::SMEM, s>>>(map, a);
+      if (!inv && a.mode == 1) k_strided_tma<T, N, false, 1, V><<<grid, C::THREADS, C::SMEM, s>>>(map, a);
+      else if (!inv) k_strided_tma<T, N, false, 0, V><<<grid, C::THREADS, C::SMEM, s>>>(map, a);
+      else if (a.mode == 2) k_strided_tma<T, N, true, 2, V><<<grid, C::THREADS, C::SMEM, s>>>(map, a);
+      else k_strided_tma<T, N, true, 0, V><<<grid, C::THREADS, C::SMEM, s>>>(map, a);
       return cudaGetLastError();
     }
   }
 };
 
-template <typename T, int N> struct XTmaInst {
+template <typename T, int N, int V> struct XTmaInst {
   static cudaError_t info(TmaInfo* out) {
-    using C = XTmaCfg<T, N>;
+    using C = XTmaCfg<T, N, V>;
     if constexpr (!C::OK) {
       return cudaErrorInvalidValue;
     } else {
@@ -78,16 +86,20 @@ template <typename T, int N> struct XTmaInst {
       out->cols = C::P;
       out->box = 0;
       out->smem = C::SMEM;
-      return cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_xproj_tma<T, N>),
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      const void* f = reinterpret_cast<const void*>(&k_xproj_tma<T, N, V>);
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      int bl = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, f, C::THREADS, C::SMEM);
+      out->blocks_per_sm = bl;
+      return e;
     }
   }
   static cudaError_t launch(const XTmaArgs& a, dim3 grid, cudaStream_t s) {
-    using C = XTmaCfg<T, N>;
+    using C = XTmaCfg<T, N, V>;
     if constexpr (!C::OK) {
       return cudaErrorInvalidValue;
     } else {
-      k_xproj_tma<T, N><<<grid, C::THREADS, C::SMEM, s>>>(a);
+      k_xproj_tma<T, N, V><<<grid, C::THREADS, C::SMEM, s>>>(a);
       return cudaGetLastError();
     }
   }
@@ -121,36 +133,37 @@ template <typename T> cudaError_t xproj_t(int n, const XArgs& a, dim3 grid, cuda
   }
 }
 
-template <typename T> cudaError_t tma_info_t(int n, TmaInfo* out) {
+template <typename T> cudaError_t tma_info_t(int n, int v, TmaInfo* out) {
   switch (n) {
-#define EQ_CASE(N) case N: return TmaInst<T, N>::info(out);
+#define EQ_CASE(N) case N: return v ? TmaInst<T, N, 1>::info(out) : TmaInst<T, N, 0>::info(out);
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;
   }
 }
 template <typename T>
-cudaError_t tma_launch_t(int n, bool inv, const CUtensorMap& map, const TmaArgs& a, dim3 grid,
+cudaError_t tma_launch_t(int n, int v, bool inv, const CUtensorMap& map, const TmaArgs& a, dim3 grid,
                          cudaStream_t s) {
   switch (n) {
-#define EQ_CASE(N) case N: return TmaInst<T, N>::launch(inv, map, a, grid, s);
+#define EQ_CASE(N) \
+  case N: return v ? TmaInst<T, N, 1>::launch(inv, map, a, grid, s) : TmaInst<T, N, 0>::launch(inv, map, a, grid, s);
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename T> cudaError_t xtma_info_t(int n, TmaInfo* out) {
+template <typename T> cudaError_t xtma_info_t(int n, int v, TmaInfo* out) {
   switch (n) {
-#define EQ_CASE(N) case N: return XTmaInst<T, N>::info(out);
+#define EQ_CASE(N) case N: return v ? XTmaInst<T, N, 1>::info(out) : XTmaInst<T, N, 0>::info(out);
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;
   }
 }
-template <typename T> cudaError_t xtma_launch_t(int n, const XTmaArgs& a, dim3 grid, cudaStream_t s) {
+template <typename T> cudaError_t xtma_launch_t(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s) {
   switch (n) {
-#define EQ_CASE(N) case N: return XTmaInst<T, N>::launch(a, grid, s);
+#define EQ_CASE(N) case N: return v ? XTmaInst<T, N, 1>::launch(a, grid, s) : XTmaInst<T, N, 0>::launch(a, grid, s);
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;

@@ -9,13 +9,13 @@ cudaError_t launch_strided_f64(int n, bool inv, const StridedArgs& a, dim3 grid,
 cudaError_t launch_xproj_f64(int n, const XArgs& a, dim3 grid, cudaStream_t s) {
   return xproj_t<double>(n, a, grid, s);
 }
-cudaError_t tma_info_f64(int n, TmaInfo* out) { return tma_info_t<double>(n, out); }
-cudaError_t launch_tma_f64(int n, bool inv, const CUtensorMap& map, const TmaArgs& a, dim3 grid,
+cudaError_t tma_info_f64(int n, int v, TmaInfo* out) { return tma_info_t<double>(n, v, out); }
+cudaError_t launch_tma_f64(int n, int v, bool inv, const CUtensorMap& map, const TmaArgs& a, dim3 grid,
                            cudaStream_t s) {
-  return tma_launch_t<double>(n, inv, map, a, grid, s);
+  return tma_launch_t<double>(n, v, inv, map, a, grid, s);
 }
-cudaError_t xtma_info_f64(int n, TmaInfo* out) { return xtma_info_t<double>(n, out); }
-cudaError_t launch_xtma_f64(int n, const XTmaArgs& a, dim3 grid, cudaStream_t s) {
-  return xtma_launch_t<double>(n, a, grid, s);
+cudaError_t xtma_info_f64(int n, int v, TmaInfo* out) { return xtma_info_t<double>(n, v, out); }
+cudaError_t launch_xtma_f64(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s) {
+  return xtma_launch_t<double>(n, v, a, grid, s);
 }
 }  // namespace eqk

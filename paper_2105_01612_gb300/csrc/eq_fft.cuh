@@ -94,9 +94,45 @@ __host__ __device__ constexpr int stage_span(int N, int s) {  // Ns before stage
   return ns;
 }
 
+// Per-stage twiddle tables: offset of the table of the stage with span NS (stages with NS > 1
+// hold NS (R - 1) entries) and their total size.
+__host__ __device__ constexpr int staged_offset(int N, int NS) {
+  int off = 0, ns = 1, s = 0;
+  while (ns < NS) {
+    const int R = stage_radix(N, s);
+    if (ns > 1) off += ns * (R - 1);
+    ns *= R;
+    ++s;
+  }
+  return off;
+}
+__host__ __device__ constexpr int staged_size(int N) { return staged_offset(N, N); }
+
+// Twiddle sources of a stage: the plain table tw[m] = W_N^m (any layout), or per-stage tables
+// laid out [k][r - 1] for k < Ns (consecutive k are consecutive threads in the x pass, so a warp
+// reads consecutive words: no shared-memory bank conflicts), split into cos and sin arrays.
+template <typename T2> struct TwPlain {
+  const T2* tw;
+  template <int N, int NS, int R>
+  __device__ __forceinline__ T2 get(int k, int r) const { return tw[(r * k) * (N / (NS * R))]; }
+};
+template <typename T> struct TwStaged {
+  const T* c;   // cos, all stages back to back
+  const T* s;   // sin
+  // offset of stage table with span NS: sum of NS' (R' - 1) over earlier stages
+  template <int N, int NS, int R>
+  __device__ __forceinline__ typename V2<T>::t get(int k, int r) const {
+    constexpr int off = staged_offset(N, NS);
+    const int i = off + k * (R - 1) + (r - 1);
+    return {c[i], s[i]};
+  }
+};
+
+
+
 // One Stockham stage on the thread's registers; leaves outputs in the same slots.
-template <int N, int E, int S, bool INV, typename T2>
-__device__ __forceinline__ void fft_stage(T2 (&x)[E], int t, const T2* __restrict__ tw) {
+template <int N, int E, int S, bool INV, typename T2, typename TW>
+__device__ __forceinline__ void fft_stage(T2 (&x)[E], int t, const TW& tw) {
   constexpr int R = stage_radix(N, S);
   constexpr int NS = stage_span(N, S);
   constexpr int TPC = N / E;
@@ -110,7 +146,7 @@ __device__ __forceinline__ void fft_stage(T2 (&x)[E], int t, const T2* __restric
       const int k = (t + TPC * q) & (NS - 1);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        T2 w = tw[(r * k) * (N / (NS * R))];
+        T2 w = tw.template get<N, NS, R>(k, r);
         if (INV) w.y = -w.y;
         v[r] = cmul(v[r], w);
       }
@@ -131,12 +167,36 @@ __device__ __forceinline__ int stage_out_pos(int t, int q, int r) {
   return (j / NS) * NS * R + (j & (NS - 1)) + r * NS;
 }
 
-// Full transform of one column.  `idx(i)` maps element index i to the column's shared-memory
-// slot.  All threads of the block must call this together (it synchronises the block).  On
-// entry the caller guarantees the block is done reading `buf` from any earlier use.
-template <int N, int E, bool INV, int S = 0, typename T2, typename IDX>
-__device__ __forceinline__ void fft_column(T2 (&x)[E], int t, T2* buf, const IDX& idx,
-                                           const T2* __restrict__ tw) {
+// Exchange storage between stages: interleaved complex through an index map, or split real and
+// imaginary arrays with a bank swizzle (for the x pass, whose warps run along one transform).
+template <typename T2, typename IDX> struct AosAcc {
+  T2* buf;
+  IDX idx;
+  __device__ __forceinline__ void put(int i, T2 v) const { buf[idx(i)] = v; }
+  __device__ __forceinline__ T2 get(int i) const { return buf[idx(i)]; }
+};
+// Split real/imaginary rows of N words, element i stored at swz(i): an XOR of the low five bits
+// with bits 5..7 of i, so the contiguous, stage-output and projector access patterns of a warp
+// (32 consecutive threads of one transform) touch 32 distinct banks.
+__host__ __device__ __forceinline__ int swz(int i) { return i ^ ((i >> 5) & 7) ^ (((i >> 6) & 3) << 3); }
+template <typename T> struct SoaAcc {
+  T* re;
+  T* im;
+  __device__ __forceinline__ void put(int i, typename V2<T>::t v) const {
+    const int j = swz(i);
+    re[j] = v.x;
+    im[j] = v.y;
+  }
+  __device__ __forceinline__ typename V2<T>::t get(int i) const {
+    const int j = swz(i);
+    return {re[j], im[j]};
+  }
+};
+
+// Full transform of one column through the accessor `acc` (synchronises the block).  On entry
+// the caller guarantees the block is done reading the exchange storage from any earlier use.
+template <int N, int E, bool INV, int S = 0, typename T2, typename ACC, typename TW>
+__device__ __forceinline__ void fft_column_acc(T2 (&x)[E], int t, const ACC& acc, const TW& tw) {
   if constexpr (S < num_stages(N)) {
     fft_stage<N, E, S, INV>(x, t, tw);
     if constexpr (S + 1 < num_stages(N)) {
@@ -145,15 +205,22 @@ __device__ __forceinline__ void fft_column(T2 (&x)[E], int t, T2* buf, const IDX
 #pragma unroll
       for (int q = 0; q < Q; ++q)
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[idx(stage_out_pos<N, E, S>(t, q, r))] = x[q + r * Q];
+        for (int r = 0; r < R; ++r) acc.put(stage_out_pos<N, E, S>(t, q, r), x[q + r * Q]);
       __syncthreads();
       constexpr int TPC = N / E;
 #pragma unroll
-      for (int e = 0; e < E; ++e) x[e] = buf[idx(t + TPC * e)];
+      for (int e = 0; e < E; ++e) x[e] = acc.get(t + TPC * e);
       __syncthreads();
-      fft_column<N, E, INV, S + 1>(x, t, buf, idx, tw);
+      fft_column_acc<N, E, INV, S + 1>(x, t, acc, tw);
     }
   }
+}
+
+// Interleaved-complex exchange through `idx(i)`, twiddles from the plain table.
+template <int N, int E, bool INV, typename T2, typename IDX>
+__device__ __forceinline__ void fft_column(T2 (&x)[E], int t, T2* buf, const IDX& idx,
+                                           const T2* __restrict__ tw) {
+  fft_column_acc<N, E, INV>(x, t, AosAcc<T2, IDX>{buf, idx}, TwPlain<T2>{tw});
 }
 
 // Kahan-compensated FP32/FP64 running sum (per-thread partial of a global FP64 reduction).

@@ -8,6 +8,7 @@
 #include <sstream>
 #include <complex>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -42,56 +43,94 @@ bool gen_length_supported(int n) {
   return false;
 }
 
-// ---- finalisation (one thread per field, fixed order) -------------------------------------
+// ---- finalisation: one block per field; each thread sums a fixed strided share of the
+// field's partial records, then a fixed-shape tree (bitwise reproducible for a given launch).
 
-__global__ void k_gen_finalize_mean(const double* __restrict__ part, const long long* __restrict__ item0,
-                                    const FieldDesc* __restrict__ fields, int nf,
-                                    double* __restrict__ mean, double* __restrict__ instats) {
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
-    const long long i0 = item0[f], i1 = item0[f + 1];
-    const long long per_comp = (i1 - i0) / 3;
-    double sq = 0.0, nfin = 0.0;
-    for (int c = 0; c < 3; ++c) {
-      double sa = 0.0, sb = 0.0;
-      for (long long it = i0 + c * per_comp; it < i0 + (c + 1) * per_comp; ++it)
-        for (int w = 0; w < WARPS_MAX; ++w) {
-          const double* p = part + (it * WARPS_MAX + w) * 4;
-          sa += p[0]; sb += p[1]; sq += p[2]; nfin += p[3];
-        }
-      const double vol = double(fields[f].V);
-      mean[f * 6 + 2 * c] = sa / vol;
-      mean[f * 6 + 2 * c + 1] = sb / vol;
+constexpr int FIN_THREADS = 256;
+
+template <int K>
+__device__ __forceinline__ void fin_block_sum(double (&v)[K], double* red) {
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[warp * K + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < FIN_THREADS / 32; ++w) s += red[w * K + k];
+      v[k] = s;
     }
-    instats[f * 2] = sq;
-    instats[f * 2 + 1] = nfin;
+}
+
+__global__ void __launch_bounds__(FIN_THREADS)
+k_gen_finalize_mean(const double* __restrict__ part, const long long* __restrict__ item0,
+                    const FieldDesc* __restrict__ fields, int nf, double* __restrict__ mean,
+                    double* __restrict__ instats) {
+  __shared__ double red[(FIN_THREADS / 32) * 8];
+  const int f = blockIdx.x;
+  if (f >= nf) return;
+  const long long i0 = item0[f], i1 = item0[f + 1];
+  const long long per_comp = (i1 - i0) / 3;
+  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // sa, sb per component, sq, nonfinite
+  for (int c = 0; c < 3; ++c) {
+    const long long r0 = (i0 + c * per_comp) * WARPS_MAX, r1 = (i0 + (c + 1) * per_comp) * WARPS_MAX;
+    for (long long r = r0 + threadIdx.x; r < r1; r += FIN_THREADS) {
+      const double* p = part + r * 4;
+      v[2 * c] += p[0];
+      v[2 * c + 1] += p[1];
+      v[6] += p[2];
+      v[7] += p[3];
+    }
+  }
+  fin_block_sum<8>(v, red);
+  if (threadIdx.x == 0) {
+    const double vol = double(fields[f].V);
+    for (int j = 0; j < 6; ++j) mean[f * 6 + j] = v[j] / vol;
+    instats[f * 2] = v[6];
+    instats[f * 2 + 1] = v[7];
   }
 }
 
-__global__ void k_gen_finalize_norms(const double* __restrict__ partx, const long long* __restrict__ itemx,
-                                     const double* __restrict__ partl, const long long* __restrict__ iteml,
-                                     const FieldDesc* __restrict__ fields, int nf,
-                                     const double* __restrict__ mean, const double* __restrict__ instats,
-                                     int linf_flag, eq_norms_t* __restrict__ out) {
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
-    double r2 = 0.0, di = 0.0, dout = 0.0, o2 = 0.0;
-    for (long long it = itemx[f]; it < itemx[f + 1]; ++it)
-      for (int w = 0; w < WARPS_MAX; ++w) {
-        const double* p = partx + (it * WARPS_MAX + w) * 4;
-        r2 += p[0]; di += p[1]; dout += p[2]; o2 += p[3];
-      }
+__global__ void __launch_bounds__(FIN_THREADS)
+k_gen_finalize_norms(const double* __restrict__ partx, const long long* __restrict__ itemx,
+                     const double* __restrict__ partl, const long long* __restrict__ iteml,
+                     const FieldDesc* __restrict__ fields, int nf, const double* __restrict__ mean,
+                     const double* __restrict__ instats, int linf_flag, eq_norms_t* __restrict__ out) {
+  __shared__ double red[(FIN_THREADS / 32) * 4];
+  __shared__ double redm[FIN_THREADS / 32];
+  const int f = blockIdx.x;
+  if (f >= nf) return;
+  double v[4] = {0, 0, 0, 0};   // resid^2, div_in^2, div_out^2, out^2 (spectral sums)
+  for (long long r = itemx[f] * WARPS_MAX + threadIdx.x; r < itemx[f + 1] * WARPS_MAX; r += FIN_THREADS) {
+    const double* p = partx + r * 4;
+    v[0] += p[0]; v[1] += p[1]; v[2] += p[2]; v[3] += p[3];
+  }
+  double lm = 0.0;
+  if (partl)
+    for (long long r = iteml[f] * WARPS_MAX * 4 + threadIdx.x; r < iteml[f + 1] * WARPS_MAX * 4; r += FIN_THREADS)
+      lm = fmax(lm, partl[r]);
+  fin_block_sum<4>(v, red);
+  for (int o = 16; o > 0; o >>= 1) lm = fmax(lm, __shfl_down_sync(0xffffffffu, lm, o));
+  if ((threadIdx.x & 31) == 0) redm[threadIdx.x >> 5] = lm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < FIN_THREADS / 32; ++w) lm = fmax(lm, redm[w]);
     const double vol = double(fields[f].V), v2 = vol * vol;
     eq_norms_t n;
     for (int j = 0; j < 6; ++j) n.mean[j] = mean[f * 6 + j];
     n.norm_in = sqrt(instats[f * 2] / vol);
-    n.norm_out = sqrt(o2 / v2);
-    n.resid_l2 = sqrt(r2 / v2);
+    n.norm_out = sqrt(v[3] / v2);
+    n.resid_l2 = sqrt(v[0] / v2);
     n.resid_rel = n.norm_in > 0.0 ? n.resid_l2 / n.norm_in : 0.0;
-    n.div_in_l2 = sqrt(di / v2);
-    n.div_out_l2 = sqrt(dout / v2);
-    double lm = 0.0;
-    if (partl)
-      for (long long it = iteml[f]; it < iteml[f + 1]; ++it)
-        for (int w = 0; w < WARPS_MAX * 4; ++w) lm = fmax(lm, partl[it * WARPS_MAX * 4 + w]);
+    n.div_in_l2 = sqrt(v[1] / v2);
+    n.div_out_l2 = sqrt(v[2] / v2);
     n.resid_linf = lm;
     n.flags = (instats[f * 2 + 1] > 0.0 ? EQ_FLAG_NONFINITE : 0) | linf_flag;
     out[f] = n;
@@ -155,6 +194,26 @@ template <typename T> void push_real(std::vector<unsigned char>& pool, double v)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// DFT_m(b) / m of the wrapped conjugate chirp, computed once per (n, m) in the process (a direct
+// O(m^2) sum in FP64) and kept for later plans.
+const std::vector<std::complex<double>>& chirp_transform(int n, int m,
+                                                         const std::vector<std::complex<double>>& b) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, std::vector<std::complex<double>>> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find({n, m});
+  if (it != cache.end()) return it->second;
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<std::complex<double>> w(m), out(m);
+  for (int j = 0; j < m; ++j) w[j] = std::polar(1.0, -two_pi * double(j) / double(m));
+  for (int k = 0; k < m; ++k) {
+    std::complex<double> acc = 0.0;
+    for (int d = 0; d < m; ++d) acc += b[d] * w[(long long)k * d % m];
+    out[k] = acc / double(m);
+  }
+  return cache.emplace(std::make_pair(n, m), std::move(out)).first->second;
+}
+
 template <typename T>
 void build_tables(GenPlan* g, const std::vector<int>& lens, std::vector<unsigned char>& cpool,
                   std::map<int, int>& axis_of_len) {
@@ -201,12 +260,7 @@ void build_tables(GenPlan* g, const std::vector<int>& lens, std::vector<unsigned
       ap.chirp = int(cpool.size() / (2 * sizeof(T)));
       for (int j = 0; j < n; ++j) push_complex<T>(cpool, c[j]);
       ap.bhat = int(cpool.size() / (2 * sizeof(T)));
-      for (int k = 0; k < ap.m; ++k) {
-        std::complex<double> acc = 0.0;
-        for (int d = 0; d < ap.m; ++d)
-          acc += b[d] * std::polar(1.0, -two_pi * double((long long)k * d % ap.m) / ap.m);
-        push_complex<T>(cpool, acc / double(ap.m));
-      }
+      for (const std::complex<double>& v : chirp_transform(n, ap.m, b)) push_complex<T>(cpool, v);
     }
     axis_of_len[n] = (int)g->ah.size();
     g->ah.push_back(ap);
@@ -498,8 +552,8 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   a.in = d_in; a.out = d_out; a.ref = nullptr; a.partials = g->part_first; a.axis = 2; a.mode = 1;
   if ((e = launch(0, a, g->z)) != cudaSuccess) { *err = std::string("z forward: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
   mark(1);
-  k_gen_finalize_mean<<<(g->F + 127) / 128, 128, 0, s>>>(g->part_first, g->z.item0, g->fields, g->F,
-                                                         g->mean, g->instats);
+  k_gen_finalize_mean<<<g->F, FIN_THREADS, 0, s>>>(g->part_first, g->z.item0, g->fields, g->F,
+                                                   g->mean, g->instats);
   if ((e = cudaGetLastError()) != cudaSuccess) { *err = std::string("mean: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
   mark(2);
   shape(g->y);
@@ -519,7 +573,7 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   a.ref = linf ? d_in : nullptr; a.partials = g->part_last; a.axis = 2; a.mode = linf ? 2 : 0;
   if ((e = launch(1, a, g->z)) != cudaSuccess) { *err = std::string("z inverse: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
   mark(6);
-  k_gen_finalize_norms<<<(g->F + 127) / 128, 128, 0, s>>>(
+  k_gen_finalize_norms<<<g->F, FIN_THREADS, 0, s>>>(
       g->part_x, g->x.item0, linf ? g->part_last : nullptr, g->z.item0, g->fields, g->F, g->mean,
       g->instats, linf ? 0 : EQ_FLAG_NO_LINF, g->norms);
   if ((e = cudaGetLastError()) != cudaSuccess) { *err = std::string("norms: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }

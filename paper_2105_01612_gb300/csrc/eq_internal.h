@@ -31,21 +31,22 @@ cudaError_t launch_xproj_f32(int n, const XArgs& a, dim3 grid, cudaStream_t s);
 cudaError_t launch_xproj_f64(int n, const XArgs& a, dim3 grid, cudaStream_t s);
 
 // TMA-fed strided passes: info returns cudaErrorInvalidValue when no instance exists for n.
+// v selects the shape variant (0: wide tiles, one block per SM; 1: narrow tiles, two blocks).
 struct TmaInfo {
-  int threads = 0, cols = 0, box = 0;
+  int threads = 0, cols = 0, box = 0, blocks_per_sm = 0;
   size_t smem = 0;
 };
-cudaError_t tma_info_f32(int n, TmaInfo* out);
-cudaError_t tma_info_f64(int n, TmaInfo* out);
-cudaError_t launch_tma_f32(int n, bool inv, const CUtensorMap& map, const TmaArgs& a, dim3 grid,
-                           cudaStream_t s);
-cudaError_t launch_tma_f64(int n, bool inv, const CUtensorMap& map, const TmaArgs& a, dim3 grid,
-                           cudaStream_t s);
+cudaError_t tma_info_f32(int n, int v, TmaInfo* out);
+cudaError_t tma_info_f64(int n, int v, TmaInfo* out);
+cudaError_t launch_tma_f32(int n, int v, bool inv, const CUtensorMap& map, const TmaArgs& a,
+                           dim3 grid, cudaStream_t s);
+cudaError_t launch_tma_f64(int n, int v, bool inv, const CUtensorMap& map, const TmaArgs& a,
+                           dim3 grid, cudaStream_t s);
 // bulk-copy fused x pass: info fails when no instance exists for n
-cudaError_t xtma_info_f32(int n, TmaInfo* out);
-cudaError_t xtma_info_f64(int n, TmaInfo* out);
-cudaError_t launch_xtma_f32(int n, const XTmaArgs& a, dim3 grid, cudaStream_t s);
-cudaError_t launch_xtma_f64(int n, const XTmaArgs& a, dim3 grid, cudaStream_t s);
+cudaError_t xtma_info_f32(int n, int v, TmaInfo* out);
+cudaError_t xtma_info_f64(int n, int v, TmaInfo* out);
+cudaError_t launch_xtma_f32(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s);
+cudaError_t launch_xtma_f64(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s);
 
 // Finalisation kernels of the power-of-two path (fixed-order FP64 reductions of block partials).
 void finalize_mean(const double* part, int grid, int batch, double vol, double* mean,

@@ -61,11 +61,14 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
       : "memory");
 }
 
-template <typename T, int N> struct TmaCfg {
+// V = 0: 64-byte tile rows (16 FP32 / 8 FP64 columns), one block per SM; V = 1: 32-byte rows,
+// half the shared memory, two blocks per SM.
+template <typename T, int N, int V = 0> struct TmaCfg {
   static constexpr int E = 8;
   static constexpr int TPC = N / E;
-  static constexpr int B = (sizeof(T) == 4 ? 16 : 8) * TPC <= 1024 ? (sizeof(T) == 4 ? 16 : 8)
-                                                                    : 1024 / TPC;
+  static constexpr int BW = (sizeof(T) == 4 ? 16 : 8) >> V;
+  static constexpr int B = BW * TPC <= 1024 ? BW : 1024 / TPC;
+  static constexpr int MINB = V == 0 ? 1 : 2;
   static constexpr int THREADS = B * TPC;
   static constexpr int BOX = N < 256 ? N : 256;       // points per TMA box along the axis
   static constexpr int NBOX = N / BOX;
@@ -73,7 +76,7 @@ template <typename T, int N> struct TmaCfg {
   static constexpr size_t STAGE_BYTES = 2 * sizeof(T) * size_t(N) * B;   // re + im planes
   static constexpr size_t SMEM = 1024 /*align + barriers*/ + sizeof(T2) * N + 2 * STAGE_BYTES +
                                  sizeof(T2) * size_t(N) * B;
-  static constexpr bool OK = N >= 64 && SMEM <= 227 * 1024;
+  static constexpr bool OK = N >= 64 && SMEM * MINB <= 227 * 1024 && (V == 0 || B * TPC <= 512);
 };
 
 struct TmaArgs {
@@ -89,18 +92,18 @@ struct TmaArgs {
   long long ntiles;        // tiles per (field, component)
 };
 
-template <typename T, int N, bool INV>
-__global__ void __launch_bounds__(TmaCfg<T, N>::THREADS, 1)
+// MODE: 0 middle pass, 1 first pass (input statistics), 2 last pass (L-inf against a.ref)
+template <typename T, int N, bool INV, int MODE, int V>
+__global__ void __launch_bounds__(TmaCfg<T, N, V>::THREADS, TmaCfg<T, N, V>::MINB)
 k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
-  using C = TmaCfg<T, N>;
+  using C = TmaCfg<T, N, V>;
   using T2 = typename C::T2;
   constexpr int E = C::E, TPC = C::TPC, B = C::B, BOX = C::BOX, NBOX = C::NBOX;
   extern __shared__ __align__(16) unsigned char smem_tma[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_tma) + 127) & ~uintptr_t(127));
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(base);
-  T* stage0 = reinterpret_cast<T*>(base + 128);
-  T* stage[2] = {stage0, stage0 + 2 * N * B};
+  T* stage0 = reinterpret_cast<T*>(base + 128);      // stage s at stage0 + s * 2 N B
   T2* tw = reinterpret_cast<T2*>(stage0 + 4 * N * B);
   T2* xbuf = tw + N;
   __shared__ double red[32 * 4];
@@ -113,7 +116,7 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
   const long long fbase = field * a.field_stride + (2LL * comp) * a.V;
   T* out_re = reinterpret_cast<T*>(a.out) + fbase;
   T* out_im = out_re + a.V;
-  const T* ref_re = a.ref ? reinterpret_cast<const T*>(a.ref) + fbase : nullptr;
+  const T* ref_re = (MODE == 2 && a.ref) ? reinterpret_cast<const T*>(a.ref) + fbase : nullptr;
   const T wa = comp == 2 ? T(2) : T(1), wb = comp == 0 ? T(1) : T(2);
   const int tiles_x = a.nx / B;
   const long long nstride = a.axis == 2 ? (long long)a.nx * a.ny : a.nx;
@@ -128,17 +131,17 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
   __syncthreads();
 
   // coordinates of tile u: (x0, row) with row = y (z pass) or z (y pass)
-  int issued[2] = {0, 0};                              // loads issued per stage (thread 0)
+  int issued0 = 0, issued1 = 0;                        // loads issued per stage (thread 0)
   auto issue = [&](long long u, int s) {
     const int x0 = (int)(u % tiles_x) * B;
     const int row = (int)(u / tiles_x);
-    ++issued[s];
+    if (s) ++issued1; else ++issued0;
     mbar_expect_tx(&bar[s], (unsigned)C::STAGE_BYTES);
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
       for (int q = 0; q < NBOX; ++q) {
-        T* dst = stage[s] + p * N * B + q * BOX * B;
+        T* dst = stage0 + s * 2 * N * B + p * N * B + q * BOX * B;
         if (a.axis == 2) tma_load_4d(dst, &map, &bar[s], x0, row, q * BOX, plane_re + p);
         else tma_load_4d(dst, &map, &bar[s], x0, q * BOX, row, plane_re + p);
       }
@@ -163,7 +166,7 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
     __syncthreads();
     if (abort_flag) break;
     T2 x[E];
-    const T* sre = stage[s];
+    const T* sre = stage0 + s * 2 * N * B;
     const T* sim = sre + N * B;
 #pragma unroll
     for (int e = 0; e < E; ++e) x[e] = T2{sre[(t + TPC * e) * B + b], sim[(t + TPC * e) * B + b]};
@@ -172,7 +175,7 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(u + 2 * step, s);
     }
-    if (a.mode == 1) {
+    if constexpr (MODE == 1) {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         if (!isfinite(x[e].x) || !isfinite(x[e].y)) nonfinite += T(1);
@@ -190,56 +193,76 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
       const long long off = col0 + (long long)(t + TPC * e) * nstride;
       out_re[off] = x[e].x;
       out_im[off] = x[e].y;
-      if (ref_re) {
-        linf = fmax(linf, fabs(ref_re[off] - x[e].x));
-        linf = fmax(linf, fabs(ref_re[off + a.V] - x[e].y));
+      if constexpr (MODE == 2) {
+        if (ref_re) {
+          linf = fmax(linf, fabs(ref_re[off] - x[e].x));
+          linf = fmax(linf, fabs(ref_re[off + a.V] - x[e].y));
+        }
       }
     }
   }
   if (abort_flag) {
     // leave no copy in flight: wait (bounded) for every phase this block issued
-    if (tid == 0)
-      for (int s = 0; s < 2; ++s)
-        if (issued[s] > 0) mbar_wait(&bar[s], (unsigned)((issued[s] - 1) & 1));
+    if (tid == 0) {
+      if (issued0 > 0) mbar_wait(&bar[0], (unsigned)((issued0 - 1) & 1));
+      if (issued1 > 0) mbar_wait(&bar[1], (unsigned)((issued1 - 1) & 1));
+    }
     __syncthreads();
     return;
   }
-  if (a.mode == 1) {
+  if constexpr (MODE == 1) {
     double v[4] = {sa.value(), sb.value(), sq.value(), double(nonfinite)};
     block_sum<4>(v, red);
     if (tid == 0) {
       double* p = a.partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 4;
       p[0] = v[0]; p[1] = v[1]; p[2] = v[2]; p[3] = v[3];
     }
-  } else if (a.mode == 2 && ref_re) {
-    double m = block_max(double(linf), red);
-    if (tid == 0) a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = m;
+  } else if constexpr (MODE == 2) {
+    if (ref_re) {
+      double m = block_max(double(linf), red);
+      if (tid == 0) a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = m;
+    }
   }
 }
 
 // ---- fused x pass with bulk-copy double buffering --------------------------------------
 //
 // Same work as k_xproj (forward x transform of P row pairs, projector per mode pair, inverse x
-// transform), but the rows of group g + 2 stream into shared memory with cp.async.bulk (one 1-D
-// copy per row and plane) while the block works on group g.
+// transform).  The rows of group g + 2 stream into shared memory with cp.async.bulk (one 1-D copy
+// per row and plane) while the block works on group g; the results leave through a shared
+// staging buffer with cp.async.bulk stores (one per row and plane), so the store traffic costs
+// the threads nothing.  The exchanges use split real/imaginary arrays and per-stage twiddle
+// tables, both laid out so that a warp's accesses hit distinct banks.
 
-template <typename T, int N> struct XTmaCfg {
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
+                   reinterpret_cast<unsigned long long>(gdst)),
+               "r"(smem_u32(ssrc)), "r"(bytes)
+               : "memory");
+}
+
+// V = 0: two row pairs per block (FP32, N <= 512), one block per SM; V = 1: one row pair per
+// block, two blocks per SM.
+template <typename T, int N, int V = 0> struct XTmaCfg {
   static constexpr int E = 8;
   static constexpr int TPC = N / E;
-  static constexpr int P = (sizeof(T) == 4 && N <= 512) ? 2 : 1;
+  static constexpr int P = (V == 0 && sizeof(T) == 4 && N <= 512) ? 2 : 1;
+  static constexpr int MINB = V == 0 ? 1 : 2;
   static constexpr int XCOLS = 6 * P;
   static constexpr int THREADS = XCOLS * TPC;
-  static constexpr int PITCH = N + (N >> 3);
+  static constexpr int PF = N;                                          // exchange row (swizzled)
+  static constexpr int TWS = staged_size(N);
   using T2 = typename V2<T>::t;
   static constexpr size_t STAGE_BYTES = 2 * sizeof(T) * size_t(N) * XCOLS;   // re + im rows
-  static constexpr size_t SMEM = 1024 + 2 * STAGE_BYTES + sizeof(T2) * size_t(XCOLS) * PITCH +
-                                 sizeof(T2) * N + sizeof(T) * N;
-  static constexpr bool OK = N >= 64 && THREADS <= 1024 && SMEM <= 227 * 1024;
+  static constexpr size_t SMEM = 1024 + 3 * STAGE_BYTES + 2 * sizeof(T) * size_t(XCOLS) * PF +
+                                 2 * sizeof(T) * TWS + sizeof(T) * N;
+  static constexpr bool OK = N >= 64 && THREADS * MINB <= 1024 && SMEM * MINB <= 227 * 1024 &&
+                            (V == 0 || P == 1);
 };
 
 struct XTmaArgs {
   void* data;
-  const void* tw;
+  const void* tws;         // per-stage twiddles of the x length: cos[TWS] then sin[TWS]
   const void* xi_x;
   const void* xi_y;
   const void* xi_z;
@@ -254,29 +277,34 @@ struct XTmaArgs {
   double inv_v;
 };
 
-template <typename T, int N>
-__global__ void __launch_bounds__(XTmaCfg<T, N>::THREADS, 1)
+template <typename T, int N, int V>
+__global__ void __launch_bounds__(XTmaCfg<T, N, V>::THREADS, XTmaCfg<T, N, V>::MINB)
 k_xproj_tma(const XTmaArgs a) {
-  using C = XTmaCfg<T, N>;
+  using C = XTmaCfg<T, N, V>;
   using T2 = typename C::T2;
-  constexpr int E = C::E, TPC = C::TPC, P = C::P, PITCH = C::PITCH, XCOLS = C::XCOLS;
+  constexpr int E = C::E, TPC = C::TPC, P = C::P, PF = C::PF, XCOLS = C::XCOLS, TWS = C::TWS;
   extern __shared__ __align__(16) unsigned char smem_xt[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_xt) + 127) & ~uintptr_t(127));
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(base);
-  T* stage0 = reinterpret_cast<T*>(base + 128);
-  T* stage[2] = {stage0, stage0 + 2 * N * XCOLS};
-  T2* buf = reinterpret_cast<T2*>(stage0 + 4 * N * XCOLS);
-  T2* tw = buf + XCOLS * PITCH;
-  T* xix = reinterpret_cast<T*>(tw + N);
+  T* stage0 = reinterpret_cast<T*>(base + 128);       // stage s at stage0 + s * 2 N XCOLS
+  T* outs = stage0 + 4 * N * XCOLS;                     // bulk-store source, [col][plane][N]
+  T* xre = outs + 2 * N * XCOLS;                        // exchange, [col][PF]
+  T* xim = xre + XCOLS * PF;
+  T* twc = xim + XCOLS * PF;
+  T* tws = twc + TWS;
+  T* xix = tws + TWS;
   __shared__ double red[32 * 4];
   __shared__ int abort_flag;
+  __shared__ int rinfo[2][P][6];                        // rowA, rowB, self, valid, kz, ky
+  __shared__ T rxi[2][P][2];                            // Xi_y(ky), Xi_z(kz)
 
   const int tid = threadIdx.x;
-  for (int i = tid; i < N; i += blockDim.x) {
-    tw[i] = reinterpret_cast<const T2*>(a.tw)[i];
-    xix[i] = reinterpret_cast<const T*>(a.xi_x)[i];
+  for (int i = tid; i < TWS; i += blockDim.x) {
+    twc[i] = reinterpret_cast<const T*>(a.tws)[i];
+    tws[i] = reinterpret_cast<const T*>(a.tws)[TWS + i];
   }
+  for (int i = tid; i < N; i += blockDim.x) xix[i] = reinterpret_cast<const T*>(a.xi_x)[i];
   if (tid == 0) {
     abort_flag = 0;
     mbar_init(&bar[0], 1);
@@ -284,16 +312,15 @@ k_xproj_tma(const XTmaArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  const TwStaged<T> tw{twc, tws};
   const T* xiy = reinterpret_cast<const T*>(a.xi_y);
   const T* xiz = reinterpret_cast<const T*>(a.xi_z);
   const int col = tid / TPC, t = tid % TPC;
-  const int slot = col / 6, side = (col % 6) / 3, comp = col % 3;
+  const int slot = col / 6, side = (col % 6) / 3;
   const int field = blockIdx.y;
   T* fdata = reinterpret_cast<T*>(a.data) + field * a.field_stride;
-  T* pre = fdata + (2LL * comp) * a.V;
-  T* pim = pre + a.V;
   const double* mean = a.mean ? a.mean + field * 6 : nullptr;
-  const IdxRow idx{col * PITCH};
+  const SoaAcc<T> acc{xre + col * PF, xim + col * PF};
   const T inv_v = T(a.inv_v);
   const double vol = 1.0 / a.inv_v;
 
@@ -301,7 +328,7 @@ k_xproj_tma(const XTmaArgs a) {
     const int kz = r / a.ny, ky = r - kz * a.ny;
     return (kz == 0 ? 0 : a.nz - kz) * a.ny + (ky == 0 ? 0 : a.ny - ky);
   };
-  int issued[2] = {0, 0};
+  int issued0 = 0, issued1 = 0;
   // thread 0: stream the rows of group g into stage s (skipping absent and mirror-of-self rows)
   auto issue = [&](int g, int s) {
     unsigned bytes = 0;
@@ -315,10 +342,11 @@ k_xproj_tma(const XTmaArgs a) {
         rows[2 * q] = rA;
         rows[2 * q + 1] = rB == rA ? -1 : rB;
       }
-      bytes += (rows[2 * q] >= 0 ? 6u : 0u) * N * sizeof(T) + (rows[2 * q + 1] >= 0 ? 6u : 0u) * N * sizeof(T);
+      bytes += ((rows[2 * q] >= 0 ? 6u : 0u) + (rows[2 * q + 1] >= 0 ? 6u : 0u)) * N * sizeof(T);
     }
-    ++issued[s];
+    if (s) ++issued1; else ++issued0;
     mbar_expect_tx(&bar[s], bytes);
+    T* st = stage0 + s * 2 * N * XCOLS;
 #pragma unroll
     for (int q = 0; q < P; ++q)
 #pragma unroll
@@ -330,9 +358,8 @@ k_xproj_tma(const XTmaArgs a) {
 #pragma unroll
           for (int pl = 0; pl < 2; ++pl) {
             const int cc = q * 6 + sd * 3 + c;
-            T* dst = stage[s] + (2 * cc + pl) * N;
-            const T* src = fdata + (2LL * c + pl) * a.V + (long long)r * N;
-            bulk_load(dst, src, N * sizeof(T), &bar[s]);
+            bulk_load(st + (2 * cc + pl) * N, fdata + (2LL * c + pl) * a.V + (long long)r * N,
+                      N * sizeof(T), &bar[s]);
           }
       }
   };
@@ -346,23 +373,30 @@ k_xproj_tma(const XTmaArgs a) {
   int k = 0;
   for (int g = first; g < a.ngroups; g += step, ++k) {
     const int s = k & 1;
+    if (tid < P) {                                      // row information of this group
+      const int p = g * P + tid;
+      const int rA = p < a.npairs ? a.pairs[p] : 0;
+      const int rB = mirror(rA);
+      const int kz = rA / a.ny, ky = rA - kz * a.ny;
+      rinfo[s][tid][0] = rA;
+      rinfo[s][tid][1] = rB;
+      rinfo[s][tid][2] = rA == rB;
+      rinfo[s][tid][3] = p < a.npairs;
+      rinfo[s][tid][4] = kz;
+      rinfo[s][tid][5] = ky;
+      rxi[s][tid][0] = xiy[ky];
+      rxi[s][tid][1] = xiz[kz];
+    }
     if (!mbar_wait(&bar[s], (k >> 1) & 1)) {
       atomicOr(a.err, 1);
       abort_flag = 1;
     }
     __syncthreads();
     if (abort_flag) break;
-    const int p = g * P + slot;
-    const bool valid = p < a.npairs;
-    int rowA = 0, rowB = 0;
-    if (valid) {
-      rowA = a.pairs[p];
-      rowB = mirror(rowA);
-    }
-    const bool active = valid && !(side == 1 && rowA == rowB);
+    const bool active = rinfo[s][slot][3] && !(side == 1 && rinfo[s][slot][2]);
     T2 x[E];
     {
-      const T* sre = stage[s] + (2 * col) * N;
+      const T* sre = stage0 + s * 2 * N * XCOLS + (2 * col) * N;
       const T* sim = sre + N;
 #pragma unroll
       for (int e = 0; e < E; ++e)
@@ -373,53 +407,83 @@ k_xproj_tma(const XTmaArgs a) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(g + 2 * step, s);
     }
-    fft_column<N, E, false>(x, t, buf, idx, tw);
+    fft_column_acc<N, E, false>(x, t, acc, tw);
 #pragma unroll
-    for (int e = 0; e < E; ++e) buf[idx(t + TPC * e)] = x[e];
+    for (int e = 0; e < E; ++e) acc.put(t + TPC * e, x[e]);
     __syncthreads();
     for (int item = tid; item < P * N; item += blockDim.x) {
       const int s2 = item / N, kx = item - s2 * N;
-      const int p2 = g * P + s2;
-      if (p2 >= a.npairs) continue;
-      const int rA = a.pairs[p2];
-      const int kz = rA / a.ny, ky = rA - kz * a.ny;
-      const bool self2 = mirror(rA) == rA;
+      if (!rinfo[s][s2][3]) continue;
+      const int rA = rinfo[s][s2][0];
+      const bool self2 = rinfo[s][s2][2];
       const int kxm = kx == 0 ? 0 : N - kx;
       if (self2 && kx > kxm) continue;
       const int colA = s2 * 6, colB = self2 ? s2 * 6 : s2 * 6 + 3;
+      const int ja = swz(kx), jb = swz(kxm);
       T2 av[3], bv[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        av[c] = buf[(colA + c) * PITCH + kx + (kx >> 3)];
-        bv[c] = buf[(colB + c) * PITCH + kxm + (kxm >> 3)];
+        av[c] = T2{xre[(colA + c) * PF + ja], xim[(colA + c) * PF + ja]};
+        bv[c] = T2{xre[(colB + c) * PF + jb], xim[(colB + c) * PF + jb]};
       }
       const bool selfmode = self2 && kx == kxm;
-      project_pair<T>(av, bv, xix[kx], xiy[ky], xiz[kz], rA == 0 && kx == 0, mean, vol,
+      project_pair<T>(av, bv, xix[kx], rxi[s][s2][0], rxi[s][s2][1], rA == 0 && kx == 0, mean, vol,
                       a.nyq_zero != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        buf[(colA + c) * PITCH + kx + (kx >> 3)] = av[c];
-        if (!selfmode) buf[(colB + c) * PITCH + kxm + (kxm >> 3)] = bv[c];
+        xre[(colA + c) * PF + ja] = av[c].x;
+        xim[(colA + c) * PF + ja] = av[c].y;
+        if (!selfmode) {
+          xre[(colB + c) * PF + jb] = bv[c].x;
+          xim[(colB + c) * PF + jb] = bv[c].y;
+        }
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = buf[idx(t + TPC * e)];
+    for (int e = 0; e < E; ++e) x[e] = acc.get(t + TPC * e);
     __syncthreads();
-    fft_column<N, E, true>(x, t, buf, idx, tw);
+    fft_column_acc<N, E, true>(x, t, acc, tw);
+    // results -> staging -> bulk stores; the previous group's stores must have read it first
+    if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    __syncthreads();
     if (active) {
-      const long long roff = (long long)(side == 0 ? rowA : rowB) * N;
+      T* ore = outs + (2 * col) * N;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        pre[roff + t + TPC * e] = x[e].x;
-        pim[roff + t + TPC * e] = x[e].y;
+        ore[t + TPC * e] = x[e].x;
+        ore[N + t + TPC * e] = x[e].y;
       }
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        if (!rinfo[s][q][3]) continue;
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          if (sd == 1 && rinfo[s][q][2]) continue;
+          const int r = rinfo[s][q][sd];
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int pl = 0; pl < 2; ++pl) {
+              const int cc = q * 6 + sd * 3 + c;
+              bulk_store(fdata + (2LL * c + pl) * a.V + (long long)r * N, outs + (2 * cc + pl) * N,
+                         N * sizeof(T));
+            }
+        }
+      }
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
   }
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   if (abort_flag) {
-    if (tid == 0)
-      for (int s = 0; s < 2; ++s)
-        if (issued[s] > 0) mbar_wait(&bar[s], (unsigned)((issued[s] - 1) & 1));
+    if (tid == 0) {
+      if (issued0 > 0) mbar_wait(&bar[0], (unsigned)((issued0 - 1) & 1));
+      if (issued1 > 0) mbar_wait(&bar[1], (unsigned)((issued1 - 1) & 1));
+    }
     __syncthreads();
     return;
   }
