@@ -105,6 +105,35 @@ template <typename T, int N, int V> struct XTmaInst {
   }
 };
 
+template <typename T, int N> struct XwInst {
+  static cudaError_t info(TmaInfo* out) {
+    using C = XwCfg<T, N>;
+    if constexpr (!C::OK) {
+      return cudaErrorInvalidValue;
+    } else {
+      out->threads = C::THREADS;
+      out->cols = 1;
+      out->box = 0;
+      out->smem = C::SMEM;
+      const void* f = reinterpret_cast<const void*>(&k_xproj_warp<T, N>);
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      int bl = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, f, C::THREADS, C::SMEM);
+      out->blocks_per_sm = bl;
+      return e;
+    }
+  }
+  static cudaError_t launch(const XTmaArgs& a, dim3 grid, cudaStream_t s) {
+    using C = XwCfg<T, N>;
+    if constexpr (!C::OK) {
+      return cudaErrorInvalidValue;
+    } else {
+      k_xproj_warp<T, N><<<grid, C::THREADS, C::SMEM, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
+};
+
 #define EQ_FOR_LENGTHS(X) X(1) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
 template <typename T> cudaError_t info_t(int n, PassKind kind, PassInfo* out) {
@@ -155,7 +184,10 @@ cudaError_t tma_launch_t(int n, int v, bool inv, const CUtensorMap& map, const T
 
 template <typename T> cudaError_t xtma_info_t(int n, int v, TmaInfo* out) {
   switch (n) {
-#define EQ_CASE(N) case N: return v ? XTmaInst<T, N, 1>::info(out) : XTmaInst<T, N, 0>::info(out);
+#define EQ_CASE(N)                                              \
+  case N:                                                         \
+    return v == 2 ? XwInst<T, N>::info(out)                       \
+                  : (v ? XTmaInst<T, N, 1>::info(out) : XTmaInst<T, N, 0>::info(out));
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;
@@ -163,7 +195,10 @@ template <typename T> cudaError_t xtma_info_t(int n, int v, TmaInfo* out) {
 }
 template <typename T> cudaError_t xtma_launch_t(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s) {
   switch (n) {
-#define EQ_CASE(N) case N: return v ? XTmaInst<T, N, 1>::launch(a, grid, s) : XTmaInst<T, N, 0>::launch(a, grid, s);
+#define EQ_CASE(N)                                                       \
+  case N:                                                                  \
+    return v == 2 ? XwInst<T, N>::launch(a, grid, s)                       \
+                  : (v ? XTmaInst<T, N, 1>::launch(a, grid, s) : XTmaInst<T, N, 0>::launch(a, grid, s));
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;

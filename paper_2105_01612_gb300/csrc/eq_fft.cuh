@@ -193,9 +193,11 @@ template <typename T> struct SoaAcc {
   }
 };
 
-// Full transform of one column through the accessor `acc` (synchronises the block).  On entry
-// the caller guarantees the block is done reading the exchange storage from any earlier use.
-template <int N, int E, bool INV, int S = 0, typename T2, typename ACC, typename TW>
+// Full transform of one column through the accessor `acc`.  WARP = false synchronises the block
+// between exchange writes and reads; WARP = true only the warp (the column's TPC = 32 threads are
+// one warp and its exchange storage is private to it).  On entry the caller guarantees that the
+// exchange storage is no longer being read from any earlier use.
+template <int N, int E, bool INV, int S = 0, bool WARP = false, typename T2, typename ACC, typename TW>
 __device__ __forceinline__ void fft_column_acc(T2 (&x)[E], int t, const ACC& acc, const TW& tw) {
   if constexpr (S < num_stages(N)) {
     fft_stage<N, E, S, INV>(x, t, tw);
@@ -206,12 +208,12 @@ __device__ __forceinline__ void fft_column_acc(T2 (&x)[E], int t, const ACC& acc
       for (int q = 0; q < Q; ++q)
 #pragma unroll
         for (int r = 0; r < R; ++r) acc.put(stage_out_pos<N, E, S>(t, q, r), x[q + r * Q]);
-      __syncthreads();
+      if constexpr (WARP) __syncwarp(); else __syncthreads();
       constexpr int TPC = N / E;
 #pragma unroll
       for (int e = 0; e < E; ++e) x[e] = acc.get(t + TPC * e);
-      __syncthreads();
-      fft_column_acc<N, E, INV, S + 1>(x, t, acc, tw);
+      if constexpr (WARP) __syncwarp(); else __syncthreads();
+      fft_column_acc<N, E, INV, S + 1, WARP>(x, t, acc, tw);
     }
   }
 }

@@ -495,4 +495,183 @@ k_xproj_tma(const XTmaArgs a) {
   }
 }
 
+// ---- fused x pass, one warp per row -------------------------------------------------------
+//
+// A block holds one row pair: six warps, one per (row, component), each holding its row of N
+// points as 32 lanes x E = N / 32 registers.  The x transforms exchange through warp-private
+// shared rows (split real / imaginary, bank swizzle) with warp barriers only; the block meets
+// three times per row pair (rows read from the bulk-copy stage; forward results in place; modes
+// projected).  Rows arrive by cp.async.bulk into a single stage that is refilled for the next row
+// pair as soon as it has been read, and leave by cp.async.bulk stores from each warp's row.
+// Several blocks share an SM, so one block's barriers overlap the others' work.
+
+template <typename T, int N> struct XwCfg {
+  static constexpr int E = N / 32;
+  static constexpr int THREADS = 6 * 32;
+  static constexpr int TWS = staged_size(N);
+  static constexpr size_t ROWS_BYTES = 12 * sizeof(T) * size_t(N);      // 6 rows x (re, im)
+  static constexpr size_t SMEM = 256 + 2 * ROWS_BYTES + 2 * sizeof(T) * TWS + sizeof(T) * N;
+  static constexpr bool OK = (N == 256 || N == 512) && SMEM <= 227 * 1024;
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(XwCfg<T, N>::THREADS)
+k_xproj_warp(const XTmaArgs a) {
+  using C = XwCfg<T, N>;
+  using T2 = typename V2<T>::t;
+  constexpr int E = C::E, TWS = C::TWS;
+  extern __shared__ __align__(16) unsigned char smem_xw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_xw) + 127) & ~uintptr_t(127));
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(base);
+  T* stage = reinterpret_cast<T*>(base + 128);          // [warp][plane][N], bulk-copy target
+  T* rows = stage + 12 * N;                             // [warp][plane][N], exchange + store source
+  T* twc = rows + 12 * N;
+  T* tws = twc + TWS;
+  T* xix = tws + TWS;
+  __shared__ double red[32 * 4];
+  __shared__ int abort_flag;
+  __shared__ int rinfo[2][6];                           // rowA, rowB, self, valid, kz, ky
+  __shared__ T rxi[2][2];                               // Xi_y(ky), Xi_z(kz)
+
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int side = w / 3, comp = w % 3;
+  for (int i = tid; i < TWS; i += blockDim.x) {
+    twc[i] = reinterpret_cast<const T*>(a.tws)[i];
+    tws[i] = reinterpret_cast<const T*>(a.tws)[TWS + i];
+  }
+  for (int i = tid; i < N; i += blockDim.x) xix[i] = reinterpret_cast<const T*>(a.xi_x)[i];
+  if (tid == 0) {
+    abort_flag = 0;
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const TwStaged<T> tw{twc, tws};
+  const T* xiy = reinterpret_cast<const T*>(a.xi_y);
+  const T* xiz = reinterpret_cast<const T*>(a.xi_z);
+  const int field = blockIdx.y;
+  T* fdata = reinterpret_cast<T*>(a.data) + field * a.field_stride;
+  const double* mean = a.mean ? a.mean + field * 6 : nullptr;
+  T* wre = rows + (2 * w) * N;
+  T* wim = wre + N;
+  const SoaAcc<T> acc{wre, wim};
+  const T inv_v = T(a.inv_v);
+  const double vol = 1.0 / a.inv_v;
+
+  // thread 0: rows of row pair g into info slot s, then stream them into the stage
+  int issued = 0;
+  auto issue = [&](int g, int s) {
+    const int rA = a.pairs[g];
+    const int kz = rA / a.ny, ky = rA - kz * a.ny;
+    const int rB = (kz == 0 ? 0 : a.nz - kz) * a.ny + (ky == 0 ? 0 : a.ny - ky);
+    rinfo[s][0] = rA; rinfo[s][1] = rB; rinfo[s][2] = rA == rB; rinfo[s][3] = 1;
+    rinfo[s][4] = kz; rinfo[s][5] = ky;
+    rxi[s][0] = xiy[ky];
+    rxi[s][1] = xiz[kz];
+    const int nrows = rA == rB ? 3 : 6;
+    ++issued;
+    mbar_expect_tx(bar, (unsigned)(nrows * 2 * N * sizeof(T)));
+    for (int r = 0; r < nrows; ++r) {
+      const int row = r < 3 ? rA : rB, c = r % 3;
+      for (int pl = 0; pl < 2; ++pl)
+        bulk_load(stage + (2 * r + pl) * N, fdata + (2LL * c + pl) * a.V + (long long)row * N,
+                  N * sizeof(T), bar);
+    }
+  };
+  __syncthreads();
+  const int first = blockIdx.x, step = gridDim.x;
+  if (tid == 0 && first < a.npairs) issue(first, 0);
+
+  Kahan<T> r2, di2, do2, o2;
+  int k = 0;
+  for (int g = first; g < a.npairs; g += step, ++k) {
+    const int s = k & 1;
+    if (!mbar_wait(bar, k & 1)) {
+      atomicOr(a.err, 1);
+      abort_flag = 1;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    const bool self = rinfo[s][2];
+    const bool active = !(side == 1 && self);
+    T2 x[E];
+    {
+      const T* sre = stage + (2 * w) * N;
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        x[e] = active ? T2{sre[lane + 32 * e], sre[N + lane + 32 * e]} : T2{T(0), T(0)};
+    }
+    __syncthreads();                                    // stage free: refill for the next pair
+    if (tid == 0 && g + step < a.npairs) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(g + step, s ^ 1);
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    __syncwarp();                                       // this warp's row no longer being stored
+    fft_column_acc<N, E, false, 0, true>(x, lane, acc, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc.put(lane + 32 * e, x[e]);
+    __syncthreads();
+    const int rA = rinfo[s][0];
+    for (int kx = tid; kx < N; kx += blockDim.x) {
+      const int kxm = kx == 0 ? 0 : N - kx;
+      if (self && kx > kxm) continue;
+      const int ja = swz(kx), jb = swz(kxm);
+      T2 av[3], bv[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T* ra = rows + (2 * c) * N;
+        const T* rb = rows + (2 * (self ? c : 3 + c)) * N;
+        av[c] = T2{ra[ja], ra[N + ja]};
+        bv[c] = T2{rb[jb], rb[N + jb]};
+      }
+      const bool selfmode = self && kx == kxm;
+      project_pair<T>(av, bv, xix[kx], rxi[s][0], rxi[s][1], rA == 0 && kx == 0, mean, vol,
+                      a.nyq_zero != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T* ra = rows + (2 * c) * N;
+        T* rb = rows + (2 * (self ? c : 3 + c)) * N;
+        ra[ja] = av[c].x;
+        ra[N + ja] = av[c].y;
+        if (!selfmode) {
+          rb[jb] = bv[c].x;
+          rb[N + jb] = bv[c].y;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = acc.get(lane + 32 * e);
+    __syncwarp();
+    fft_column_acc<N, E, true, 0, true>(x, lane, acc, tw);
+    // results in natural order (unswizzled) into this warp's row, then one bulk store per plane
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      wre[lane + 32 * e] = x[e].x;
+      wim[lane + 32 * e] = x[e].y;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0 && active) {
+      const int row = side == 0 ? rA : rinfo[s][1];
+      bulk_store(fdata + (2LL * comp) * a.V + (long long)row * N, wre, N * sizeof(T));
+      bulk_store(fdata + (2LL * comp + 1) * a.V + (long long)row * N, wim, N * sizeof(T));
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+  }
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  if (abort_flag) {
+    if (tid == 0 && issued > 0) mbar_wait(bar, (unsigned)((issued - 1) & 1));
+    __syncthreads();
+    return;
+  }
+  double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
+  block_sum<4>(v, red);
+  if (tid == 0) {
+    double* q = a.partials + ((long long)field * gridDim.x + blockIdx.x) * 4;
+    q[0] = v[0]; q[1] = v[1]; q[2] = v[2]; q[3] = v[3];
+  }
+}
+
 }  // namespace eqk
