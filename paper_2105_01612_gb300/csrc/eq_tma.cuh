@@ -92,10 +92,12 @@ struct TmaArgs {
   long long ntiles;        // tiles per (field, component)
 };
 
-// MODE: 0 middle pass, 1 first pass (input statistics), 2 last pass (L-inf against a.ref)
+// MODE: 0 middle pass, 1 first pass (input statistics), 2 last pass (L-inf against a.ref, whose
+// tile streams through `refmap` into the stage the transform has just read, while it computes)
 template <typename T, int N, bool INV, int MODE, int V>
 __global__ void __launch_bounds__(TmaCfg<T, N, V>::THREADS, TmaCfg<T, N, V>::MINB)
-k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
+k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap refmap,
+              const TmaArgs a) {
   using C = TmaCfg<T, N, V>;
   using T2 = typename C::T2;
   constexpr int E = C::E, TPC = C::TPC, B = C::B, BOX = C::BOX, NBOX = C::NBOX;
@@ -132,7 +134,7 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
 
   // coordinates of tile u: (x0, row) with row = y (z pass) or z (y pass)
   int issued0 = 0, issued1 = 0;                        // loads issued per stage (thread 0)
-  auto issue = [&](long long u, int s) {
+  auto issue = [&](long long u, int s, const CUtensorMap* m) {
     const int x0 = (int)(u % tiles_x) * B;
     const int row = (int)(u / tiles_x);
     if (s) ++issued1; else ++issued0;
@@ -142,15 +144,17 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
 #pragma unroll
       for (int q = 0; q < NBOX; ++q) {
         T* dst = stage0 + s * 2 * N * B + p * N * B + q * BOX * B;
-        if (a.axis == 2) tma_load_4d(dst, &map, &bar[s], x0, row, q * BOX, plane_re + p);
-        else tma_load_4d(dst, &map, &bar[s], x0, q * BOX, row, plane_re + p);
+        if (a.axis == 2) tma_load_4d(dst, m, &bar[s], x0, row, q * BOX, plane_re + p);
+        else tma_load_4d(dst, m, &bar[s], x0, q * BOX, row, plane_re + p);
       }
   };
+  const bool with_ref = MODE == 2 && ref_re != nullptr;
+  int ph0 = 0, ph1 = 0;                                  // completed phases per stage
 
   const long long first = blockIdx.x, step = gridDim.x;
   if (tid == 0) {
-    if (first < a.ntiles) issue(first, 0);
-    if (first + step < a.ntiles) issue(first + step, 1);
+    if (first < a.ntiles) issue(first, 0, &map);
+    if (first + step < a.ntiles) issue(first + step, 1, &map);
   }
 
   Kahan<T> sa, sb, sq;
@@ -159,10 +163,12 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
   int k = 0;
   for (long long u = first; u < a.ntiles; u += step, ++k) {
     const int s = k & 1;
-    if (!mbar_wait(&bar[s], (k >> 1) & 1)) {
+    // one thread polls the barrier; the block barrier then publishes the stage to everyone
+    if (tid == 0 && !mbar_wait(&bar[s], (unsigned)((s ? ph1 : ph0) & 1))) {
       atomicOr(a.err, 1);
       abort_flag = 1;
     }
+    if (s) ++ph1; else ++ph0;
     __syncthreads();
     if (abort_flag) break;
     T2 x[E];
@@ -171,9 +177,10 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
 #pragma unroll
     for (int e = 0; e < E; ++e) x[e] = T2{sre[(t + TPC * e) * B + b], sim[(t + TPC * e) * B + b]};
     __syncthreads();                                   // stage s is free again
-    if (tid == 0 && u + 2 * step < a.ntiles) {
+    if (tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(u + 2 * step, s);
+      if (with_ref) issue(u, s, &refmap);              // this tile's input, for the residual
+      else if (u + 2 * step < a.ntiles) issue(u + 2 * step, s, &map);
     }
     if constexpr (MODE == 1) {
 #pragma unroll
@@ -193,10 +200,26 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const TmaArgs a) {
       const long long off = col0 + (long long)(t + TPC * e) * nstride;
       out_re[off] = x[e].x;
       out_im[off] = x[e].y;
-      if constexpr (MODE == 2) {
-        if (ref_re) {
-          linf = fmax(linf, fabs(ref_re[off] - x[e].x));
-          linf = fmax(linf, fabs(ref_re[off + a.V] - x[e].y));
+    }
+    if constexpr (MODE == 2) {
+      if (with_ref) {
+        if (tid == 0 && !mbar_wait(&bar[s], (unsigned)((s ? ph1 : ph0) & 1))) {
+          atomicOr(a.err, 1);
+          abort_flag = 1;
+        }
+        if (s) ++ph1; else ++ph0;
+        __syncthreads();
+        if (abort_flag) break;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          linf = fmax(linf, fabs(sre[(t + TPC * e) * B + b] - x[e].x));
+          linf = fmax(linf, fabs(sim[(t + TPC * e) * B + b] - x[e].y));
+        }
+        __syncthreads();                               // stage s read: refill with tile k + 2
+        if (abort_flag) break;
+        if (tid == 0 && u + 2 * step < a.ntiles) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(u + 2 * step, s, &map);
         }
       }
     }
@@ -387,7 +410,7 @@ k_xproj_tma(const XTmaArgs a) {
       rxi[s][tid][0] = xiy[ky];
       rxi[s][tid][1] = xiz[kz];
     }
-    if (!mbar_wait(&bar[s], (k >> 1) & 1)) {
+    if (tid == 0 && !mbar_wait(&bar[s], (k >> 1) & 1)) {
       atomicOr(a.err, 1);
       abort_flag = 1;
     }
@@ -586,7 +609,7 @@ k_xproj_warp(const XTmaArgs a) {
   int k = 0;
   for (int g = first; g < a.npairs; g += step, ++k) {
     const int s = k & 1;
-    if (!mbar_wait(bar, k & 1)) {
+    if (tid == 0 && !mbar_wait(bar, k & 1)) {
       atomicOr(a.err, 1);
       abort_flag = 1;
     }
