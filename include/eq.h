@@ -73,7 +73,8 @@ typedef struct {
   int flags;             /* EQ_FLAG_* */
 } eq_norms_t;
 
-#define EQ_FLAG_NONFINITE 1   /* the input held a NaN or an infinity */
+#define EQ_FLAG_NONFINITE 1   /* the input held a NaN or an infinity, or a partial sum of it
+                                 overflowed the working type (inputs near FLT_MAX in FP32) */
 #define EQ_FLAG_NO_LINF 2     /* resid_linf was not computed (in-place call or want_linf = 0) */
 
 typedef struct eq_plan eq_plan;

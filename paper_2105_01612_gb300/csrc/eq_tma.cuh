@@ -183,13 +183,20 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
       else if (u + 2 * step < a.ntiles) issue(u + 2 * step, s, &map);
     }
     if constexpr (MODE == 1) {
+      // plain sums over the thread's E points, compensated across tiles.  A NaN or infinity in
+      // any point makes its tile sum non-finite (so does a sum beyond the type's range, which
+      // the flag then reports as well)
+      T ta = T(0), tb = T(0), tq = T(0);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        if (!isfinite(x[e].x) || !isfinite(x[e].y)) nonfinite += T(1);
-        sa.add(x[e].x);
-        sb.add(x[e].y);
-        sq.add(wa * x[e].x * x[e].x + wb * x[e].y * x[e].y);
+        ta += x[e].x;
+        tb += x[e].y;
+        tq += wa * x[e].x * x[e].x + wb * x[e].y * x[e].y;
       }
+      if (!isfinite(ta) || !isfinite(tb)) nonfinite += T(1);
+      sa.add(ta);
+      sb.add(tb);
+      sq.add(tq);
     }
     fft_column<N, E, INV>(x, t, xbuf, idx, tw);
     const int x0 = (int)(u % tiles_x) * B;
