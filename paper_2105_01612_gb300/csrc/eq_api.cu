@@ -606,17 +606,17 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
     p->tma_allow = !(no_tma && no_tma[0] == '1') && encode_fn() != nullptr &&
                    ((size_t)nx * p->esize) % 16 == 0;
     int gmax_z = 1, gmax_x = 1;
-    for (int v = 2; v >= 0; --v) {
+    for (int v = 3; v >= 0; --v) {
       tma_setup(p, v == 1, v == 1, v);
       gmax_z = std::max(gmax_z, std::max(p->gtz, p->gty));
       gmax_x = std::max(gmax_x, p->gtx);
     }
-    // defaults measured on GB300 at 512^3: wide tiles for the strided passes, one row pair per
-    // block with two blocks per SM for the x pass (eq_plan_autotune re-decides per plan)
+    // defaults measured on GB300 at 256^3 and 512^3: wide tiles for the strided passes, the
+    // warp-per-row x pass compiled for four blocks per SM (eq_plan_autotune re-decides per plan)
     const char* vs = getenv("EQ_TMA_VARIANT");
     const char* vxs = getenv("EQ_X_VARIANT");
     const int v0 = (vs && vs[0] == '1') ? 1 : 0;
-    const int vx0 = vxs && vxs[0] >= '0' && vxs[0] <= '2' ? vxs[0] - '0' : 2;
+    const int vx0 = vxs && vxs[0] >= '0' && vxs[0] <= '3' ? vxs[0] - '0' : 3;
     tma_setup(p, v0, v0, vx0);
     for (int v = vx0 - 1; !p->tma_x && v >= 0; --v) tma_setup(p, v0, v0, v);   // fall back
     p->gtz_max = gmax_z;
@@ -818,14 +818,17 @@ eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stre
   cudaEvent_t ev[EQ_NUM_PASSES + 1];
   for (auto& x : ev)
     if ((e = cudaEventCreate(&x)) != cudaSuccess) return fail_cuda(e, "eq_plan_autotune: events");
-  float ms[4][EQ_NUM_PASSES] = {};
-  bool ok[4][3] = {};                                   // [config][axis z, y, x] available
+  constexpr int NCFG = 5;
+  float ms[NCFG][EQ_NUM_PASSES] = {};
+  bool ok[NCFG][3] = {};                                // [config][axis z, y, x] available
   const int saved_cap = p->tcap, saved_used = p->tused;
-  // configs: 0 wide tiles, 1 narrow tiles, 2 plain kernels, 3 warp-per-row x pass
-  for (int cfg = 0; cfg < 4; ++cfg) {
-    tma_setup(p, cfg == 1, cfg == 1, cfg == 1 ? 1 : (cfg == 3 ? 2 : 0));
+  // configs: 0 wide tiles, 1 narrow tiles, 2 plain kernels, 3 and 4 warp-per-row x pass (one
+  // and four blocks per SM asked of the register allocator); x variant of each config:
+  auto xvar = [](int cfg) { return cfg == 1 ? 1 : (cfg >= 3 ? cfg - 1 : 0); };
+  for (int cfg = 0; cfg < NCFG; ++cfg) {
+    tma_setup(p, cfg == 1, cfg == 1, xvar(cfg));
     if (cfg == 2) p->tma_z = p->tma_y = p->tma_x = false;
-    if (cfg == 3) p->tma_z = p->tma_y = false;
+    if (cfg >= 3) p->tma_z = p->tma_y = false;
     ok[cfg][0] = cfg == 2 || p->tma_z;
     ok[cfg][1] = cfg == 2 || p->tma_y;
     ok[cfg][2] = cfg == 2 || p->tma_x;
@@ -851,8 +854,8 @@ eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stre
   };
   const int bz = pick(0, 2, [](const float* m) { return m[0] + m[5]; });
   const int by = pick(1, 2, [](const float* m) { return m[2] + m[4]; });
-  const int bx = pick(2, 4, [](const float* m) { return m[3]; });
-  tma_setup(p, bz == 1, by == 1, bx == 3 ? 2 : (bx == 1 ? 1 : 0));
+  const int bx = pick(2, NCFG, [](const float* m) { return m[3]; });
+  tma_setup(p, bz == 1, by == 1, xvar(bx));
   if (bz == 2) p->tma_z = false;
   if (by == 2) p->tma_y = false;
   if (bx == 2) p->tma_x = false;

@@ -105,9 +105,9 @@ template <typename T, int N, int V> struct XTmaInst {
   }
 };
 
-template <typename T, int N> struct XwInst {
+template <typename T, int N, int MINB> struct XwInst {
   static cudaError_t info(TmaInfo* out) {
-    using C = XwCfg<T, N>;
+    using C = XwCfg<T, N, MINB>;
     if constexpr (!C::OK) {
       return cudaErrorInvalidValue;
     } else {
@@ -115,8 +115,11 @@ template <typename T, int N> struct XwInst {
       out->cols = 1;
       out->box = 0;
       out->smem = C::SMEM;
-      const void* f = reinterpret_cast<const void*>(&k_xproj_warp<T, N>);
+      const void* f = reinterpret_cast<const void*>(&k_xproj_warp<T, N, MINB>);
       cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
       int bl = 0;
       if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, f, C::THREADS, C::SMEM);
       out->blocks_per_sm = bl;
@@ -124,15 +127,21 @@ template <typename T, int N> struct XwInst {
     }
   }
   static cudaError_t launch(const XTmaArgs& a, dim3 grid, cudaStream_t s) {
-    using C = XwCfg<T, N>;
+    using C = XwCfg<T, N, MINB>;
     if constexpr (!C::OK) {
       return cudaErrorInvalidValue;
     } else {
-      k_xproj_warp<T, N><<<grid, C::THREADS, C::SMEM, s>>>(a);
+      k_xproj_warp<T, N, MINB><<<grid, C::THREADS, C::SMEM, s>>>(a);
       return cudaGetLastError();
     }
   }
 };
+
+// blocks per SM asked of the register allocator for the warp-per-row x pass: FP32 variants 2 and
+// 3 target three and four blocks; FP64 rows take twice the shared memory, so one and two
+template <typename T> constexpr int XW_MINB(int fp32_blocks) {
+  return sizeof(T) == 4 ? fp32_blocks : fp32_blocks - 2;
+}
 
 #define EQ_FOR_LENGTHS(X) X(1) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
@@ -188,8 +197,9 @@ template <typename T> cudaError_t xtma_info_t(int n, int v, TmaInfo* out) {
   switch (n) {
 #define EQ_CASE(N)                                              \
   case N:                                                         \
-    return v == 2 ? XwInst<T, N>::info(out)                       \
-                  : (v ? XTmaInst<T, N, 1>::info(out) : XTmaInst<T, N, 0>::info(out));
+    return v == 3   ? XwInst<T, N, XW_MINB<T>(4)>::info(out)                  \
+           : v == 2 ? XwInst<T, N, XW_MINB<T>(3)>::info(out)                  \
+                    : (v ? XTmaInst<T, N, 1>::info(out) : XTmaInst<T, N, 0>::info(out));
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;
@@ -199,8 +209,9 @@ template <typename T> cudaError_t xtma_launch_t(int n, int v, const XTmaArgs& a,
   switch (n) {
 #define EQ_CASE(N)                                                       \
   case N:                                                                  \
-    return v == 2 ? XwInst<T, N>::launch(a, grid, s)                       \
-                  : (v ? XTmaInst<T, N, 1>::launch(a, grid, s) : XTmaInst<T, N, 0>::launch(a, grid, s));
+    return v == 3   ? XwInst<T, N, XW_MINB<T>(4)>::launch(a, grid, s)                  \
+           : v == 2 ? XwInst<T, N, XW_MINB<T>(3)>::launch(a, grid, s)                  \
+                    : (v ? XTmaInst<T, N, 1>::launch(a, grid, s) : XTmaInst<T, N, 0>::launch(a, grid, s));
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;

@@ -231,6 +231,7 @@ __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T x
   }
   const T k2 = xi0 * xi0 + xi1 * xi1 + xi2 * xi2;
   T orr[6], oi[6];
+  T din = T(0);                        // |xi . S^|^2 = k2 |S^ n|^2
   if (k2 > T(0)) {
     const T rn = rsqrt_t(k2);
     const T n0 = xi0 * rn, n1 = xi1 * rn, n2 = xi2 * rn;
@@ -241,6 +242,7 @@ __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T x
       const T v1 = S[5] * n0 + S[1] * n1 + S[3] * n2;                          \
       const T v2 = S[4] * n0 + S[3] * n1 + S[2] * n2;                          \
       const T s = n0 * v0 + n1 * v1 + n2 * v2;                                 \
+      din += k2 * (v0 * v0 + v1 * v1 + v2 * v2);                               \
       O[0] = S[0] - T(2) * n0 * v0 + s * n0 * n0;                              \
       O[1] = S[1] - T(2) * n1 * v1 + s * n1 * n1;                              \
       O[2] = S[2] - T(2) * n2 * v2 + s * n2 * n2;                              \
@@ -269,7 +271,7 @@ __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T x
       rr += w * (dr * dr + dii * dii);
       oo += w * (orr[j] * orr[j] + oi[j] * oi[j]);
     }
-    T din = T(0), dout = T(0);
+    T dout = T(0);
 #define EQ_DIV(S, ACC)                                                          \
     {                                                                          \
       const T d0 = xi0 * S[0] + xi1 * S[5] + xi2 * S[4];                       \
@@ -277,7 +279,7 @@ __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T x
       const T d2 = xi0 * S[4] + xi1 * S[3] + xi2 * S[2];                       \
       ACC += d0 * d0 + d1 * d1 + d2 * d2;                                      \
     }
-    EQ_DIV(sr, din) EQ_DIV(si, din) EQ_DIV(orr, dout) EQ_DIV(oi, dout)
+    EQ_DIV(orr, dout) EQ_DIV(oi, dout)
 #undef EQ_DIV
     r2.add(mult * rr);
     o2.add(mult * oo);

@@ -535,7 +535,7 @@ k_xproj_tma(const XTmaArgs a) {
 // pair as soon as it has been read, and leave by cp.async.bulk stores from each warp's row.
 // Several blocks share an SM, so one block's barriers overlap the others' work.
 
-template <typename T, int N> struct XwCfg {
+template <typename T, int N, int MINB = 1> struct XwCfg {
   static constexpr int E = N / 32;
   static constexpr int THREADS = 6 * 32;
   static constexpr int TWS = staged_size(N);
@@ -544,10 +544,10 @@ template <typename T, int N> struct XwCfg {
   static constexpr bool OK = (N == 256 || N == 512) && SMEM <= 227 * 1024;
 };
 
-template <typename T, int N>
-__global__ void __launch_bounds__(XwCfg<T, N>::THREADS)
+template <typename T, int N, int MINB>
+__global__ void __launch_bounds__(XwCfg<T, N, MINB>::THREADS, MINB)
 k_xproj_warp(const XTmaArgs a) {
-  using C = XwCfg<T, N>;
+  using C = XwCfg<T, N, MINB>;
   using T2 = typename V2<T>::t;
   constexpr int E = C::E, TWS = C::TWS;
   extern __shared__ __align__(16) unsigned char smem_xw[];
