@@ -36,24 +36,28 @@ void set_last_error(const std::string& msg) { g_last_error = msg; }
 // ---------------------------------------------------------------- finalisation kernels
 
 // c0 and ||S_in||^2 per field from the first pass's block partials (fixed order, FP64).
+// One block per field; each thread sums a fixed stride of the block partials in order, then a
+// fixed shuffle/shared-memory tree: the result does not depend on timing.
 __global__ void k_finalize_mean(const double* __restrict__ part, int grid, int batch, double vol,
                                 double* __restrict__ mean, double* __restrict__ instats) {
-  for (int f = threadIdx.x; f < batch; f += blockDim.x) {
-    double sq = 0.0, nf = 0.0;
-    for (int c = 0; c < 3; ++c) {
-      double sa = 0.0, sb = 0.0;
-      const double* p = part + ((long long)(f * 3 + c) * grid) * 4;
-      for (int g = 0; g < grid; ++g) {
-        sa += p[g * 4 + 0];
-        sb += p[g * 4 + 1];
-        sq += p[g * 4 + 2];
-        nf += p[g * 4 + 3];
-      }
-      mean[f * 6 + 2 * c] = sa / vol;
-      mean[f * 6 + 2 * c + 1] = sb / vol;
+  __shared__ double red[32 * 8];
+  const int f = blockIdx.x;
+  if (f >= batch) return;
+  double v[8] = {};                                  // sa, sb of each component, sq, nonfinite
+  for (int c = 0; c < 3; ++c) {
+    const double* p = part + ((long long)(f * 3 + c) * grid) * 4;
+    for (int g = threadIdx.x; g < grid; g += blockDim.x) {
+      v[2 * c] += p[g * 4 + 0];
+      v[2 * c + 1] += p[g * 4 + 1];
+      v[6] += p[g * 4 + 2];
+      v[7] += p[g * 4 + 3];
     }
-    instats[f * 2 + 0] = sq;
-    instats[f * 2 + 1] = nf;
+  }
+  eqk::block_sum<8>(v, red);
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < 6; ++j) mean[f * 6 + j] = v[j] / vol;
+    instats[f * 2 + 0] = v[6];
+    instats[f * 2 + 1] = v[7];
   }
 }
 
@@ -63,29 +67,30 @@ __global__ void k_finalize_norms(const double* __restrict__ partx, int gridx,
                                  double vol, const double* __restrict__ mean,
                                  const double* __restrict__ instats, int linf_flag,
                                  eq_norms_t* __restrict__ out) {
-  for (int f = threadIdx.x; f < batch; f += blockDim.x) {
-    double r2 = 0.0, di = 0.0, dout = 0.0, o2 = 0.0;
-    const double* p = partx + (long long)f * gridx * 4;
-    for (int g = 0; g < gridx; ++g) {
-      r2 += p[g * 4 + 0];
-      di += p[g * 4 + 1];
-      dout += p[g * 4 + 2];
-      o2 += p[g * 4 + 3];
-    }
+  __shared__ double red[32 * 4];
+  const int f = blockIdx.x;
+  if (f >= batch) return;
+  double v[4] = {};                                  // r2, div in, div out, o2
+  const double* p = partx + (long long)f * gridx * 4;
+  for (int g = threadIdx.x; g < gridx; g += blockDim.x)
+    for (int j = 0; j < 4; ++j) v[j] += p[g * 4 + j];
+  eqk::block_sum<4>(v, red);
+  double lm = 0.0;
+  if (partl) {
+    const double* q = partl + (long long)f * 3 * gridl;
+    for (int g = threadIdx.x; g < 3 * gridl; g += blockDim.x) lm = fmax(lm, q[g]);
+  }
+  lm = eqk::block_max(lm, red);
+  if (threadIdx.x == 0) {
     const double v2 = vol * vol;
     eq_norms_t n;
     for (int j = 0; j < 6; ++j) n.mean[j] = mean[f * 6 + j];
     n.norm_in = sqrt(instats[f * 2 + 0] / vol);
-    n.norm_out = sqrt(o2 / v2);
-    n.resid_l2 = sqrt(r2 / v2);
+    n.norm_out = sqrt(v[3] / v2);
+    n.resid_l2 = sqrt(v[0] / v2);
     n.resid_rel = n.norm_in > 0.0 ? n.resid_l2 / n.norm_in : 0.0;
-    n.div_in_l2 = sqrt(di / v2);
-    n.div_out_l2 = sqrt(dout / v2);
-    double lm = 0.0;
-    if (partl) {
-      const double* q = partl + (long long)f * 3 * gridl;
-      for (int g = 0; g < 3 * gridl; ++g) lm = fmax(lm, q[g]);
-    }
+    n.div_in_l2 = sqrt(v[1] / v2);
+    n.div_out_l2 = sqrt(v[2] / v2);
     n.resid_linf = lm;
     n.flags = (instats[f * 2 + 1] > 0.0 ? EQ_FLAG_NONFINITE : 0) | linf_flag;
     out[f] = n;
@@ -95,13 +100,13 @@ __global__ void k_finalize_norms(const double* __restrict__ partx, int gridx,
 namespace eqk {
 void finalize_mean(const double* part, int grid, int batch, double vol, double* mean,
                    double* instats, cudaStream_t s) {
-  k_finalize_mean<<<1, 128, 0, s>>>(part, grid, batch, vol, mean, instats);
+  k_finalize_mean<<<batch, 256, 0, s>>>(part, grid, batch, vol, mean, instats);
 }
 void finalize_norms(const double* partx, int gridx, const double* partl, int gridl, int batch,
                     double vol, const double* mean, const double* instats, int linf_flag,
                     eq_norms_t* out, cudaStream_t s) {
-  k_finalize_norms<<<1, 128, 0, s>>>(partx, gridx, partl, gridl, batch, vol, mean, instats,
-                                     linf_flag, out);
+  k_finalize_norms<<<batch, 256, 0, s>>>(partx, gridx, partl, gridl, batch, vol, mean, instats,
+                                         linf_flag, out);
 }
 }  // namespace eqk
 
@@ -340,8 +345,8 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     if (e != cudaSuccess) return fail_cuda(e, "z forward pass");
   }
   mark(1);
-  k_finalize_mean<<<1, 128, 0, s>>>(p->part1, gz_used, p->batch, double(V),
-                                    p->mean, p->instats);
+  k_finalize_mean<<<p->batch, 256, 0, s>>>(p->part1, gz_used, p->batch, double(V),
+                                           p->mean, p->instats);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "mean finalisation");
   mark(2);
   // pass 2: y forward
@@ -398,6 +403,7 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     if (e != cudaSuccess) return fail_cuda(e, "x projection pass");
   }
   mark(4);
+  const bool linf = p->opts.want_linf && d_in != d_out;
   // pass 4: y inverse
   {
     dim3 grid(p->gy, p->batch * 3);
@@ -408,7 +414,6 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
   }
   mark(5);
   // pass 5: z inverse (+ residual L-inf against d_in)
-  const bool linf = p->opts.want_linf && d_in != d_out;
   {
     eqk::StridedArgs az = a;
     az.in = d_out; az.out = d_out; az.ref = linf ? d_in : nullptr;
@@ -420,9 +425,9 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     if (e != cudaSuccess) return fail_cuda(e, "z inverse pass");
   }
   mark(6);
-  k_finalize_norms<<<1, 128, 0, s>>>(p->partx, gx_used, linf ? p->partl : nullptr, gl_used, p->batch,
-                                     double(V), p->mean, p->instats, linf ? 0 : EQ_FLAG_NO_LINF,
-                                     p->norms);
+  k_finalize_norms<<<p->batch, 256, 0, s>>>(p->partx, gx_used, linf ? p->partl : nullptr, gl_used,
+                                            p->batch, double(V), p->mean, p->instats,
+                                            linf ? 0 : EQ_FLAG_NO_LINF, p->norms);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "norm finalisation");
   mark(7);
   return EQ_OK;
@@ -802,6 +807,22 @@ eq_status eq_plan_pass_ms(eq_plan* p, double* ms_out, int* ncalls_out) {
   return EQ_OK;
 }
 
+// Per-pass times (ms) of the second of two direct runs with the plan's current choices.
+eq_status time_passes(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, cudaEvent_t* ev,
+                      float* ms) {
+  for (int rep = 0; rep < 2; ++rep) {
+    std::vector<cudaEvent_t> keep(p->tev);
+    p->tev.assign(ev, ev + EQ_NUM_PASSES + 1);
+    p->tcap = 1; p->tused = 0;
+    eq_status st = enqueue(p, d_in, d_out, s);
+    p->tev.swap(keep);
+    if (st != EQ_OK) return st;
+    cudaEventSynchronize(ev[EQ_NUM_PASSES]);
+    for (int i = 0; i < EQ_NUM_PASSES; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+  }
+  return EQ_OK;
+}
+
 eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stream) {
   if (!p || !d_in || !d_out) return fail(EQ_ERR_INVALID, "eq_plan_autotune: NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -832,19 +853,13 @@ eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stre
     ok[cfg][0] = cfg == 2 || p->tma_z;
     ok[cfg][1] = cfg == 2 || p->tma_y;
     ok[cfg][2] = cfg == 2 || p->tma_x;
-    for (int rep = 0; rep < 2; ++rep) {
-      std::vector<cudaEvent_t> keep(p->tev);
-      p->tev.assign(ev, ev + EQ_NUM_PASSES + 1);
-      p->tcap = 1; p->tused = 0;
-      eq_status st = enqueue(p, d_in, d_out, s);
-      p->tev.swap(keep);
-      if (st != EQ_OK) { p->tcap = saved_cap; p->tused = saved_used; return st; }
-      cudaEventSynchronize(ev[EQ_NUM_PASSES]);
-      for (int i = 0; i < EQ_NUM_PASSES; ++i) cudaEventElapsedTime(&ms[cfg][i], ev[i], ev[i + 1]);
+    const eq_status st = time_passes(p, d_in, d_out, s, ev, ms[cfg]);
+    if (st != EQ_OK) {
+      p->tcap = saved_cap; p->tused = saved_used;
+      for (auto& x : ev) cudaEventDestroy(x);
+      return st;
     }
   }
-  p->tcap = saved_cap; p->tused = saved_used;
-  for (auto& x : ev) cudaEventDestroy(x);
   // pass indices: 0 z forward, 2 y forward, 3 x, 4 y inverse, 5 z inverse
   auto pick = [&](int axis, int ncfg, float (*cost)(const float*)) {
     int best = 2;
@@ -859,6 +874,8 @@ eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stre
   if (bz == 2) p->tma_z = false;
   if (by == 2) p->tma_y = false;
   if (bx == 2) p->tma_x = false;
+  p->tcap = saved_cap; p->tused = saved_used;
+  for (auto& x : ev) cudaEventDestroy(x);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "eq_plan_autotune");
   return EQ_OK;
 }

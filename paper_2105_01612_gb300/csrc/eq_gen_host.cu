@@ -308,7 +308,7 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
   g->opts = o;
   g->F = count;
   g->sms = sms;
-  const size_t es = dtype == EQ_F32 ? 4 : 8, cs = 2 * es;
+  const size_t es = dtype == EQ_F32 ? 4 : 8;
   std::vector<int> lens;
   for (int i = 0; i < 3 * count; ++i) lens.push_back(dims[i]);
   std::vector<unsigned char> cpool, xipool;
