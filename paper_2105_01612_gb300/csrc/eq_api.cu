@@ -210,11 +210,23 @@ template <typename T> void staged_twiddles(int n, std::vector<unsigned char>& ou
     ns *= R;
     ++st;
   }
-  out.resize(sizeof(T) * 2 * std::max<size_t>(1, c.size()));
+  // n = 512: the warp-per-row x pass factors 512 = 16 x 32 and takes W512^(l k1) as a table
+  // [k1][l] (k1 < 16, l < 32) of complex values after the per-stage tables
+  const size_t staged = sizeof(T) * 2 * std::max<size_t>(1, c.size());
+  out.resize(staged + (n == 512 ? 2 * sizeof(T) * 512 : 0));   // (read by the FP32 instance)
   T* o = reinterpret_cast<T*>(out.data());
   for (size_t i = 0; i < c.size(); ++i) {
     o[i] = T(c[i]);
     o[c.size() + i] = T(sn[i]);
+  }
+  if (n == 512) {
+    T* w = reinterpret_cast<T*>(out.data() + staged);
+    for (int k1 = 0; k1 < 16; ++k1)
+      for (int l = 0; l < 32; ++l) {
+        const double ang = -two_pi * double(l * k1) / 512.0;
+        w[2 * (k1 * 32 + l)] = T(std::cos(ang));
+        w[2 * (k1 * 32 + l) + 1] = T(std::sin(ang));
+      }
   }
 }
 

@@ -70,6 +70,84 @@ template <bool INV, typename T2> __device__ __forceinline__ void dft8(T2* v) {
   }
 }
 
+// cos(pi j / 16), j = 0..8; W32^q = cos(2 pi q / 32) -+ i sin(2 pi q / 32) follows by symmetry
+__host__ __device__ constexpr double cos_pi16(int j) {
+  constexpr double c[9] = {1.0,
+                           0.9807852804032304491262,
+                           0.9238795325112867561282,
+                           0.8314696123025452370788,
+                           0.7071067811865475244008,
+                           0.5555702330196022247428,
+                           0.3826834323650897717285,
+                           0.1950903220161282678483,
+                           0.0};
+  return j <= 8 ? c[j] : -c[16 - j];                // j in 0..16
+}
+__host__ __device__ constexpr double sin_pi16(int j) {  // j in 0..16
+  return j <= 8 ? cos_pi16(8 - j) : cos_pi16(j - 8);
+}
+// v * W32^q (forward: exp(-2 pi i q / 32); INV: the conjugate), q in 0..15, trivial q skip the
+// multiply
+template <int Q, bool INV, typename T2> __device__ __forceinline__ T2 mul_w32(T2 v) {
+  using T = decltype(v.x);
+  if constexpr (Q == 0) {
+    return v;
+  } else if constexpr (Q == 8) {
+    return mul_mi<INV>(v);
+  } else {
+    constexpr T c = T(cos_pi16(Q));
+    constexpr T s = INV ? T(sin_pi16(Q)) : T(-sin_pi16(Q));
+    return T2{v.x * c - v.y * s, v.x * s + v.y * c};
+  }
+}
+
+// v * W32^q for a q known after unrolling (dispatch to the constant forms)
+template <bool INV, typename T2> __device__ __forceinline__ T2 mul_w32_rt(int q, T2 v) {
+  switch (q) {
+    case 1: return mul_w32<1, INV>(v);
+    case 2: return mul_w32<2, INV>(v);
+    case 3: return mul_w32<3, INV>(v);
+    case 4: return mul_w32<4, INV>(v);
+    case 5: return mul_w32<5, INV>(v);
+    case 6: return mul_w32<6, INV>(v);
+    case 7: return mul_w32<7, INV>(v);
+    case 8: return mul_w32<8, INV>(v);
+    case 9: return mul_w32<9, INV>(v);
+    case 10: return mul_w32<10, INV>(v);
+    case 11: return mul_w32<11, INV>(v);
+    case 12: return mul_w32<12, INV>(v);
+    case 13: return mul_w32<13, INV>(v);
+    case 14: return mul_w32<14, INV>(v);
+    case 15: return mul_w32<15, INV>(v);
+    default: return v;
+  }
+}
+
+// radix 16 as two radix-8 transforms of the sums / W16-twiddled differences of v_m and v_{m+8};
+// outputs in natural order
+template <bool INV, typename T2> __device__ __forceinline__ void dft16(T2* v) {
+  T2 a[8], b[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    a[m] = cadd(v[m], v[m + 8]);
+    b[m] = csub(v[m], v[m + 8]);
+  }
+  b[1] = mul_w32<2, INV>(b[1]);
+  b[2] = mul_w32<4, INV>(b[2]);
+  b[3] = mul_w32<6, INV>(b[3]);
+  b[4] = mul_w32<8, INV>(b[4]);
+  b[5] = mul_w32<10, INV>(b[5]);
+  b[6] = mul_w32<12, INV>(b[6]);
+  b[7] = mul_w32<14, INV>(b[7]);
+  dft8<INV>(a);
+  dft8<INV>(b);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    v[2 * q] = a[q];
+    v[2 * q + 1] = b[q];
+  }
+}
+
 template <int R, bool INV, typename T2> __device__ __forceinline__ void dftR(T2* v) {
   if constexpr (R == 8) dft8<INV>(v);
   else if constexpr (R == 4) dft4<INV>(v);
@@ -179,6 +257,10 @@ template <typename T2, typename IDX> struct AosAcc {
 // with bits 5..7 of i, so the contiguous, stage-output and projector access patterns of a warp
 // (32 consecutive threads of one transform) touch 32 distinct banks.
 __host__ __device__ __forceinline__ int swz(int i) { return i ^ ((i >> 5) & 7) ^ (((i >> 6) & 3) << 3); }
+// Spectrum rows of the 512-point warp transform: element i at i ^ (bit 8 of i moved to bit 4), so
+// the transform's output stores (lanes 2 kap + h write kap + 16 q + 256 h), its input loads
+// (l + 32 e) and the projector's runs of 32 consecutive modes all touch 32 distinct banks.
+__host__ __device__ __forceinline__ int sx512(int i) { return i ^ (((i >> 8) & 1) << 4); }
 template <typename T> struct SoaAcc {
   T* re;
   T* im;
@@ -223,6 +305,56 @@ template <int N, int E, bool INV, typename T2, typename IDX>
 __device__ __forceinline__ void fft_column(T2 (&x)[E], int t, T2* buf, const IDX& idx,
                                            const T2* __restrict__ tw) {
   fft_column_acc<N, E, INV>(x, t, AosAcc<T2, IDX>{buf, idx}, TwPlain<T2>{tw});
+}
+
+// 512-point transform of one row held by one warp, lane l holding point l + 32 e in slot e
+// (e < 16).  With n = l + 32 e and k = k1 + 16 k2 (k1 < 16, k2 < 32):
+//   1. a 16-point DFT over e in registers: Y_l[k1];
+//   2. Y_l[k1] *= W512^(l k1) (tw = 16 x 32 table [k1][l] of the forward factors);
+//   3. one exchange through the warp's split re/im row (512 words each): Y_l[k1] stored at
+//      32 k1 + (l ^ 2 k1), so that both the store (fixed k1) and the load below hit 32 banks;
+//   4. lane L = 2 kap + h loads Y_{h + 2 m}[kap], m < 16, and takes a 16-point DFT over m:
+//      Z_h[q] for the even (h = 0) and odd (h = 1) halves of the 32-point DFT over l;
+//   5. lanes L and L ^ 1 combine by shuffle: X[kap + 16 q + 256 h] = Z_0[q] +- W32^q Z_1[q].
+// On return slot q of lane L holds output kap + 16 q + 256 h.  The caller guarantees that no lane
+// still reads the row on entry; the row is free again on return.
+template <bool INV, typename T, typename T2>
+__device__ __forceinline__ void fft512_warp(T2 (&v)[16], int lane, T* re, T* im,
+                                            const T2* __restrict__ tw) {
+  dft16<INV>(v);
+#pragma unroll
+  for (int k1 = 1; k1 < 16; ++k1) {
+    T2 w = tw[k1 * 32 + lane];
+    if (INV) w.y = -w.y;
+    v[k1] = cmul(v[k1], w);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) {
+    const int pos = k1 * 32 + (lane ^ (2 * k1));
+    re[pos] = v[k1].x;
+    im[pos] = v[k1].y;
+  }
+  __syncwarp();
+  const int kap = lane >> 1, h = lane & 1;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int pos = kap * 32 + h + 2 * (m ^ kap);
+    v[m] = T2{re[pos], im[pos]};
+  }
+  __syncwarp();
+  dft16<INV>(v);
+  const T sg = h ? T(-1) : T(1);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    // lane h = 1 sends W32^q Z_1[q], lane h = 0 sends Z_0[q]; each adds +- its own value
+    const T2 t = mul_w32_rt<INV>(q, v[q]);
+    const T2 send = h ? t : v[q];
+    T2 recv;
+    recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+    recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+    v[q] = T2{recv.x + sg * send.x, recv.y + sg * send.y};
+  }
 }
 
 // Kahan-compensated FP32/FP64 running sum (per-thread partial of a global FP64 reduction).

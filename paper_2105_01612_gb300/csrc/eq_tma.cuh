@@ -292,7 +292,8 @@ template <typename T, int N, int V = 0> struct XTmaCfg {
 
 struct XTmaArgs {
   void* data;
-  const void* tws;         // per-stage twiddles of the x length: cos[TWS] then sin[TWS]
+  const void* tws;         // per-stage twiddles of the x length: cos[TWS] then sin[TWS]; for
+                           // N = 512 followed by W512^(l k1) as complex [16][32]
   const void* xi_x;
   const void* xi_y;
   const void* xi_z;
@@ -539,8 +540,12 @@ template <typename T, int N, int MINB = 1> struct XwCfg {
   static constexpr int E = N / 32;
   static constexpr int THREADS = 6 * 32;
   static constexpr int TWS = staged_size(N);
+  // 16 x 32 transform (fft512_warp) in FP32; in FP64 (ALU-bound on GB300) the radix-8 stages
+  // measured faster
+  static constexpr bool F16 = N == 512 && sizeof(T) == 4;
   static constexpr size_t ROWS_BYTES = 12 * sizeof(T) * size_t(N);      // 6 rows x (re, im)
-  static constexpr size_t SMEM = 256 + 2 * ROWS_BYTES + 2 * sizeof(T) * TWS + sizeof(T) * N;
+  static constexpr size_t TW_BYTES = F16 ? 2 * sizeof(T) * 512 : 2 * sizeof(T) * TWS;
+  static constexpr size_t SMEM = 256 + 2 * ROWS_BYTES + TW_BYTES + sizeof(T) * N;
   static constexpr bool OK = (N == 256 || N == 512) && SMEM <= 227 * 1024;
 };
 
@@ -550,15 +555,17 @@ k_xproj_warp(const XTmaArgs a) {
   using C = XwCfg<T, N, MINB>;
   using T2 = typename V2<T>::t;
   constexpr int E = C::E, TWS = C::TWS;
+  constexpr bool F16 = C::F16;
   extern __shared__ __align__(16) unsigned char smem_xw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_xw) + 127) & ~uintptr_t(127));
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(base);
   T* stage = reinterpret_cast<T*>(base + 128);          // [warp][plane][N], bulk-copy target
   T* rows = stage + 12 * N;                             // [warp][plane][N], exchange + store source
-  T* twc = rows + 12 * N;
+  T* twc = rows + 12 * N;                               // staged cos, or the W512 table (F16)
   T* tws = twc + TWS;
-  T* xix = tws + TWS;
+  T2* tw16 = reinterpret_cast<T2*>(twc);
+  T* xix = F16 ? reinterpret_cast<T*>(tw16 + 512) : tws + TWS;
   __shared__ double red[32 * 4];
   __shared__ int abort_flag;
   __shared__ int rinfo[2][6];                           // rowA, rowB, self, valid, kz, ky
@@ -566,9 +573,14 @@ k_xproj_warp(const XTmaArgs a) {
 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int side = w / 3, comp = w % 3;
-  for (int i = tid; i < TWS; i += blockDim.x) {
-    twc[i] = reinterpret_cast<const T*>(a.tws)[i];
-    tws[i] = reinterpret_cast<const T*>(a.tws)[TWS + i];
+  if constexpr (F16) {
+    const T2* src = reinterpret_cast<const T2*>(reinterpret_cast<const T*>(a.tws) + 2 * TWS);
+    for (int i = tid; i < 512; i += blockDim.x) tw16[i] = src[i];
+  } else {
+    for (int i = tid; i < TWS; i += blockDim.x) {
+      twc[i] = reinterpret_cast<const T*>(a.tws)[i];
+      tws[i] = reinterpret_cast<const T*>(a.tws)[TWS + i];
+    }
   }
   for (int i = tid; i < N; i += blockDim.x) xix[i] = reinterpret_cast<const T*>(a.xi_x)[i];
   if (tid == 0) {
@@ -638,15 +650,26 @@ k_xproj_warp(const XTmaArgs a) {
     }
     if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     __syncwarp();                                       // this warp's row no longer being stored
-    fft_column_acc<N, E, false, 0, true>(x, lane, acc, tw);
+    if constexpr (F16) {
+      fft512_warp<false>(x, lane, wre, wim, tw16);
+      const int kap = lane >> 1, h = lane & 1;
 #pragma unroll
-    for (int e = 0; e < E; ++e) acc.put(lane + 32 * e, x[e]);
+      for (int q = 0; q < 16; ++q) {
+        const int j = sx512(kap + 16 * q + 256 * h);
+        wre[j] = x[q].x;
+        wim[j] = x[q].y;
+      }
+    } else {
+      fft_column_acc<N, E, false, 0, true>(x, lane, acc, tw);
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc.put(lane + 32 * e, x[e]);
+    }
     __syncthreads();
     const int rA = rinfo[s][0];
     for (int kx = tid; kx < N; kx += blockDim.x) {
       const int kxm = kx == 0 ? 0 : N - kx;
       if (self && kx > kxm) continue;
-      const int ja = swz(kx), jb = swz(kxm);
+      const int ja = F16 ? sx512(kx) : swz(kx), jb = F16 ? sx512(kxm) : swz(kxm);
       T2 av[3], bv[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -671,15 +694,31 @@ k_xproj_warp(const XTmaArgs a) {
       }
     }
     __syncthreads();
+    if constexpr (F16) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = acc.get(lane + 32 * e);
-    __syncwarp();
-    fft_column_acc<N, E, true, 0, true>(x, lane, acc, tw);
-    // results in natural order (unswizzled) into this warp's row, then one bulk store per plane
+      for (int e = 0; e < E; ++e) {
+        const int j = sx512(lane + 32 * e);
+        x[e] = T2{wre[j], wim[j]};
+      }
+      fft512_warp<true>(x, lane, wre, wim, tw16);
+      // results in natural order into this warp's row, then one bulk store per plane
+      const int kap = lane >> 1, h = lane & 1;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      wre[lane + 32 * e] = x[e].x;
-      wim[lane + 32 * e] = x[e].y;
+      for (int q = 0; q < 16; ++q) {
+        wre[kap + 16 * q + 256 * h] = x[q].x;
+        wim[kap + 16 * q + 256 * h] = x[q].y;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) x[e] = acc.get(lane + 32 * e);
+      __syncwarp();
+      fft_column_acc<N, E, true, 0, true>(x, lane, acc, tw);
+      // results in natural order (unswizzled) into this warp's row, then one bulk store per plane
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        wre[lane + 32 * e] = x[e].x;
+        wim[lane + 32 * e] = x[e].y;
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
