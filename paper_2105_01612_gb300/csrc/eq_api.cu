@@ -298,24 +298,27 @@ bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src,
              const void* ref, double* partials, cudaStream_t s, cudaError_t* e) {
   if (!on) return false;
   const eqk::TmaInfo& ti = axis == 2 ? p->tz : p->ty;
-  CUtensorMap map, refmap;
+  CUtensorMap map, refmap, outmap;
   if (!make_map(&map, src, p, axis, ti.cols, ti.box) ||
-      (ref && !make_map(&refmap, ref, p, axis, ti.cols, ti.box))) {
+      (ref && !make_map(&refmap, ref, p, axis, ti.cols, ti.box)) ||
+      (dst != src && !make_map(&outmap, dst, p, axis, ti.cols, ti.box))) {
     *e = cudaErrorInvalidValue;
     return true;
   }
   if (!ref) refmap = map;
+  if (dst == src) outmap = map;
   eqk::TmaArgs t{};
   t.ref = ref; t.out = dst; t.tw = p->tw[axis]; t.partials = partials; t.err = p->err;
   t.field_stride = 6 * p->V; t.V = p->V;
   t.nx = p->nx; t.ny = p->ny; t.nz = p->nz;
   t.axis = axis; t.mode = mode;
+  t.tma_store = axis == 2 && mode == 2;   // measured: faster for the last z pass only
   t.ntiles = (axis == 2 ? (long long)p->ny : (long long)p->nz) * (p->nx / ti.cols);
   dim3 grid(axis == 2 ? p->gtz : p->gty, p->batch * 3);
   const int n = axis == 2 ? p->nz : p->ny;
   const int v = axis == 2 ? p->vz : p->vy;
-  *e = p->dtype == EQ_F32 ? eqk::launch_tma_f32(n, v, inv, map, refmap, t, grid, s)
-                          : eqk::launch_tma_f64(n, v, inv, map, refmap, t, grid, s);
+  *e = p->dtype == EQ_F32 ? eqk::launch_tma_f32(n, v, inv, map, refmap, outmap, t, grid, s)
+                          : eqk::launch_tma_f64(n, v, inv, map, refmap, outmap, t, grid, s);
   return true;
 }
 

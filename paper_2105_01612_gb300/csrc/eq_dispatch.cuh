@@ -62,15 +62,19 @@ template <typename T, int N, int V> struct TmaInst {
     }
   }
   static cudaError_t launch(bool inv, const CUtensorMap& map, const CUtensorMap& refmap,
-                            const TmaArgs& a, dim3 grid, cudaStream_t s) {
+                            const CUtensorMap& outmap, const TmaArgs& a, dim3 grid, cudaStream_t s) {
     using C = TmaCfg<T, N, V>;
     if constexpr (!C::OK) {
       return cudaErrorInvalidValue;
     } else {
-      if (!inv && a.mode == 1) k_strided_tma<T, N, false, 1, V><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, a);
-      else if (!inv) k_strided_tma<T, N, false, 0, V><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, a);
-      else if (a.mode == 2) k_strided_tma<T, N, true, 2, V><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, a);
-      else k_strided_tma<T, N, true, 0, V><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, a);
+      if (!inv && a.mode == 1)
+        k_strided_tma<T, N, false, 1, V><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
+      else if (!inv)
+        k_strided_tma<T, N, false, 0, V><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
+      else if (a.mode == 2)
+        k_strided_tma<T, N, true, 2, V><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
+      else
+        k_strided_tma<T, N, true, 0, V><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
       return cudaGetLastError();
     }
   }
@@ -181,12 +185,12 @@ template <typename T> cudaError_t tma_info_t(int n, int v, TmaInfo* out) {
 }
 template <typename T>
 cudaError_t tma_launch_t(int n, int v, bool inv, const CUtensorMap& map, const CUtensorMap& refmap,
-                         const TmaArgs& a, dim3 grid, cudaStream_t s) {
+                         const CUtensorMap& outmap, const TmaArgs& a, dim3 grid, cudaStream_t s) {
   switch (n) {
-#define EQ_CASE(N)                                                        \
-  case N:                                                                   \
-    return v ? TmaInst<T, N, 1>::launch(inv, map, refmap, a, grid, s)      \
-             : TmaInst<T, N, 0>::launch(inv, map, refmap, a, grid, s);
+#define EQ_CASE(N)                                                              \
+  case N:                                                                         \
+    return v ? TmaInst<T, N, 1>::launch(inv, map, refmap, outmap, a, grid, s)    \
+             : TmaInst<T, N, 0>::launch(inv, map, refmap, outmap, a, grid, s);
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;

@@ -11,8 +11,8 @@ cudaError_t launch_xproj_f32(int n, const XArgs& a, dim3 grid, cudaStream_t s) {
 }
 cudaError_t tma_info_f32(int n, int v, TmaInfo* out) { return tma_info_t<float>(n, v, out); }
 cudaError_t launch_tma_f32(int n, int v, bool inv, const CUtensorMap& map, const CUtensorMap& refmap,
-                           const TmaArgs& a, dim3 grid, cudaStream_t s) {
-  return tma_launch_t<float>(n, v, inv, map, refmap, a, grid, s);
+                           const CUtensorMap& outmap, const TmaArgs& a, dim3 grid, cudaStream_t s) {
+  return tma_launch_t<float>(n, v, inv, map, refmap, outmap, a, grid, s);
 }
 cudaError_t xtma_info_f32(int n, int v, TmaInfo* out) { return xtma_info_t<float>(n, v, out); }
 cudaError_t launch_xtma_f32(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s) {

@@ -39,9 +39,9 @@ struct TmaInfo {
 cudaError_t tma_info_f32(int n, int v, TmaInfo* out);
 cudaError_t tma_info_f64(int n, int v, TmaInfo* out);
 cudaError_t launch_tma_f32(int n, int v, bool inv, const CUtensorMap& map, const CUtensorMap& refmap,
-                           const TmaArgs& a, dim3 grid, cudaStream_t s);
+                           const CUtensorMap& outmap, const TmaArgs& a, dim3 grid, cudaStream_t s);
 cudaError_t launch_tma_f64(int n, int v, bool inv, const CUtensorMap& map, const CUtensorMap& refmap,
-                           const TmaArgs& a, dim3 grid, cudaStream_t s);
+                           const CUtensorMap& outmap, const TmaArgs& a, dim3 grid, cudaStream_t s);
 // bulk-copy fused x pass: info fails when no instance exists for n
 cudaError_t xtma_info_f32(int n, int v, TmaInfo* out);
 cudaError_t xtma_info_f64(int n, int v, TmaInfo* out);

@@ -52,6 +52,16 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// tiled store from shared memory (bulk group; the caller commits and waits)
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1,
+                                             int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+          reinterpret_cast<unsigned long long>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+      : "memory");
+}
+
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
                                           unsigned long long* bar) {
   asm volatile(
@@ -74,8 +84,9 @@ template <typename T, int N, int V = 0> struct TmaCfg {
   static constexpr int NBOX = N / BOX;
   using T2 = typename V2<T>::t;
   static constexpr size_t STAGE_BYTES = 2 * sizeof(T) * size_t(N) * B;   // re + im planes
-  static constexpr size_t SMEM = 1024 /*align + barriers*/ + sizeof(T2) * N + 2 * STAGE_BYTES +
-                                 sizeof(T2) * size_t(N) * B;
+  // alignment + barriers, twiddles, two stages, exchange, per-thread running sums
+  static constexpr size_t SMEM = 1024 + sizeof(T2) * N + 2 * STAGE_BYTES +
+                                 sizeof(T2) * size_t(N) * B + 6 * sizeof(T) * size_t(THREADS);
   static constexpr bool OK = N >= 64 && SMEM * MINB <= 227 * 1024 && (V == 0 || B * TPC <= 512);
 };
 
@@ -89,18 +100,25 @@ struct TmaArgs {
   int nx, ny, nz;
   int axis;                // 2 = z, 1 = y
   int mode;                // 0 middle, 1 first (statistics), 2 last
+  int tma_store;           // 1: store tiles by TMA through the exchange buffer
   long long ntiles;        // tiles per (field, component)
 };
 
 // MODE: 0 middle pass, 1 first pass (input statistics), 2 last pass (L-inf against a.ref, whose
-// tile streams through `refmap` into the stage the transform has just read, while it computes)
+// tile streams through `refmap` into the stage the transform has just read, while it computes).
+// At 1024 threads a thread has 64 registers; the running statistics of MODE 1 (three compensated
+// sums) and the L-inf of MODE 2 live in a per-thread slot of shared memory instead, so that no
+// register spills to local memory (whose reloads would go to L2 every tile).  The transformed
+// tile leaves by per-thread stores or, with a.tma_store, through the exchange buffer by tiled TMA
+// stores (`outmap`); the host takes the latter for the last z pass, where it measured faster.
 template <typename T, int N, bool INV, int MODE, int V>
 __global__ void __launch_bounds__(TmaCfg<T, N, V>::THREADS, TmaCfg<T, N, V>::MINB)
 k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap refmap,
-              const TmaArgs a) {
+              const __grid_constant__ CUtensorMap outmap, const TmaArgs a) {
   using C = TmaCfg<T, N, V>;
   using T2 = typename C::T2;
   constexpr int E = C::E, TPC = C::TPC, B = C::B, BOX = C::BOX, NBOX = C::NBOX;
+  constexpr int THREADS = C::THREADS;
   extern __shared__ __align__(16) unsigned char smem_tma[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_tma) + 127) & ~uintptr_t(127));
@@ -108,24 +126,25 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
   T* stage0 = reinterpret_cast<T*>(base + 128);      // stage s at stage0 + s * 2 N B
   T2* tw = reinterpret_cast<T2*>(stage0 + 4 * N * B);
   T2* xbuf = tw + N;
+  T* acc = reinterpret_cast<T*>(xbuf + N * B);       // [6][THREADS] running sums (MODE 1, 2)
   __shared__ double red[32 * 4];
-  __shared__ int abort_flag;
+  __shared__ int abort_flag, nonfinite;
 
   const int tid = threadIdx.x;
   const int b = tid % B, t = tid / B;
   const int field = blockIdx.y / 3, comp = blockIdx.y % 3;
   const int plane_re = field * 6 + 2 * comp;
-  const long long fbase = field * a.field_stride + (2LL * comp) * a.V;
-  T* out_re = reinterpret_cast<T*>(a.out) + fbase;
-  T* out_im = out_re + a.V;
-  const T* ref_re = (MODE == 2 && a.ref) ? reinterpret_cast<const T*>(a.ref) + fbase : nullptr;
-  const T wa = comp == 2 ? T(2) : T(1), wb = comp == 0 ? T(1) : T(2);
   const int tiles_x = a.nx / B;
-  const long long nstride = a.axis == 2 ? (long long)a.nx * a.ny : a.nx;
+  const int ntiles = (int)a.ntiles;
 
   for (int i = tid; i < N; i += blockDim.x) tw[i] = reinterpret_cast<const T2*>(a.tw)[i];
+  if constexpr (MODE != 0) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc[j * THREADS + tid] = T(0);
+  }
   if (tid == 0) {
     abort_flag = 0;
+    nonfinite = 0;
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -134,9 +153,9 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
 
   // coordinates of tile u: (x0, row) with row = y (z pass) or z (y pass)
   int issued0 = 0, issued1 = 0;                        // loads issued per stage (thread 0)
-  auto issue = [&](long long u, int s, const CUtensorMap* m) {
-    const int x0 = (int)(u % tiles_x) * B;
-    const int row = (int)(u / tiles_x);
+  auto issue = [&](int u, int s, const CUtensorMap* m) {
+    const int x0 = (u % tiles_x) * B;
+    const int row = u / tiles_x;
     if (s) ++issued1; else ++issued0;
     mbar_expect_tx(&bar[s], (unsigned)C::STAGE_BYTES);
 #pragma unroll
@@ -148,20 +167,17 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
         else tma_load_4d(dst, m, &bar[s], x0, q * BOX, row, plane_re + p);
       }
   };
-  const bool with_ref = MODE == 2 && ref_re != nullptr;
   int ph0 = 0, ph1 = 0;                                  // completed phases per stage
 
-  const long long first = blockIdx.x, step = gridDim.x;
+  const int first = blockIdx.x, step = gridDim.x;
   if (tid == 0) {
-    if (first < a.ntiles) issue(first, 0, &map);
-    if (first + step < a.ntiles) issue(first + step, 1, &map);
+    if (first < ntiles) issue(first, 0, &map);
+    if (first + step < ntiles) issue(first + step, 1, &map);
   }
 
-  Kahan<T> sa, sb, sq;
-  T nonfinite = T(0), linf = T(0);
   const IdxStrided idx{b, B};
   int k = 0;
-  for (long long u = first; u < a.ntiles; u += step, ++k) {
+  for (int u = first; u < ntiles; u += step, ++k) {
     const int s = k & 1;
     // one thread polls the barrier; the block barrier then publishes the stage to everyone
     if (tid == 0 && !mbar_wait(&bar[s], (unsigned)((s ? ph1 : ph0) & 1))) {
@@ -172,44 +188,82 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
     __syncthreads();
     if (abort_flag) break;
     T2 x[E];
-    const T* sre = stage0 + s * 2 * N * B;
-    const T* sim = sre + N * B;
+    {
+      const T* sre = stage0 + s * 2 * N * B;
 #pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = T2{sre[(t + TPC * e) * B + b], sim[(t + TPC * e) * B + b]};
+      for (int e = 0; e < E; ++e)
+        x[e] = T2{sre[(t + TPC * e) * B + b], sre[N * B + (t + TPC * e) * B + b]};
+    }
+    // the previous tile's stores must have read the exchange buffer before the transform reuses it
+    if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     __syncthreads();                                   // stage s is free again
     if (tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (with_ref) issue(u, s, &refmap);              // this tile's input, for the residual
-      else if (u + 2 * step < a.ntiles) issue(u + 2 * step, s, &map);
+      if (MODE == 2 && a.ref) issue(u, s, &refmap);    // this tile's input, for the residual
+      else if (u + 2 * step < ntiles) issue(u + 2 * step, s, &map);
     }
     if constexpr (MODE == 1) {
-      // plain sums over the thread's E points, compensated across tiles.  A NaN or infinity in
-      // any point makes its tile sum non-finite (so does a sum beyond the type's range, which
-      // the flag then reports as well)
-      T ta = T(0), tb = T(0), tq = T(0);
+      // plain sums over the thread's E points, compensated across tiles in the thread's slot.
+      // A NaN or infinity in any point makes its tile sum non-finite (so does a sum beyond the
+      // type's range, which the flag then reports as well)
+      const T wa = comp == 2 ? T(2) : T(1), wb = comp == 0 ? T(1) : T(2);
+      T tsum[3] = {T(0), T(0), T(0)};
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        ta += x[e].x;
-        tb += x[e].y;
-        tq += wa * x[e].x * x[e].x + wb * x[e].y * x[e].y;
+        tsum[0] += x[e].x;
+        tsum[1] += x[e].y;
+        tsum[2] += wa * x[e].x * x[e].x + wb * x[e].y * x[e].y;
       }
-      if (!isfinite(ta) || !isfinite(tb)) nonfinite += T(1);
-      sa.add(ta);
-      sb.add(tb);
-      sq.add(tq);
-    }
-    fft_column<N, E, INV>(x, t, xbuf, idx, tw);
-    const int x0 = (int)(u % tiles_x) * B;
-    const long long row = u / tiles_x;
-    const long long col0 = a.axis == 2 ? row * a.nx + x0 + b : row * (long long)a.nx * a.ny + x0 + b;
+      if (!isfinite(tsum[0]) || !isfinite(tsum[1])) nonfinite = 1;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const long long off = col0 + (long long)(t + TPC * e) * nstride;
-      out_re[off] = x[e].x;
-      out_im[off] = x[e].y;
+      for (int j = 0; j < 3; ++j) {
+        Kahan<T> kh{acc[(2 * j) * THREADS + tid], acc[(2 * j + 1) * THREADS + tid]};
+        kh.add(tsum[j]);
+        acc[(2 * j) * THREADS + tid] = kh.s;
+        acc[(2 * j + 1) * THREADS + tid] = kh.c;
+      }
+    }
+    fft_column<N, E, INV>(x, t, xbuf, idx, tw);      // ends after a barrier past its last read
+    if (!a.tma_store) {
+      const int x0 = (u % tiles_x) * B;
+      const int row = u / tiles_x;
+      // offsets within one plane (nx ny nz < 2^31); the plane bases are 64-bit pointers
+      const int col0 = a.axis == 2 ? row * a.nx + x0 + b : row * a.nx * a.ny + x0 + b;
+      const int nstride = a.axis == 2 ? a.nx * a.ny : a.nx;
+      T* out_re = reinterpret_cast<T*>(a.out) + field * a.field_stride + (2LL * comp) * a.V;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int off = col0 + (t + TPC * e) * nstride;
+        out_re[off] = x[e].x;
+        out_re[a.V + off] = x[e].y;
+      }
+    } else {
+      // the tile in box layout ([point][column], re plane then im plane) into the exchange
+      // buffer, then out by tiled stores
+      T* ore = reinterpret_cast<T*>(xbuf);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        ore[(t + TPC * e) * B + b] = x[e].x;
+        ore[N * B + (t + TPC * e) * B + b] = x[e].y;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        const int x0 = (u % tiles_x) * B;
+        const int row = u / tiles_x;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int q = 0; q < NBOX; ++q) {
+            const T* src = ore + p * N * B + q * BOX * B;
+            if (a.axis == 2) tma_store_4d(&outmap, src, x0, row, q * BOX, plane_re + p);
+            else tma_store_4d(&outmap, src, x0, q * BOX, row, plane_re + p);
+          }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
     }
     if constexpr (MODE == 2) {
-      if (with_ref) {
+      if (a.ref) {
         if (tid == 0 && !mbar_wait(&bar[s], (unsigned)((s ? ph1 : ph0) & 1))) {
           atomicOr(a.err, 1);
           abort_flag = 1;
@@ -217,20 +271,24 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
         if (s) ++ph1; else ++ph0;
         __syncthreads();
         if (abort_flag) break;
+        const T* sre = stage0 + s * 2 * N * B;
+        T linf = acc[tid];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           linf = fmax(linf, fabs(sre[(t + TPC * e) * B + b] - x[e].x));
-          linf = fmax(linf, fabs(sim[(t + TPC * e) * B + b] - x[e].y));
+          linf = fmax(linf, fabs(sre[N * B + (t + TPC * e) * B + b] - x[e].y));
         }
+        acc[tid] = linf;
         __syncthreads();                               // stage s read: refill with tile k + 2
         if (abort_flag) break;
-        if (tid == 0 && u + 2 * step < a.ntiles) {
+        if (tid == 0 && u + 2 * step < ntiles) {
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           issue(u + 2 * step, s, &map);
         }
       }
     }
   }
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete
   if (abort_flag) {
     // leave no copy in flight: wait (bounded) for every phase this block issued
     if (tid == 0) {
@@ -241,15 +299,19 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
     return;
   }
   if constexpr (MODE == 1) {
-    double v[4] = {sa.value(), sb.value(), sq.value(), double(nonfinite)};
-    block_sum<4>(v, red);
+    double v[4];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      v[j] = double(acc[(2 * j) * THREADS + tid]) - double(acc[(2 * j + 1) * THREADS + tid]);
+    v[3] = 0.0;
+    block_sum<4>(v, red);                              // starts with a block barrier
     if (tid == 0) {
       double* p = a.partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 4;
-      p[0] = v[0]; p[1] = v[1]; p[2] = v[2]; p[3] = v[3];
+      p[0] = v[0]; p[1] = v[1]; p[2] = v[2]; p[3] = nonfinite ? 1.0 : 0.0;
     }
   } else if constexpr (MODE == 2) {
-    if (ref_re) {
-      double m = block_max(double(linf), red);
+    if (a.ref) {
+      double m = block_max(double(acc[tid]), red);
       if (tid == 0) a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = m;
     }
   }
