@@ -257,10 +257,11 @@ template <typename T2, typename IDX> struct AosAcc {
 // with bits 5..7 of i, so the contiguous, stage-output and projector access patterns of a warp
 // (32 consecutive threads of one transform) touch 32 distinct banks.
 __host__ __device__ __forceinline__ int swz(int i) { return i ^ ((i >> 5) & 7) ^ (((i >> 6) & 3) << 3); }
-// Spectrum rows of the 512-point warp transform: element i at i ^ (bit 8 of i moved to bit 4), so
-// the transform's output stores (lanes 2 kap + h write kap + 16 q + 256 h), its input loads
-// (l + 32 e) and the projector's runs of 32 consecutive modes all touch 32 distinct banks.
-__host__ __device__ __forceinline__ int sx512(int i) { return i ^ (((i >> 8) & 1) << 4); }
+// Spectrum rows of the 512-point warp transform, interleaved complex (8-byte words, served 16
+// lanes per wavefront): element i at i ^ (bit 8 of i moved to bit 3), so that the transform's
+// output stores (lanes 2 kap + h write kap + 16 q + 256 h), its input loads (l + 32 e) and the
+// projector's runs of consecutive modes touch 16 distinct word pairs in each half-warp.
+__host__ __device__ __forceinline__ int sx512(int i) { return i ^ (((i >> 8) & 1) << 3); }
 template <typename T> struct SoaAcc {
   T* re;
   T* im;
@@ -311,16 +312,18 @@ __device__ __forceinline__ void fft_column(T2 (&x)[E], int t, T2* buf, const IDX
 // (e < 16).  With n = l + 32 e and k = k1 + 16 k2 (k1 < 16, k2 < 32):
 //   1. a 16-point DFT over e in registers: Y_l[k1];
 //   2. Y_l[k1] *= W512^(l k1) (tw = 16 x 32 table [k1][l] of the forward factors);
-//   3. one exchange through the warp's split re/im row (512 words each): Y_l[k1] stored at
-//      32 k1 + (l ^ 2 k1), so that both the store (fixed k1) and the load below hit 32 banks;
+//   3. one exchange through the warp's row (512 interleaved complex values): Y_l[k1] stored at
+//      32 k1 + (l ^ 2 k1), so that both the store (fixed k1) and the load below are
+//      conflict-free in each half-warp;
 //   4. lane L = 2 kap + h loads Y_{h + 2 m}[kap], m < 16, and takes a 16-point DFT over m:
 //      Z_h[q] for the even (h = 0) and odd (h = 1) halves of the 32-point DFT over l;
 //   5. lanes L and L ^ 1 combine by shuffle: X[kap + 16 q + 256 h] = Z_0[q] +- W32^q Z_1[q].
 // On return slot q of lane L holds output kap + 16 q + 256 h.  The caller guarantees that no lane
 // still reads the row on entry; the row is free again on return.
-template <bool INV, typename T, typename T2>
-__device__ __forceinline__ void fft512_warp(T2 (&v)[16], int lane, T* re, T* im,
+template <bool INV, typename T2>
+__device__ __forceinline__ void fft512_warp(T2 (&v)[16], int lane, T2* buf,
                                             const T2* __restrict__ tw) {
+  using T = decltype(v[0].x);
   dft16<INV>(v);
 #pragma unroll
   for (int k1 = 1; k1 < 16; ++k1) {
@@ -331,16 +334,13 @@ __device__ __forceinline__ void fft512_warp(T2 (&v)[16], int lane, T* re, T* im,
   __syncwarp();
 #pragma unroll
   for (int k1 = 0; k1 < 16; ++k1) {
-    const int pos = k1 * 32 + (lane ^ (2 * k1));
-    re[pos] = v[k1].x;
-    im[pos] = v[k1].y;
+    buf[k1 * 32 + (lane ^ (2 * k1))] = v[k1];
   }
   __syncwarp();
   const int kap = lane >> 1, h = lane & 1;
 #pragma unroll
   for (int m = 0; m < 16; ++m) {
-    const int pos = kap * 32 + h + 2 * (m ^ kap);
-    v[m] = T2{re[pos], im[pos]};
+    v[m] = buf[kap * 32 + h + 2 * (m ^ kap)];
   }
   __syncwarp();
   dft16<INV>(v);

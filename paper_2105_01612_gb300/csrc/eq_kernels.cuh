@@ -207,31 +207,35 @@ __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
 // The per-mode projector and its norm terms for one mode pair (k, -k).
 //   in:  a[c] = Z_c(k), bb[c] = Z_c(-k)  (c = 0..2)
 //   out: a[c] <- Zout_c(k) / V,  bb[c] <- Zout_c(-k) / V
+// Works on twice the Voigt components (the unpack's 1/2 is folded into the repack and into the
+// norm weights).  With n = xi / |xi|, v = S n and s = n . v, the projector removes
+// D = n (x) v + v (x) n - s n (x) n, whose squared Frobenius norm is 2 |v|^2 - s^2 (no
+// cancellation: |v|^2 >= s^2), and |xi . S|^2 = |xi|^2 |v|^2.
 template <typename T, typename T2>
 __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T xi1, T xi2,
                                              bool zero_mode, const double* mean, double vol,
                                              bool nyq_zero, T inv_v, T mult,
                                              Kahan<T>& r2, Kahan<T>& di2, Kahan<T>& do2,
                                              Kahan<T>& o2) {
-  // unpack the six Voigt components of S^(k): S_2c = (A + conj B) / 2, S_2c+1 = -i (A - conj B) / 2
+  // 2 S_2c = A + conj B, 2 S_2c+1 = -i (A - conj B)
   T sr[6], si[6];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    sr[2 * c] = T(0.5) * (a[c].x + bb[c].x);
-    si[2 * c] = T(0.5) * (a[c].y - bb[c].y);
-    sr[2 * c + 1] = T(0.5) * (a[c].y + bb[c].y);
-    si[2 * c + 1] = T(0.5) * (bb[c].x - a[c].x);
+    sr[2 * c] = a[c].x + bb[c].x;
+    si[2 * c] = a[c].y - bb[c].y;
+    sr[2 * c + 1] = a[c].y + bb[c].y;
+    si[2 * c + 1] = bb[c].x - a[c].x;
   }
   if (zero_mode && mean) {
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-      sr[j] = T(mean[j] * vol);
+      sr[j] = T(2.0 * mean[j] * vol);
       si[j] = T(0);
     }
   }
   const T k2 = xi0 * xi0 + xi1 * xi1 + xi2 * xi2;
   T orr[6], oi[6];
-  T din = T(0);                        // |xi . S^|^2 = k2 |S^ n|^2
+  T rr = T(0), din = T(0);
   if (k2 > T(0)) {
     const T rn = rsqrt_t(k2);
     const T n0 = xi0 * rn, n1 = xi1 * rn, n2 = xi2 * rn;
@@ -242,7 +246,9 @@ __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T x
       const T v1 = S[5] * n0 + S[1] * n1 + S[3] * n2;                          \
       const T v2 = S[4] * n0 + S[3] * n1 + S[2] * n2;                          \
       const T s = n0 * v0 + n1 * v1 + n2 * v2;                                 \
-      din += k2 * (v0 * v0 + v1 * v1 + v2 * v2);                               \
+      const T vv = v0 * v0 + v1 * v1 + v2 * v2;                               \
+      rr += T(2) * vv - s * s;                                                 \
+      din += k2 * vv;                                                          \
       O[0] = S[0] - T(2) * n0 * v0 + s * n0 * n0;                              \
       O[1] = S[1] - T(2) * n1 * v1 + s * n1 * n1;                              \
       O[2] = S[2] - T(2) * n2 * v2 + s * n2 * n2;                              \
@@ -254,24 +260,24 @@ __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T x
     EQ_PROJ(si, oi)
 #undef EQ_PROJ
   } else {
+    // the zero mode and the all-Nyquist corners: kept, or dropped (literal route, not the mean)
     const bool drop = nyq_zero && !zero_mode;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
+      const T w = j < 3 ? T(1) : T(2);
+      if (drop) rr += w * (sr[j] * sr[j] + si[j] * si[j]);
       orr[j] = drop ? T(0) : sr[j];
       oi[j] = drop ? T(0) : si[j];
     }
   }
   // norm terms (sums of |.|^2 over modes; Parseval turns them into voxel means)
   {
-    T rr = T(0), oo = T(0);
+    T oo = T(0), dout = T(0);
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const T w = j < 3 ? T(1) : T(2);
-      const T dr = sr[j] - orr[j], dii = si[j] - oi[j];
-      rr += w * (dr * dr + dii * dii);
       oo += w * (orr[j] * orr[j] + oi[j] * oi[j]);
     }
-    T dout = T(0);
 #define EQ_DIV(S, ACC)                                                          \
     {                                                                          \
       const T d0 = xi0 * S[0] + xi1 * S[5] + xi2 * S[4];                       \
@@ -281,17 +287,19 @@ __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T x
     }
     EQ_DIV(orr, dout) EQ_DIV(oi, dout)
 #undef EQ_DIV
-    r2.add(mult * rr);
-    o2.add(mult * oo);
-    di2.add(mult * din);
-    do2.add(mult * dout);
+    const T m4 = T(0.25) * mult;                      // (1/2)^2 of the doubled components
+    r2.add(m4 * rr);
+    o2.add(m4 * oo);
+    di2.add(m4 * din);
+    do2.add(m4 * dout);
   }
-  // repack: Zout_c(k) = O_2c + i O_2c+1, Zout_c(-k) = conj(O_2c) + i conj(O_2c+1)
+  // repack: Zout_c(k) = O_2c + i O_2c+1, Zout_c(-k) = conj(O_2c) + i conj(O_2c+1), halved
+  const T hv = T(0.5) * inv_v;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const T or_ = orr[2 * c], oi_ = oi[2 * c], pr = orr[2 * c + 1], pi_ = oi[2 * c + 1];
-    a[c] = T2{(or_ - pi_) * inv_v, (oi_ + pr) * inv_v};
-    bb[c] = T2{(or_ + pi_) * inv_v, (pr - oi_) * inv_v};
+    a[c] = T2{(or_ - pi_) * hv, (oi_ + pr) * hv};
+    bb[c] = T2{(or_ + pi_) * hv, (pr - oi_) * hv};
   }
 }
 

@@ -713,14 +713,12 @@ k_xproj_warp(const XTmaArgs a) {
     if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     __syncwarp();                                       // this warp's row no longer being stored
     if constexpr (F16) {
-      fft512_warp<false>(x, lane, wre, wim, tw16);
+      // spectrum as interleaved complex values in the warp's row
+      T2* wrow = reinterpret_cast<T2*>(wre);
+      fft512_warp<false>(x, lane, wrow, tw16);
       const int kap = lane >> 1, h = lane & 1;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int j = sx512(kap + 16 * q + 256 * h);
-        wre[j] = x[q].x;
-        wim[j] = x[q].y;
-      }
+      for (int q = 0; q < 16; ++q) wrow[sx512(kap + 16 * q + 256 * h)] = x[q];
     } else {
       fft_column_acc<N, E, false, 0, true>(x, lane, acc, tw);
 #pragma unroll
@@ -737,8 +735,13 @@ k_xproj_warp(const XTmaArgs a) {
       for (int c = 0; c < 3; ++c) {
         const T* ra = rows + (2 * c) * N;
         const T* rb = rows + (2 * (self ? c : 3 + c)) * N;
-        av[c] = T2{ra[ja], ra[N + ja]};
-        bv[c] = T2{rb[jb], rb[N + jb]};
+        if constexpr (F16) {
+          av[c] = reinterpret_cast<const T2*>(ra)[ja];
+          bv[c] = reinterpret_cast<const T2*>(rb)[jb];
+        } else {
+          av[c] = T2{ra[ja], ra[N + ja]};
+          bv[c] = T2{rb[jb], rb[N + jb]};
+        }
       }
       const bool selfmode = self && kx == kxm;
       project_pair<T>(av, bv, xix[kx], rxi[s][0], rxi[s][1], rA == 0 && kx == 0, mean, vol,
@@ -747,22 +750,25 @@ k_xproj_warp(const XTmaArgs a) {
       for (int c = 0; c < 3; ++c) {
         T* ra = rows + (2 * c) * N;
         T* rb = rows + (2 * (self ? c : 3 + c)) * N;
-        ra[ja] = av[c].x;
-        ra[N + ja] = av[c].y;
-        if (!selfmode) {
-          rb[jb] = bv[c].x;
-          rb[N + jb] = bv[c].y;
+        if constexpr (F16) {
+          reinterpret_cast<T2*>(ra)[ja] = av[c];
+          if (!selfmode) reinterpret_cast<T2*>(rb)[jb] = bv[c];
+        } else {
+          ra[ja] = av[c].x;
+          ra[N + ja] = av[c].y;
+          if (!selfmode) {
+            rb[jb] = bv[c].x;
+            rb[N + jb] = bv[c].y;
+          }
         }
       }
     }
     __syncthreads();
     if constexpr (F16) {
+      T2* wrow = reinterpret_cast<T2*>(wre);
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int j = sx512(lane + 32 * e);
-        x[e] = T2{wre[j], wim[j]};
-      }
-      fft512_warp<true>(x, lane, wre, wim, tw16);
+      for (int e = 0; e < E; ++e) x[e] = wrow[sx512(lane + 32 * e)];
+      fft512_warp<true>(x, lane, wrow, tw16);
       // results in natural order into this warp's row, then one bulk store per plane
       const int kap = lane >> 1, h = lane & 1;
 #pragma unroll
