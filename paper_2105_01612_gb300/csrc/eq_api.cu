@@ -272,10 +272,19 @@ void tma_setup(eq_plan* p, int vz, int vy, int vx) {
   p->tma_z = p->tma_y = p->tma_x = false;
   if (p->tma_allow) {
     const bool f32 = p->dtype == EQ_F32;
-    cudaError_t te = f32 ? eqk::tma_info_f32(p->nz, vz, &p->tz) : eqk::tma_info_f64(p->nz, vz, &p->tz);
-    p->tma_z = te == cudaSuccess && p->tz.cols > 0 && p->nx % p->tz.cols == 0 && p->tz.blocks_per_sm > 0;
-    te = f32 ? eqk::tma_info_f32(p->ny, vy, &p->ty) : eqk::tma_info_f64(p->ny, vy, &p->ty);
-    p->tma_y = te == cudaSuccess && p->ty.cols > 0 && p->nx % p->ty.cols == 0 && p->ty.blocks_per_sm > 0;
+    // strided variant 2 exists for some lengths only: fall back to the wide tiles elsewhere
+    auto strided = [&](int n, int& v, eqk::TmaInfo* ti) {
+      cudaError_t te = f32 ? eqk::tma_info_f32(n, v, ti) : eqk::tma_info_f64(n, v, ti);
+      if (te != cudaSuccess && v == 2) {
+        cudaGetLastError();
+        v = 0;
+        te = f32 ? eqk::tma_info_f32(n, v, ti) : eqk::tma_info_f64(n, v, ti);
+      }
+      return te == cudaSuccess && ti->cols > 0 && p->nx % ti->cols == 0 && ti->blocks_per_sm > 0;
+    };
+    p->tma_z = strided(p->nz, p->vz, &p->tz);
+    p->tma_y = strided(p->ny, p->vy, &p->ty);
+    cudaError_t te;
     te = f32 ? eqk::xtma_info_f32(p->nx, vx, &p->tx) : eqk::xtma_info_f64(p->nx, vx, &p->tx);
     p->tma_x = te == cudaSuccess && p->tx.blocks_per_sm > 0;
     cudaGetLastError();
@@ -312,7 +321,17 @@ bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src,
   t.field_stride = 6 * p->V; t.V = p->V;
   t.nx = p->nx; t.ny = p->ny; t.nz = p->nz;
   t.axis = axis; t.mode = mode;
-  t.tma_store = axis == 2 && mode == 2;   // measured: faster for the last z pass only
+  // TMA stores through the exchange buffer: measured faster for the z passes (the 16 x 32
+  // kernel: both; the wide tiles: the last one) and slower for the y passes.  EQ_TMA_STORE
+  // overrides for measurements (0 never, 1 last z pass, 2 every z pass, 3 every pass).
+  {
+    static const int ts = [] {
+      const char* e = getenv("EQ_TMA_STORE");
+      return e && e[0] >= '0' && e[0] <= '3' ? e[0] - '0' : -1;
+    }();
+    if (ts < 0) t.tma_store = axis == 2 && (p->vz == 2 || mode == 2);
+    else t.tma_store = ts == 3 || (axis == 2 && (ts == 2 || (ts == 1 && mode == 2)));
+  }
   t.ntiles = (axis == 2 ? (long long)p->ny : (long long)p->nz) * (p->nx / ti.cols);
   dim3 grid(axis == 2 ? p->gtz : p->gty, p->batch * 3);
   const int n = axis == 2 ? p->nz : p->ny;
@@ -627,18 +646,21 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
                    ((size_t)nx * p->esize) % 16 == 0;
     int gmax_z = 1, gmax_x = 1;
     for (int v = 3; v >= 0; --v) {
-      tma_setup(p, v == 1, v == 1, v);
+      tma_setup(p, v <= 2 ? v : 0, v <= 2 ? v : 0, v);
       gmax_z = std::max(gmax_z, std::max(p->gtz, p->gty));
       gmax_x = std::max(gmax_x, p->gtx);
     }
-    // defaults measured on GB300 at 256^3 and 512^3: wide tiles for the strided passes, the
-    // warp-per-row x pass compiled for four blocks per SM (eq_plan_autotune re-decides per plan)
+    // defaults measured on GB300 at 256^3 and 512^3: the 16 x 32 column kernel for 512-point FP32
+    // strided passes (z: with TMA stores), wide tiles for the others, the warp-per-row x pass
+    // compiled for four blocks per SM (eq_plan_autotune re-decides per plan)
     const char* vs = getenv("EQ_TMA_VARIANT");
     const char* vxs = getenv("EQ_X_VARIANT");
-    const int v0 = (vs && vs[0] == '1') ? 1 : 0;
+    const char* vzs = getenv("EQ_TMA_VARIANT_Z");
+    const int v0 = vs && vs[0] >= '0' && vs[0] <= '2' ? vs[0] - '0' : 2;
+    const int vz0 = vzs && vzs[0] >= '0' && vzs[0] <= '2' ? vzs[0] - '0' : v0;
     const int vx0 = vxs && vxs[0] >= '0' && vxs[0] <= '3' ? vxs[0] - '0' : 3;
-    tma_setup(p, v0, v0, vx0);
-    for (int v = vx0 - 1; !p->tma_x && v >= 0; --v) tma_setup(p, v0, v0, v);   // fall back
+    tma_setup(p, vz0, v0, vx0);
+    for (int v = vx0 - 1; !p->tma_x && v >= 0; --v) tma_setup(p, vz0, v0, v);   // fall back
     p->gtz_max = gmax_z;
     p->gtx_max = gmax_x;
   }
@@ -854,17 +876,24 @@ eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stre
   cudaEvent_t ev[EQ_NUM_PASSES + 1];
   for (auto& x : ev)
     if ((e = cudaEventCreate(&x)) != cudaSuccess) return fail_cuda(e, "eq_plan_autotune: events");
-  constexpr int NCFG = 5;
+  constexpr int NCFG = 6;
   float ms[NCFG][EQ_NUM_PASSES] = {};
   bool ok[NCFG][3] = {};                                // [config][axis z, y, x] available
   const int saved_cap = p->tcap, saved_used = p->tused;
-  // configs: 0 wide tiles, 1 narrow tiles, 2 plain kernels, 3 and 4 warp-per-row x pass (one
-  // and four blocks per SM asked of the register allocator); x variant of each config:
-  auto xvar = [](int cfg) { return cfg == 1 ? 1 : (cfg >= 3 ? cfg - 1 : 0); };
+  // configs: 0 wide tiles, 1 narrow tiles, 2 plain kernels, 3 and 4 warp-per-row x pass (three
+  // and four blocks per SM asked of the register allocator), 5 the 16 x 32 strided kernel (where
+  // it exists; its config counts for an axis only if the axis really ran it)
+  auto xvar = [](int cfg) { return cfg == 1 ? 1 : (cfg == 3 ? 2 : (cfg == 4 ? 3 : 0)); };
+  auto svar = [](int cfg) { return cfg == 1 ? 1 : (cfg == 5 ? 2 : 0); };
   for (int cfg = 0; cfg < NCFG; ++cfg) {
-    tma_setup(p, cfg == 1, cfg == 1, xvar(cfg));
+    tma_setup(p, svar(cfg), svar(cfg), xvar(cfg));
     if (cfg == 2) p->tma_z = p->tma_y = p->tma_x = false;
-    if (cfg >= 3) p->tma_z = p->tma_y = false;
+    if (cfg == 3 || cfg == 4) p->tma_z = p->tma_y = false;
+    if (cfg == 5) {
+      p->tma_x = false;
+      if (p->vz != 2) p->tma_z = false;
+      if (p->vy != 2) p->tma_y = false;
+    }
     ok[cfg][0] = cfg == 2 || p->tma_z;
     ok[cfg][1] = cfg == 2 || p->tma_y;
     ok[cfg][2] = cfg == 2 || p->tma_x;
@@ -882,10 +911,10 @@ eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stre
       if (c != 2 && ok[c][axis] && cost(ms[c]) < cost(ms[best])) best = c;
     return best;
   };
-  const int bz = pick(0, 2, [](const float* m) { return m[0] + m[5]; });
-  const int by = pick(1, 2, [](const float* m) { return m[2] + m[4]; });
+  const int bz = pick(0, NCFG, [](const float* m) { return m[0] + m[5]; });
+  const int by = pick(1, NCFG, [](const float* m) { return m[2] + m[4]; });
   const int bx = pick(2, NCFG, [](const float* m) { return m[3]; });
-  tma_setup(p, bz == 1, by == 1, xvar(bx));
+  tma_setup(p, svar(bz), svar(by), xvar(bx));
   if (bz == 2) p->tma_z = false;
   if (by == 2) p->tma_y = false;
   if (bx == 2) p->tma_x = false;

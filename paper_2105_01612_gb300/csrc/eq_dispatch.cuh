@@ -80,6 +80,42 @@ template <typename T, int N, int V> struct TmaInst {
   }
 };
 
+// shape variant 2 of the strided passes: 512-point FP32 columns, 16 x 32 (k_strided16)
+struct Tma16Inst {
+  static cudaError_t info(TmaInfo* out) {
+    using C = Tma16Cfg;
+    out->threads = C::THREADS;
+    out->cols = C::B;
+    out->box = C::BOX;
+    out->smem = C::SMEM;
+    const void* fns[4] = {reinterpret_cast<const void*>(&k_strided16<false, 1>),
+                          reinterpret_cast<const void*>(&k_strided16<false, 0>),
+                          reinterpret_cast<const void*>(&k_strided16<true, 0>),
+                          reinterpret_cast<const void*>(&k_strided16<true, 2>)};
+    cudaError_t e = cudaSuccess;
+    for (const void* f : fns)
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    int bl = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, fns[0], C::THREADS, C::SMEM);
+    out->blocks_per_sm = bl;
+    return e;
+  }
+  static cudaError_t launch(bool inv, const CUtensorMap& map, const CUtensorMap& refmap,
+                            const CUtensorMap& outmap, const TmaArgs& a, dim3 grid, cudaStream_t s) {
+    using C = Tma16Cfg;
+    if (!inv && a.mode == 1)
+      k_strided16<false, 1><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
+    else if (!inv)
+      k_strided16<false, 0><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
+    else if (a.mode == 2)
+      k_strided16<true, 2><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
+    else
+      k_strided16<true, 0><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
+    return cudaGetLastError();
+  }
+};
+
 template <typename T, int N, int V> struct XTmaInst {
   static cudaError_t info(TmaInfo* out) {
     using C = XTmaCfg<T, N, V>;
@@ -176,6 +212,12 @@ template <typename T> cudaError_t xproj_t(int n, const XArgs& a, dim3 grid, cuda
 }
 
 template <typename T> cudaError_t tma_info_t(int n, int v, TmaInfo* out) {
+  if (v == 2) {
+    if constexpr (sizeof(T) == 4) {
+      if (n == 512) return Tma16Inst::info(out);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (n) {
 #define EQ_CASE(N) case N: return v ? TmaInst<T, N, 1>::info(out) : TmaInst<T, N, 0>::info(out);
     EQ_FOR_LENGTHS(EQ_CASE)
@@ -186,6 +228,12 @@ template <typename T> cudaError_t tma_info_t(int n, int v, TmaInfo* out) {
 template <typename T>
 cudaError_t tma_launch_t(int n, int v, bool inv, const CUtensorMap& map, const CUtensorMap& refmap,
                          const CUtensorMap& outmap, const TmaArgs& a, dim3 grid, cudaStream_t s) {
+  if (v == 2) {
+    if constexpr (sizeof(T) == 4) {
+      if (n == 512) return Tma16Inst::launch(inv, map, refmap, outmap, a, grid, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (n) {
 #define EQ_CASE(N)                                                              \
   case N:                                                                         \

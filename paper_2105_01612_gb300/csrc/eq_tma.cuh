@@ -317,6 +317,251 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
   }
 }
 
+// ---- strided passes for 512-point FP32 columns: 16 x 32 per column ----------------------
+//
+// Same tiles, stages and modes as k_strided_tma (16 columns x 512 points, TMA double buffering),
+// with 512 threads: thread (b, t) = (tid % 16, tid / 16) holds points t + 32 e (e < 16) of
+// column b.  Per column (the factorisation of fft512_warp): a 16-point DFT in registers, the
+// twiddle W512^(t k1), one exchange through a column-padded buffer (pitch 513 complex words:
+// conflict-free per half-warp), a 16-point DFT over the even / odd halves of the 32-point DFTs and
+// a radix-2 combine of threads t and t ^ 1 (lanes l and l ^ 16 of one warp) by shuffle.  Thread
+// (b, 2 kap + h) then holds output kap + 16 q + 256 h in slot q.  The next tile's copy is issued
+// after the exchange barrier, so a tile costs two block barriers (four with the L-inf residual,
+// two more with TMA stores through the exchange buffer).
+struct Tma16Cfg {
+  static constexpr int N = 512, E = 16, TPC = 32, B = 16, THREADS = 512, BOX = 256, NBOX = 2;
+  static constexpr int XP = 513;                                  // complex words per column
+  static constexpr size_t STAGE_BYTES = 2 * sizeof(float) * size_t(N) * B;
+  static constexpr size_t SMEM = 1024 + sizeof(float2) * 512 + 2 * STAGE_BYTES +
+                                 sizeof(float2) * size_t(XP) * B + 6 * sizeof(float) * THREADS;
+};
+
+template <bool INV, int MODE>
+__global__ void __launch_bounds__(Tma16Cfg::THREADS, 1)
+k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap refmap,
+            const __grid_constant__ CUtensorMap outmap, const TmaArgs a) {
+  using C = Tma16Cfg;
+  using T = float;
+  using T2 = float2;
+  constexpr int N = C::N, B = C::B, BOX = C::BOX, NBOX = C::NBOX, XP = C::XP, THREADS = C::THREADS;
+  extern __shared__ __align__(16) unsigned char smem_t16[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_t16) + 127) & ~uintptr_t(127));
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(base);
+  T* stage0 = reinterpret_cast<T*>(base + 128);      // stage s at stage0 + s * 2 N B
+  T2* tw = reinterpret_cast<T2*>(stage0 + 4 * N * B);   // W512^(t k1) at [k1][t]
+  T2* xbuf = tw + 512;
+  T* acc = reinterpret_cast<T*>(xbuf + XP * B);     // [6][THREADS] running sums (MODE 1, 2)
+  __shared__ double red[32 * 4];
+  __shared__ int abort_flag, nonfinite;
+
+  const int tid = threadIdx.x;
+  const int b = tid % B, t = tid / B;
+  const int kap = t >> 1, h = t & 1;
+  const int field = blockIdx.y / 3, comp = blockIdx.y % 3;
+  const int plane_re = field * 6 + 2 * comp;
+  const int tiles_x = a.nx / B;
+  const int ntiles = (int)a.ntiles;
+
+  // W512^(t k1) from the plain table W512^m (m < 512)
+  for (int i = tid; i < 512; i += blockDim.x)
+    tw[i] = reinterpret_cast<const T2*>(a.tw)[((i & 31) * (i >> 5)) & 511];
+  if constexpr (MODE != 0) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc[j * THREADS + tid] = T(0);
+  }
+  if (tid == 0) {
+    abort_flag = 0;
+    nonfinite = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  int issued0 = 0, issued1 = 0;                      // loads issued per stage (thread 0)
+  auto issue = [&](int u, int s, const CUtensorMap* m) {
+    const int x0 = (u % tiles_x) * B;
+    const int row = u / tiles_x;
+    if (s) ++issued1; else ++issued0;
+    mbar_expect_tx(&bar[s], (unsigned)C::STAGE_BYTES);
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int q = 0; q < NBOX; ++q) {
+        T* dst = stage0 + s * 2 * N * B + p * N * B + q * BOX * B;
+        if (a.axis == 2) tma_load_4d(dst, m, &bar[s], x0, row, q * BOX, plane_re + p);
+        else tma_load_4d(dst, m, &bar[s], x0, q * BOX, row, plane_re + p);
+      }
+  };
+  int ph0 = 0, ph1 = 0;                              // completed phases per stage
+  const int first = blockIdx.x, step = gridDim.x;
+  if (tid == 0) {
+    if (first < ntiles) issue(first, 0, &map);
+    if (first + step < ntiles) issue(first + step, 1, &map);
+  }
+  const T sg = h ? T(-1) : T(1);
+
+  int k = 0;
+  for (int u = first; u < ntiles; u += step, ++k) {
+    const int s = k & 1;
+    if (tid == 0 && !mbar_wait(&bar[s], (unsigned)((s ? ph1 : ph0) & 1))) {
+      atomicOr(a.err, 1);
+      abort_flag = 1;
+    }
+    if (s) ++ph1; else ++ph0;
+    // the last tile's TMA stores must have read the exchange buffer before it is rewritten
+    if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    __syncthreads();                                 // stage s ready; the last tile fully done
+    if (abort_flag) break;
+    T2 v[16];
+    {
+      const T* sre = stage0 + s * 2 * N * B;
+#pragma unroll
+      for (int e = 0; e < 16; ++e)
+        v[e] = T2{sre[(t + 32 * e) * B + b], sre[N * B + (t + 32 * e) * B + b]};
+    }
+    if constexpr (MODE == 1) {
+      const T wa = comp == 2 ? T(2) : T(1), wb = comp == 0 ? T(1) : T(2);
+      T tsum[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        tsum[0] += v[e].x;
+        tsum[1] += v[e].y;
+        tsum[2] += wa * v[e].x * v[e].x + wb * v[e].y * v[e].y;
+      }
+      if (!isfinite(tsum[0]) || !isfinite(tsum[1])) nonfinite = 1;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Kahan<T> kh{acc[(2 * j) * THREADS + tid], acc[(2 * j + 1) * THREADS + tid]};
+        kh.add(tsum[j]);
+        acc[(2 * j) * THREADS + tid] = kh.s;
+        acc[(2 * j + 1) * THREADS + tid] = kh.c;
+      }
+    }
+    // transform: 16-point DFT over e, twiddle, exchange
+    dft16<INV>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) {
+      T2 w = tw[k1 * 32 + t];
+      if (INV) w.y = -w.y;
+      v[k1] = cmul(v[k1], w);
+    }
+    T2* xc = xbuf + b * XP;
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) xc[k1 * 32 + (t ^ (2 * k1))] = v[k1];
+    __syncthreads();                                 // exchange written; stage s fully read
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (MODE == 2 && a.ref) issue(u, s, &refmap);  // this tile's input, for the residual
+      else if (u + 2 * step < ntiles) issue(u + 2 * step, s, &map);
+    }
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = xc[kap * 32 + h + 2 * (m ^ kap)];
+    dft16<INV>(v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const T2 tq = mul_w32_rt<INV>(q, v[q]);
+      const T2 send = h ? tq : v[q];
+      T2 recv;
+      recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+      recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+      v[q] = T2{recv.x + sg * send.x, recv.y + sg * send.y};
+    }
+    // slot q holds point kap + 16 q + 256 h of column b
+    if (!a.tma_store) {
+      const int x0 = (u % tiles_x) * B;
+      const int row = u / tiles_x;
+      const int col0 = a.axis == 2 ? row * a.nx + x0 + b : row * a.nx * a.ny + x0 + b;
+      const int nstride = a.axis == 2 ? a.nx * a.ny : a.nx;
+      T* out_re = reinterpret_cast<T*>(a.out) + field * a.field_stride + (2LL * comp) * a.V;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int off = col0 + (kap + 16 * q + 256 * h) * nstride;
+        out_re[off] = v[q].x;
+        out_re[a.V + off] = v[q].y;
+      }
+    } else {
+      // the tile in box layout ([point][column], re plane then im plane) into the exchange
+      // buffer (every read of it is behind the barrier below), then out by tiled stores
+      __syncthreads();
+      T* ore = reinterpret_cast<T*>(xbuf);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int pnt = (kap + 16 * q + 256 * h) * B + b;
+        ore[pnt] = v[q].x;
+        ore[N * B + pnt] = v[q].y;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        const int x0 = (u % tiles_x) * B;
+        const int row = u / tiles_x;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int q = 0; q < NBOX; ++q) {
+            const T* src = ore + p * N * B + q * BOX * B;
+            if (a.axis == 2) tma_store_4d(&outmap, src, x0, row, q * BOX, plane_re + p);
+            else tma_store_4d(&outmap, src, x0, q * BOX, row, plane_re + p);
+          }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+    }
+    if constexpr (MODE == 2) {
+      if (a.ref) {
+        if (tid == 0 && !mbar_wait(&bar[s], (unsigned)((s ? ph1 : ph0) & 1))) {
+          atomicOr(a.err, 1);
+          abort_flag = 1;
+        }
+        if (s) ++ph1; else ++ph0;
+        __syncthreads();
+        if (abort_flag) break;
+        const T* sre = stage0 + s * 2 * N * B;
+        T linf = acc[tid];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int pnt = (kap + 16 * q + 256 * h) * B + b;
+          linf = fmax(linf, fabs(sre[pnt] - v[q].x));
+          linf = fmax(linf, fabs(sre[N * B + pnt] - v[q].y));
+        }
+        acc[tid] = linf;
+        __syncthreads();                             // stage s read: refill with tile k + 2
+        if (tid == 0 && u + 2 * step < ntiles) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(u + 2 * step, s, &map);
+        }
+      }
+    }
+  }
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete
+  if (abort_flag) {
+    if (tid == 0) {
+      if (issued0 > 0) mbar_wait(&bar[0], (unsigned)((issued0 - 1) & 1));
+      if (issued1 > 0) mbar_wait(&bar[1], (unsigned)((issued1 - 1) & 1));
+    }
+    __syncthreads();
+    return;
+  }
+  if constexpr (MODE == 1) {
+    double r[4];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      r[j] = double(acc[(2 * j) * THREADS + tid]) - double(acc[(2 * j + 1) * THREADS + tid]);
+    r[3] = 0.0;
+    block_sum<4>(r, red);
+    if (tid == 0) {
+      double* p = a.partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 4;
+      p[0] = r[0]; p[1] = r[1]; p[2] = r[2]; p[3] = nonfinite ? 1.0 : 0.0;
+    }
+  } else if constexpr (MODE == 2) {
+    if (a.ref) {
+      double m = block_max(double(acc[tid]), red);
+      if (tid == 0) a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = m;
+    }
+  }
+}
+
 // ---- fused x pass with bulk-copy double buffering --------------------------------------
 //
 // Same work as k_xproj (forward x transform of P row pairs, projector per mode pair, inverse x
