@@ -23,11 +23,13 @@ from .projection import (project, project_literal, project_spectrum, divergence,
                          divergence_central_diff, norms, inner, frob2)
 from .fields import beltrami_field, symgrad_field, smooth_potential, inc_central_diff
 from .brute import project_bruteforce
+from .hodge import project_compat, hodge_potential
 
 __all__ = [
     "dft_axis_direct", "dft3_direct", "dft3_naive", "fft3", "ifft3",
     "wavevector", "wavevector_grids", "biharmonic_symbol_paper", "central_diff",
     "stencil25_apply", "project", "project_literal", "project_spectrum", "divergence",
     "divergence_central_diff", "norms", "inner", "frob2", "beltrami_field", "symgrad_field",
-    "smooth_potential", "inc_central_diff", "project_bruteforce",
+    "smooth_potential", "inc_central_diff", "project_bruteforce", "project_compat",
+    "hodge_potential",
 ]
