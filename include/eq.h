@@ -53,6 +53,13 @@ typedef enum { EQ_OP_DDO = 0, EQ_OP_CDO = 1 } eq_op;
  * literal Euler-Lagrange route inc(inc(S) / biharmonic) of Sec. 3.2-3.3 produces. */
 typedef enum { EQ_NYQ_KEEP = 0, EQ_NYQ_ZERO = 1 } eq_nyquist;
 
+/* What the plan returns.  EQUILIBRIUM: the closest divergence-free field S_equil (Sec. 3.2).
+ * COMPATIBILITY: the closest strain-compatible field c0 + (S - S_equil), i.e. sym grad y + c0 of
+ * the Hodge decomposition (Sec. 3.1, Theorem 2), the dual constraint named in the Conclusions;
+ * at the Nyquist corners it is 0 under KEEP and the input under ZERO.  The norms describe the
+ * returned field either way (resid = S_in - S_out, div_out of S_out). */
+typedef enum { EQ_TARGET_EQUILIBRIUM = 0, EQ_TARGET_COMPATIBILITY = 1 } eq_target;
+
 typedef struct {
   eq_op op;              /* default EQ_OP_DDO */
   double hx, hy, hz;     /* voxel spacing, default 1 (all > 0) */
@@ -60,6 +67,7 @@ typedef struct {
   int want_linf;         /* 1: also compute resid_linf (needs d_in != d_out); default 1 */
   int graph;             /* 1: capture the passes in a CUDA graph on first use of a (d_in, d_out)
                             pair and replay it while the pair is unchanged; default 1 */
+  eq_target target;      /* default EQ_TARGET_EQUILIBRIUM */
 } eq_plan_opts;
 
 /* Per-field diagnostics, FP64.  ||A|| = sqrt(mean over voxels of A:A) with A:B = sum_ij A_ij B_ij
@@ -80,7 +88,7 @@ typedef struct {
 typedef struct eq_plan eq_plan;
 typedef struct eq_server eq_server;
 
-/* Default options (DDO, unit spacing, KEEP, want_linf = 1, graph = 1). */
+/* Default options (DDO, unit spacing, KEEP, want_linf = 1, graph = 1, EQUILIBRIUM). */
 void eq_plan_opts_default(eq_plan_opts* opts);
 
 /* Create a plan for `batch` fields of one grid size.  Sizes are 1..1024 per axis (powers of two

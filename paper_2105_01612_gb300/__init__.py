@@ -23,10 +23,13 @@ __all__ = ["Plan", "VarlenPlan", "Server", "project", "eq_plan_create_varlen", "
 
 _OPS = {"ddo": _lib.EQ_OP_DDO, "cdo": _lib.EQ_OP_CDO}
 _NYQ = {"keep": _lib.EQ_NYQ_KEEP, "zero": _lib.EQ_NYQ_ZERO}
+_TARGET = {"equilibrium": _lib.EQ_TARGET_EQUILIBRIUM,
+           "compatibility": _lib.EQ_TARGET_COMPATIBILITY}
 _DT = {torch.float32: _lib.EQ_F32, torch.float64: _lib.EQ_F64}
 
 
-def _opts(op="ddo", h=(1.0, 1.0, 1.0), nyq="keep", want_linf=True, graph=True) -> EqPlanOpts:
+def _opts(op="ddo", h=(1.0, 1.0, 1.0), nyq="keep", want_linf=True, graph=True,
+          target="equilibrium") -> EqPlanOpts:
     o = EqPlanOpts()
     _lib.load().eq_plan_opts_default(ctypes.byref(o))
     o.op = _OPS[op]
@@ -34,16 +37,17 @@ def _opts(op="ddo", h=(1.0, 1.0, 1.0), nyq="keep", want_linf=True, graph=True) -
     o.nyq = _NYQ[nyq]
     o.want_linf = 1 if want_linf else 0
     o.graph = 1 if graph else 0
+    o.target = _TARGET[target]
     return o
 
 
 # ---- C-ABI names (thin marshalling) ------------------------------------------------------
 
 def eq_plan_create(nx, ny, nz, dtype=torch.float32, batch=1, op="ddo", h=(1.0, 1.0, 1.0),
-                   nyq="keep", want_linf=True) -> int:
+                   nyq="keep", want_linf=True, target="equilibrium") -> int:
     """Returns an opaque plan handle (int) on the current CUDA device."""
     handle = ctypes.c_void_p()
-    opts = _opts(op, h, nyq, want_linf)
+    opts = _opts(op, h, nyq, want_linf, target=target)
     st = _lib.load().eq_plan_create(int(nx), int(ny), int(nz), _DT[dtype], int(batch),
                                     ctypes.byref(opts), ctypes.byref(handle))
     _lib.check(st, "eq_plan_create")
@@ -51,12 +55,12 @@ def eq_plan_create(nx, ny, nz, dtype=torch.float32, batch=1, op="ddo", h=(1.0, 1
 
 
 def eq_plan_create_varlen(dims, dtype=torch.float32, op="ddo", h=(1.0, 1.0, 1.0), nyq="keep",
-                          want_linf=True) -> int:
+                          want_linf=True, target="equilibrium") -> int:
     """dims: sequence of (nx, ny, nz) per field.  Returns an opaque plan handle."""
     flat = [int(v) for d in dims for v in d]
     arr = (ctypes.c_int * len(flat))(*flat)
     handle = ctypes.c_void_p()
-    opts = _opts(op, h, nyq, want_linf)
+    opts = _opts(op, h, nyq, want_linf, target=target)
     st = _lib.load().eq_plan_create_varlen(arr, len(dims), _DT[dtype], ctypes.byref(opts),
                                            ctypes.byref(handle))
     _lib.check(st, "eq_plan_create_varlen")
@@ -107,13 +111,13 @@ class Plan:
     """A plan for `batch` fields of one grid size and dtype on one device."""
 
     def __init__(self, nx, ny, nz, dtype=torch.float32, batch=1, op="ddo", h=(1.0, 1.0, 1.0),
-                 nyq="keep", want_linf=True, device=None):
+                 nyq="keep", want_linf=True, device=None, target="equilibrium"):
         self.shape = (int(batch), 6, int(nz), int(ny), int(nx))
         self.numel = _numel(self.shape)
         self.dtype = dtype
         self.device = _cuda_device(device)
         with torch.cuda.device(self.device):
-            self.handle = eq_plan_create(nx, ny, nz, dtype, batch, op, h, nyq, want_linf)
+            self.handle = eq_plan_create(nx, ny, nz, dtype, batch, op, h, nyq, want_linf, target)
 
     def _check(self, t: torch.Tensor, name: str):
         if not t.is_cuda or t.device != self.device:
@@ -183,14 +187,14 @@ class VarlenPlan(Plan):
     """Fields of different sizes packed back to back in one flat tensor (see pack/unpack)."""
 
     def __init__(self, dims, dtype=torch.float32, op="ddo", h=(1.0, 1.0, 1.0), nyq="keep",
-                 want_linf=True, device=None):
+                 want_linf=True, device=None, target="equilibrium"):
         self.dims = [tuple(int(v) for v in d) for d in dims]
         self.dtype = dtype
         self.numel = sum(6 * nx * ny * nz for nx, ny, nz in self.dims)
         self.shape = (len(self.dims), self.numel)
         self.device = _cuda_device(device)
         with torch.cuda.device(self.device):
-            self.handle = eq_plan_create_varlen(self.dims, dtype, op, h, nyq, want_linf)
+            self.handle = eq_plan_create_varlen(self.dims, dtype, op, h, nyq, want_linf, target)
 
     def _check(self, t, name):
         if not t.is_cuda or t.device != self.device or t.dtype != self.dtype \
@@ -223,13 +227,13 @@ class Server:
         self._keep = {}
 
     def submit(self, x: torch.Tensor, out: torch.Tensor, op="ddo", h=(1.0, 1.0, 1.0),
-               nyq="keep", want_linf=True) -> int:
+               nyq="keep", want_linf=True, target="equilibrium") -> int:
         """x, out: host tensors (6, nz, ny, nx), float32/float64, contiguous (pinned is best)."""
         if x.is_cuda or out.is_cuda or x.shape != out.shape or x.dim() != 4 or x.shape[0] != 6 \
                 or x.dtype != out.dtype or not (x.is_contiguous() and out.is_contiguous()):
             raise ValueError("x and out must be contiguous host tensors of shape (6, nz, ny, nx)")
         _, nz, ny, nx = x.shape
-        opts = _opts(op, h, nyq, want_linf)
+        opts = _opts(op, h, nyq, want_linf, target=target)
         t = ctypes.c_ulonglong()
         st = _lib.load().eq_serve_submit(self.handle, nx, ny, nz, _DT[x.dtype], ctypes.byref(opts),
                                          x.data_ptr(), out.data_ptr(), ctypes.byref(t))
@@ -286,14 +290,16 @@ def _numel(shape):
     return n
 
 
-def project(x: torch.Tensor, op="ddo", h=(1.0, 1.0, 1.0), nyq="keep", out=None):
-    """Project a (6, nz, ny, nx) or (B, 6, nz, ny, nx) CUDA tensor; returns (out, norms)."""
+def project(x: torch.Tensor, op="ddo", h=(1.0, 1.0, 1.0), nyq="keep", out=None,
+            target="equilibrium"):
+    """Project a (6, nz, ny, nx) or (B, 6, nz, ny, nx) CUDA tensor; returns (out, norms).
+    target="compatibility" returns the closest strain-compatible field instead."""
     single = x.dim() == 4
     xb = x.unsqueeze(0) if single else x
     b, six, nz, ny, nx = xb.shape
     if six != 6:
         raise ValueError("expected 6 Voigt components in dimension -4")
-    plan = Plan(nx, ny, nz, x.dtype, b, op, h, nyq, device=x.device)
+    plan = Plan(nx, ny, nz, x.dtype, b, op, h, nyq, device=x.device, target=target)
     o = plan.project(xb.contiguous(), None if out is None else out.view(xb.shape))
     nrm = plan.norms()
     plan.close()

@@ -15,6 +15,7 @@ EQ_ERR_BUSY, EQ_PENDING, EQ_ERR_NOT_FOUND = 5, 6, 7
 EQ_F32, EQ_F64 = 0, 1
 EQ_OP_DDO, EQ_OP_CDO = 0, 1
 EQ_NYQ_KEEP, EQ_NYQ_ZERO = 0, 1
+EQ_TARGET_EQUILIBRIUM, EQ_TARGET_COMPATIBILITY = 0, 1
 EQ_FLAG_NONFINITE, EQ_FLAG_NO_LINF = 1, 2
 EQ_NUM_PASSES = 7
 PASS_NAMES = ["z_forward", "mean_finalise", "y_forward", "x_fwd_project_inv", "y_inverse",
@@ -26,7 +27,7 @@ STATUS_NAMES = {0: "EQ_OK", 1: "EQ_ERR_INVALID", 2: "EQ_ERR_OOM", 3: "EQ_ERR_CUD
 
 class EqPlanOpts(ctypes.Structure):
     _fields_ = [("op", c_int), ("hx", c_double), ("hy", c_double), ("hz", c_double),
-                ("nyq", c_int), ("want_linf", c_int), ("graph", c_int)]
+                ("nyq", c_int), ("want_linf", c_int), ("graph", c_int), ("target", c_int)]
 
 
 class EqNorms(ctypes.Structure):

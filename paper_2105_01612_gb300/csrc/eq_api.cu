@@ -415,6 +415,7 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     x.npairs = p->npairs;
     x.ngroups = (p->npairs + p->tx.cols - 1) / p->tx.cols;
     x.nyq_zero = p->opts.nyq == EQ_NYQ_ZERO;
+    x.compat = p->opts.target == EQ_TARGET_COMPATIBILITY;
     x.inv_v = 1.0 / double(V);
     dim3 grid(p->gtx, p->batch);
     e = f32 ? eqk::launch_xtma_f32(p->nx, p->vx, x, grid, s) : eqk::launch_xtma_f64(p->nx, p->vx, x, grid, s);
@@ -431,6 +432,7 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     const int P = p->info_x.threads / (6 * tpc);
     x.ngroups = (p->npairs + P - 1) / P;
     x.nyq_zero = p->opts.nyq == EQ_NYQ_ZERO;
+    x.compat = p->opts.target == EQ_TARGET_COMPATIBILITY;
     x.inv_v = 1.0 / double(V);
     dim3 grid(p->gx, p->batch);
     e = f32 ? eqk::launch_xproj_f32(p->nx, x, grid, s) : eqk::launch_xproj_f64(p->nx, x, grid, s);
@@ -523,6 +525,7 @@ void eq_plan_opts_default(eq_plan_opts* o) {
   o->nyq = EQ_NYQ_KEEP;
   o->want_linf = 1;
   o->graph = 1;
+  o->target = EQ_TARGET_EQUILIBRIUM;
 }
 
 const char* eq_last_error(void) { return g_last_error.c_str(); }
@@ -533,6 +536,8 @@ static eq_status check_opts(const eq_plan_opts* opts, eq_plan_opts* o, const cha
   if (o->op != EQ_OP_DDO && o->op != EQ_OP_CDO) return fail(EQ_ERR_INVALID, std::string(who) + ": bad op");
   if (o->nyq != EQ_NYQ_KEEP && o->nyq != EQ_NYQ_ZERO)
     return fail(EQ_ERR_INVALID, std::string(who) + ": bad nyquist policy");
+  if (o->target != EQ_TARGET_EQUILIBRIUM && o->target != EQ_TARGET_COMPATIBILITY)
+    return fail(EQ_ERR_INVALID, std::string(who) + ": bad target");
   if (!(o->hx > 0.0) || !(o->hy > 0.0) || !(o->hz > 0.0) || !std::isfinite(o->hx) ||
       !std::isfinite(o->hy) || !std::isfinite(o->hz))
     return fail(EQ_ERR_INVALID, std::string(who) + ": spacing must be finite and > 0");

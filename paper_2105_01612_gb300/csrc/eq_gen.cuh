@@ -69,6 +69,7 @@ struct GenArgs {
   int pitch;               // shared-memory pitch (>= C)
   int mmax;                // largest transform length among the fields
   int nyq_zero;
+  int compat;              // 1: return the compatible part c0 + (S - S_equil)
 };
 
 // ---- small DFTs -------------------------------------------------------------------------
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(512) k_gen_xproj(const GenArgs a) {
         }
         const bool selfmode = self2 && kx == kxm;
         eqk::project_pair<T>(av, bv, xix[kx], xiy[ky], xiz[kz], rA == 0 && kx == 0, mean, vol,
-                             a.nyq_zero != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
+                             a.nyq_zero != 0, a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           r[kx * pitch + colA + c] = av[c];

@@ -541,6 +541,7 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   a.fields = g->fields; a.axes = g->axes; a.cpool = g->cpool; a.xipool = g->xipool;
   a.pairpool = g->pairpool; a.mean = g->mean; a.nfields = g->F;
   a.nyq_zero = g->opts.nyq == EQ_NYQ_ZERO;
+  a.compat = g->opts.target == EQ_TARGET_COMPATIBILITY;
   auto shape = [&](const PassShape& p) {
     a.item0 = p.item0; a.nitems = p.nitems; a.tiles_per_item = p.tpi; a.cols = p.cols;
     a.pitch = p.pitch; a.mmax = p.mmax;
@@ -664,6 +665,7 @@ static float time_pass(GenPlan* g, int which, const void* d_in, void* d_out, cud
   a.fields = g->fields; a.axes = g->axes; a.cpool = g->cpool; a.xipool = g->xipool;
   a.pairpool = g->pairpool; a.mean = g->mean; a.nfields = g->F;
   a.nyq_zero = g->opts.nyq == EQ_NYQ_ZERO;
+  a.compat = g->opts.target == EQ_TARGET_COMPATIBILITY;
   const PassShape& p = which == 0 ? g->z : (which == 1 ? g->y : g->x);
   a.item0 = p.item0; a.nitems = p.nitems; a.tiles_per_item = p.tpi; a.cols = p.cols;
   a.pitch = p.pitch; a.mmax = p.mmax;

@@ -70,6 +70,7 @@ struct XArgs {
   int npairs;
   int ngroups;
   int nyq_zero;
+  int compat;              // 1: return the compatible part c0 + (S - S_equil)
   double inv_v;            // 1 / (nx ny nz)
 };
 
@@ -207,6 +208,8 @@ __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
 // The per-mode projector and its norm terms for one mode pair (k, -k).
 //   in:  a[c] = Z_c(k), bb[c] = Z_c(-k)  (c = 0..2)
 //   out: a[c] <- Zout_c(k) / V,  bb[c] <- Zout_c(-k) / V
+// Zout is the projected field Q S Q, or with `compat` its complement S - Q S Q (the mean, at
+// k = 0, is kept either way).
 // Works on twice the Voigt components (the unpack's 1/2 is folded into the repack and into the
 // norm weights).  With n = xi / |xi|, v = S n and s = n . v, the projector removes
 // D = n (x) v + v (x) n - s n (x) n, whose squared Frobenius norm is 2 |v|^2 - s^2 (no
@@ -214,7 +217,7 @@ __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
 template <typename T, typename T2>
 __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T xi1, T xi2,
                                              bool zero_mode, const double* mean, double vol,
-                                             bool nyq_zero, T inv_v, T mult,
+                                             bool nyq_zero, bool compat, T inv_v, T mult,
                                              Kahan<T>& r2, Kahan<T>& di2, Kahan<T>& do2,
                                              Kahan<T>& o2) {
   // 2 S_2c = A + conj B, 2 S_2c+1 = -i (A - conj B)
@@ -269,6 +272,18 @@ __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T x
       orr[j] = drop ? T(0) : sr[j];
       oi[j] = drop ? T(0) : si[j];
     }
+  }
+  // compatible part: out = S - O away from k = 0; the residual S - out is then O
+  if (compat && !zero_mode) {
+    T o2n = T(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const T w = j < 3 ? T(1) : T(2);
+      o2n += w * (orr[j] * orr[j] + oi[j] * oi[j]);
+      orr[j] = sr[j] - orr[j];
+      oi[j] = si[j] - oi[j];
+    }
+    rr = o2n;
   }
   // norm terms (sums of |.|^2 over modes; Parseval turns them into voxel means)
   {
@@ -382,7 +397,7 @@ k_xproj(const XArgs a) {
       const bool selfmode = self2 && kx == kxm;
       const bool zero_mode = (rA == 0) && kx == 0;
       project_pair<T>(av, bv, xix[kx], xiy[ky], xiz[kz], zero_mode, mean, vol, a.nyq_zero != 0,
-                      inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
+                      a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         buf[(colA + c) * PITCH + kx + (kx >> 3)] = av[c];

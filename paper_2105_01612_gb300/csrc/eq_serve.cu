@@ -48,11 +48,11 @@ struct Request {
   eq_norms_t norms{};
 };
 
-using PlanKey = std::tuple<int, int, int, int, int, double, double, double, int, int>;
+using PlanKey = std::tuple<int, int, int, int, int, double, double, double, int, int, int>;
 
 PlanKey key_of(const Request& r) {
   return PlanKey(r.nx, r.ny, r.nz, (int)r.dtype, (int)r.opts.op, r.opts.hx, r.opts.hy, r.opts.hz,
-                 (int)r.opts.nyq, r.opts.want_linf);
+                 (int)r.opts.nyq, r.opts.want_linf, (int)r.opts.target);
 }
 
 struct Slot {

@@ -88,6 +88,7 @@ extern "C" eq_status eq_project_static(int nx, int ny, int nz, const eq_plan_opt
   eq_plan_opts_default(&o);
   if (opts) o = *opts;
   if ((o.op != EQ_OP_DDO && o.op != EQ_OP_CDO) || (o.nyq != EQ_NYQ_KEEP && o.nyq != EQ_NYQ_ZERO) ||
+      (o.target != EQ_TARGET_EQUILIBRIUM && o.target != EQ_TARGET_COMPATIBILITY) ||
       !(o.hx > 0.0) || !(o.hy > 0.0) || !(o.hz > 0.0))
     return sfail(EQ_ERR_INVALID, "eq_project_static: bad options");
   const long long V = (long long)nx * ny * nz;
@@ -189,6 +190,7 @@ extern "C" eq_status eq_project_static(int nx, int ny, int nz, const eq_plan_opt
   x.pairs = pairs; x.mean = mean; x.partials = partx; x.field_stride = 6 * V; x.V = V;
   x.nx = nx; x.ny = ny; x.nz = nz; x.npairs = npairs; x.ngroups = (npairs + P - 1) / P;
   x.nyq_zero = o.nyq == EQ_NYQ_ZERO; x.inv_v = 1.0 / double(V);
+  x.compat = o.target == EQ_TARGET_COMPATIBILITY;
   if ((e = eqk::launch_xproj_f32(nx, x, dim3(gx, 1), s)) != cudaSuccess)
     return sfail(EQ_ERR_CUDA, std::string("eq_project_static: x pass: ") + cudaGetErrorString(e));
   if ((e = eqk::launch_strided_f32(ny, true, ay, dim3(gy, 3), s)) != cudaSuccess)

@@ -612,6 +612,7 @@ struct XTmaArgs {
   int nx, ny, nz;
   int npairs, ngroups;
   int nyq_zero;
+  int compat;              // 1: return the compatible part c0 + (S - S_equil)
   double inv_v;
 };
 
@@ -766,7 +767,7 @@ k_xproj_tma(const XTmaArgs a) {
       }
       const bool selfmode = self2 && kx == kxm;
       project_pair<T>(av, bv, xix[kx], rxi[s][s2][0], rxi[s][s2][1], rA == 0 && kx == 0, mean, vol,
-                      a.nyq_zero != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
+                      a.nyq_zero != 0, a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         xre[(colA + c) * PF + ja] = av[c].x;
@@ -990,7 +991,7 @@ k_xproj_warp(const XTmaArgs a) {
       }
       const bool selfmode = self && kx == kxm;
       project_pair<T>(av, bv, xix[kx], rxi[s][0], rxi[s][1], rA == 0 && kx == 0, mean, vol,
-                      a.nyq_zero != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
+                      a.nyq_zero != 0, a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         T* ra = rows + (2 * c) * N;

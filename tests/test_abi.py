@@ -47,24 +47,33 @@ def test_struct_layout_matches_the_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "eq.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(eq_plan_opts),"
-        " offsetof(eq_plan_opts, nyq), sizeof(eq_norms_t), offsetof(eq_norms_t, resid_linf),"
-        " offsetof(eq_norms_t, flags), offsetof(eq_norms_t, div_out_l2)); return 0;}\n")
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(eq_plan_opts),"
+        " offsetof(eq_plan_opts, nyq), offsetof(eq_plan_opts, target), sizeof(eq_norms_t),"
+        " offsetof(eq_norms_t, resid_linf), offsetof(eq_norms_t, flags),"
+        " offsetof(eq_norms_t, div_out_l2)); return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", INCLUDE, str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                           check=True).stdout.split()]
-    want = [ctypes.sizeof(EqPlanOpts), EqPlanOpts.nyq.offset, ctypes.sizeof(EqNorms),
-            EqNorms.resid_linf.offset, EqNorms.flags.offset, EqNorms.div_out_l2.offset]
+    want = [ctypes.sizeof(EqPlanOpts), EqPlanOpts.nyq.offset, EqPlanOpts.target.offset,
+            ctypes.sizeof(EqNorms), EqNorms.resid_linf.offset, EqNorms.flags.offset,
+            EqNorms.div_out_l2.offset]
     assert got == want
 
 
 def test_defaults_and_argument_validation_without_a_gpu(lib):
-    from paper_2105_01612_gb300._lib import EqPlanOpts, EQ_ERR_INVALID, EQ_OP_DDO, EQ_NYQ_KEEP
+    from paper_2105_01612_gb300._lib import (EqPlanOpts, EQ_ERR_INVALID, EQ_OP_DDO, EQ_NYQ_KEEP,
+                                            EQ_TARGET_EQUILIBRIUM)
     o = EqPlanOpts()
     lib.eq_plan_opts_default(ctypes.byref(o))
-    assert (o.op, o.hx, o.hy, o.hz, o.nyq, o.want_linf, o.graph) == \
-        (EQ_OP_DDO, 1.0, 1.0, 1.0, EQ_NYQ_KEEP, 1, 1)
+    assert (o.op, o.hx, o.hy, o.hz, o.nyq, o.want_linf, o.graph, o.target) == \
+        (EQ_OP_DDO, 1.0, 1.0, 1.0, EQ_NYQ_KEEP, 1, 1, EQ_TARGET_EQUILIBRIUM)
+    bad = EqPlanOpts()
+    lib.eq_plan_opts_default(ctypes.byref(bad))
+    bad.target = 5
+    assert lib.eq_plan_create(64, 64, 64, 0, 1, ctypes.byref(bad), ctypes.byref(ctypes.c_void_p())) \
+        == EQ_ERR_INVALID
+    assert b"target" in lib.eq_last_error()
     h = ctypes.c_void_p()
     # unsupported length, bad batch, bad spacing, NULL out: rejected before any CUDA call
     assert lib.eq_plan_create(2048, 64, 64, 0, 1, None, ctypes.byref(h)) == EQ_ERR_INVALID
