@@ -116,6 +116,18 @@ eq_status eq_plan_create_varlen(const int* dims, int count, eq_dtype dtype,
  * DFT, per-mode projector, inverse DFT, norms; the mean is taken in FP64. */
 eq_status eq_project(eq_plan* plan, const void* d_in, void* d_out, void* cuda_stream);
 
+/* eq_project plus the vector field y of the Hodge decomposition (Sec. 3.1, Theorem 2):
+ * S = inc(H) + sym grad y + c0, so sym grad y = S - S_equil with the plan's operator as the
+ * derivative.  y is periodic and mean-free; it is 0 at the modes where the operator vanishes.
+ * d_out receives exactly what eq_project writes (same kernels, same target); d_y (device, the
+ * plan's dtype, 16-byte aligned, disjoint from d_in and d_out) holds batch * 4 * nx * ny * nz
+ * elements: per field the planes y_x, y_y, y_z and one working plane that ends near zero.
+ * Power-of-two plans only (EQ_ERR_INVALID otherwise).  Extra cost: one x pass reading the
+ * spectrum and two strided passes over the 4-plane buffer.  Their times are counted in the x
+ * and z-inverse slots of eq_plan_pass_ms. */
+eq_status eq_project_hodge(eq_plan* plan, const void* d_in, void* d_out, void* d_y,
+                           void* cuda_stream);
+
 /* Same as eq_project with host buffers: copies host_in to a plan-owned device buffer
  * (allocated on first use, 2 x field bytes), projects, copies back to host_out, and waits for
  * completion.  Host buffers should be pinned for full copy bandwidth. */

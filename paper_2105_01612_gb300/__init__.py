@@ -75,6 +75,12 @@ def eq_project_host(plan: int, h_in: int, h_out: int, stream: int = 0) -> None:
     _lib.check(_lib.load().eq_project_host(plan, h_in, h_out, stream or None), "eq_project_host")
 
 
+def eq_project_hodge(handle, d_in, d_out, d_y, stream) -> None:
+    _lib.check(_lib.load().eq_project_hodge(ctypes.c_void_p(handle), ctypes.c_void_p(d_in),
+                                            ctypes.c_void_p(d_out), ctypes.c_void_p(d_y),
+                                            ctypes.c_void_p(stream)), "eq_project_hodge")
+
+
 def eq_norms(plan: int, batch: int) -> list:
     arr = (EqNorms * batch)()
     _lib.check(_lib.load().eq_norms(plan, arr), "eq_norms")
@@ -135,6 +141,26 @@ class Plan:
         with torch.cuda.device(self.device):
             eq_project(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
         return out
+
+    def project_hodge(self, x: torch.Tensor, out: torch.Tensor | None = None,
+                      y: torch.Tensor | None = None, stream=None):
+        """Projection plus the Hodge potential: returns (out, y), y of shape (batch, 4, nz, ny, nx)
+        with y_x, y_y, y_z in planes 0..2 (plane 3 is working space)."""
+        self._check(x, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        if y is None:
+            b, _, nz, ny, nx = self.shape
+            y = torch.empty((b, 4, nz, ny, nx), dtype=self.dtype, device=self.device)
+        self._check(out, "out")
+        if not y.is_cuda or y.device != self.device or y.dtype != self.dtype \
+                or not y.is_contiguous() or y.numel() != self.numel // 6 * 4:
+            raise ValueError(f"y must be a contiguous {self.dtype} tensor of shape "
+                             f"{(self.shape[0], 4) + self.shape[2:]} on {self.device}")
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            eq_project_hodge(self.handle, x.data_ptr(), out.data_ptr(), y.data_ptr(), s.cuda_stream)
+        return out, y
 
     def project_host(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
         """Host tensors in and out (pinned for full bandwidth); blocks until done."""

@@ -160,6 +160,7 @@ struct eq_plan {
   cudaGraphExec_t gexec = nullptr;
   const void* g_in = nullptr;
   void* g_out = nullptr;
+  void* g_y = nullptr;
 };
 
 namespace {
@@ -247,14 +248,15 @@ EncodeTiled encode_fn() {
   return fn;
 }
 
-// 4-D view (x, y, z, plane) of a buffer of `planes` planes; box of `cols` x values and `box`
-// points along the transformed axis (2 = z, 1 = y).
-bool make_map(CUtensorMap* m, const void* base, const eq_plan* p, int axis, int cols, int box) {
+// 4-D view (x, y, z, plane) of a buffer of `planes` planes (6 per stress field, 4 per potential
+// field); box of `cols` x values and `box` points along the transformed axis (2 = z, 1 = y).
+bool make_map(CUtensorMap* m, const void* base, const eq_plan* p, int axis, int cols, int box,
+              int planes) {
   EncodeTiled enc = encode_fn();
   if (!enc || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
   const cuuint64_t es = p->esize;
   const cuuint64_t dims[4] = {(cuuint64_t)p->nx, (cuuint64_t)p->ny, (cuuint64_t)p->nz,
-                              (cuuint64_t)(6 * p->batch)};
+                              (cuuint64_t)planes};
   const cuuint64_t strides[3] = {p->nx * es, (cuuint64_t)p->nx * p->ny * es, (cuuint64_t)p->V * es};
   const cuuint32_t boxd[4] = {(cuuint32_t)cols, axis == 1 ? (cuuint32_t)box : 1u,
                               axis == 2 ? (cuuint32_t)box : 1u, 1u};
@@ -303,14 +305,16 @@ void tma_setup(eq_plan* p, int vz, int vy, int vx) {
 }
 
 // Strided pass along `axis` through the TMA kernel; false if not applicable for these buffers.
+// ncomp: complex fields per field of the buffers (3 for stress fields, 2 for the potential).
 bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src, void* dst,
-             const void* ref, double* partials, cudaStream_t s, cudaError_t* e) {
+             const void* ref, double* partials, cudaStream_t s, cudaError_t* e, int ncomp = 3) {
   if (!on) return false;
   const eqk::TmaInfo& ti = axis == 2 ? p->tz : p->ty;
   CUtensorMap map, refmap, outmap;
-  if (!make_map(&map, src, p, axis, ti.cols, ti.box) ||
-      (ref && !make_map(&refmap, ref, p, axis, ti.cols, ti.box)) ||
-      (dst != src && !make_map(&outmap, dst, p, axis, ti.cols, ti.box))) {
+  const int planes = 2 * ncomp * p->batch;
+  if (!make_map(&map, src, p, axis, ti.cols, ti.box, planes) ||
+      (ref && !make_map(&refmap, ref, p, axis, ti.cols, ti.box, planes)) ||
+      (dst != src && !make_map(&outmap, dst, p, axis, ti.cols, ti.box, planes))) {
     *e = cudaErrorInvalidValue;
     return true;
   }
@@ -318,9 +322,9 @@ bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src,
   if (dst == src) outmap = map;
   eqk::TmaArgs t{};
   t.ref = ref; t.out = dst; t.tw = p->tw[axis]; t.partials = partials; t.err = p->err;
-  t.field_stride = 6 * p->V; t.V = p->V;
+  t.field_stride = 2LL * ncomp * p->V; t.V = p->V;
   t.nx = p->nx; t.ny = p->ny; t.nz = p->nz;
-  t.axis = axis; t.mode = mode;
+  t.axis = axis; t.mode = mode; t.ncomp = ncomp;
   // TMA stores through the exchange buffer: measured faster for the z passes (the 16 x 32
   // kernel: both; the wide tiles: the last one) and slower for the y passes.  EQ_TMA_STORE
   // overrides for measurements (0 never, 1 last z pass, 2 every z pass, 3 every pass).
@@ -333,7 +337,10 @@ bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src,
     else t.tma_store = ts == 3 || (axis == 2 && (ts == 2 || (ts == 1 && mode == 2)));
   }
   t.ntiles = (axis == 2 ? (long long)p->ny : (long long)p->nz) * (p->nx / ti.cols);
-  dim3 grid(axis == 2 ? p->gtz : p->gty, p->batch * 3);
+  // one resident wave over (field, component) pairs: the plan's grid is sized for three
+  const long long g3 = axis == 2 ? p->gtz : p->gty;
+  const long long gx = std::max(1LL, std::min<long long>(g3 * 3 / ncomp, t.ntiles));
+  dim3 grid((unsigned)(ncomp == 3 ? g3 : gx), p->batch * ncomp);
   const int n = axis == 2 ? p->nz : p->ny;
   const int v = axis == 2 ? p->vz : p->vy;
   *e = p->dtype == EQ_F32 ? eqk::launch_tma_f32(n, v, inv, map, refmap, outmap, t, grid, s)
@@ -341,7 +348,9 @@ bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src,
   return true;
 }
 
-eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
+// d_y (nullable): also write the Hodge potential y into this 4-plane-per-field buffer (a
+// potential x pass before the projector, then y and z inverse passes over the buffer).
+eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, void* d_y = nullptr) {
   const bool f32 = p->dtype == EQ_F32;
   cudaEvent_t* ev = nullptr;
   if (p->tused < p->tcap) ev = &p->tev[(size_t)p->tused++ * (EQ_NUM_PASSES + 1)];
@@ -371,7 +380,7 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     a.ncols = a.inner;
     const int B = p->info_z_f.threads / std::max(1, p->nz / std::min(8, p->nz));
     a.ntiles = (a.ncols + B - 1) / B;
-    a.partials = p->part1; a.mode = 1;
+    a.partials = p->part1; a.mode = 1; a.ncomp = 3;
     dim3 grid(p->g1, p->batch * 3);
     if (!try_tma(p, on_z, 2, false, 1, d_in, d_out, nullptr, p->part1, s, &e))
       e = f32 ? eqk::launch_strided_f32(p->nz, false, a, grid, s)
@@ -393,7 +402,7 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     const int B = p->info_y_f.threads / std::max(1, p->ny / std::min(8, p->ny));
     ay.ntiles = (ay.ncols + B - 1) / B;
   }
-  ay.partials = nullptr; ay.mode = 0;
+  ay.partials = nullptr; ay.mode = 0; ay.ncomp = 3;
   {
     dim3 grid(p->gy, p->batch * 3);
     if (!try_tma(p, on_y, 1, false, 0, d_out, d_out, nullptr, nullptr, s, &e))
@@ -402,6 +411,24 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
     if (e != cudaSuccess) return fail_cuda(e, "y forward pass");
   }
   mark(3);
+  // potential x pass (reads the spectrum before the projector rewrites it)
+  if (d_y) {
+    eqk::XArgs x{};
+    x.data = d_out; x.tw = p->tw[0];
+    x.xi_x = p->xi[0]; x.xi_y = p->xi[1]; x.xi_z = p->xi[2];
+    x.pairs = p->pairs;
+    x.field_stride = fstride; x.V = V;
+    x.nx = p->nx; x.ny = p->ny; x.nz = p->nz;
+    x.npairs = p->npairs;
+    const int tpc = p->nx / std::min(8, p->nx);
+    const int P = p->info_x.threads / (6 * tpc);
+    x.ngroups = (p->npairs + P - 1) / P;
+    x.inv_v = 1.0 / double(V);
+    x.ydata = d_y; x.yfield_stride = 4 * V;
+    dim3 grid(p->gx, p->batch);
+    e = f32 ? eqk::launch_xpot_f32(p->nx, x, grid, s) : eqk::launch_xpot_f64(p->nx, x, grid, s);
+    if (e != cudaSuccess) return fail_cuda(e, "potential x pass");
+  }
   // pass 3: x forward + projector + x inverse
   const bool on_x = p->tma_x && !(reinterpret_cast<uintptr_t>(d_out) & 15);
   const int gx_used = on_x ? p->gtx : p->gx;
@@ -460,6 +487,23 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
               : eqk::launch_strided_f64(p->nz, true, az, grid, s);
     if (e != cudaSuccess) return fail_cuda(e, "z inverse pass");
   }
+  // potential: y and z inverse over the y buffer (two complex fields per field), in place
+  if (d_y) {
+    const bool on_ypot = !(reinterpret_cast<uintptr_t>(d_y) & 15);
+    eqk::StridedArgs py = ay;
+    py.in = d_y; py.out = d_y; py.field_stride = 4 * V; py.ncomp = 2;
+    if (!try_tma(p, p->tma_y && on_ypot, 1, true, 0, d_y, d_y, nullptr, nullptr, s, &e, 2))
+      e = f32 ? eqk::launch_strided_f32(p->ny, true, py, dim3(p->gy, p->batch * 2), s)
+              : eqk::launch_strided_f64(p->ny, true, py, dim3(p->gy, p->batch * 2), s);
+    if (e != cudaSuccess) return fail_cuda(e, "potential y inverse pass");
+    eqk::StridedArgs pz = a;
+    pz.in = d_y; pz.out = d_y; pz.ref = nullptr; pz.partials = nullptr; pz.mode = 0;
+    pz.field_stride = 4 * V; pz.ncomp = 2;
+    if (!try_tma(p, p->tma_z && on_ypot, 2, true, 0, d_y, d_y, nullptr, nullptr, s, &e, 2))
+      e = f32 ? eqk::launch_strided_f32(p->nz, true, pz, dim3(p->gl, p->batch * 2), s)
+              : eqk::launch_strided_f64(p->nz, true, pz, dim3(p->gl, p->batch * 2), s);
+    if (e != cudaSuccess) return fail_cuda(e, "potential z inverse pass");
+  }
   mark(6);
   k_finalize_norms<<<p->batch, 256, 0, s>>>(p->partx, gx_used, linf ? p->partl : nullptr, gl_used,
                                             p->batch, double(V), p->mean, p->instats,
@@ -471,17 +515,17 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
 
 // Enqueue one projection: replay the plan's captured CUDA graph when the buffers are the ones it
 // was captured with (capturing it first if not), or launch the passes directly when timing.
-eq_status run(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
+eq_status run(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, void* d_y = nullptr) {
   cudaError_t e;
   const bool timed = p->tused < p->tcap;
   if (p->opts.graph && !timed) {
-    if (!p->gexec || p->g_in != d_in || p->g_out != d_out) {
+    if (!p->gexec || p->g_in != d_in || p->g_out != d_out || p->g_y != d_y) {
       if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
       if (!p->cap && (e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess)
         return fail_cuda(e, "capture stream");
       if ((e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return fail_cuda(e, "begin capture");
-      eq_status st = enqueue(p, d_in, d_out, p->cap);
+      eq_status st = enqueue(p, d_in, d_out, p->cap, d_y);
       cudaGraph_t graph = nullptr;
       e = cudaStreamEndCapture(p->cap, &graph);
       if (st != EQ_OK) { if (graph) cudaGraphDestroy(graph); return st; }
@@ -491,10 +535,11 @@ eq_status run(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s) {
       if (e != cudaSuccess) { p->gexec = nullptr; return fail_cuda(e, "graph instantiate"); }
       p->g_in = d_in;
       p->g_out = d_out;
+      p->g_y = d_y;
     }
     if ((e = cudaGraphLaunch(p->gexec, s)) != cudaSuccess) return fail_cuda(e, "graph launch");
   } else {
-    eq_status st = enqueue(p, d_in, d_out, s);
+    eq_status st = enqueue(p, d_in, d_out, s, d_y);
     if (st != EQ_OK) return st;
   }
   if ((e = cudaEventRecord(p->done, s)) != cudaSuccess) return fail_cuda(e, "event record");
@@ -766,6 +811,25 @@ eq_status eq_project(eq_plan* p, const void* d_in, void* d_out, void* stream) {
   cudaGetDevice(&dev);
   if (dev != p->device) return fail(EQ_ERR_INVALID, "eq_project: current device differs from the plan's");
   return run(p, d_in, d_out, static_cast<cudaStream_t>(stream));
+}
+
+eq_status eq_project_hodge(eq_plan* p, const void* d_in, void* d_out, void* d_y, void* stream) {
+  if (!p || !d_in || !d_out || !d_y) return fail(EQ_ERR_INVALID, "eq_project_hodge: NULL argument");
+  if (p->gen)
+    return fail(EQ_ERR_INVALID, "eq_project_hodge: needs a plan with power-of-two axis lengths");
+  const size_t bytes = (size_t)p->total_elems * p->esize;
+  const size_t ybytes = bytes / 6 * 4;
+  const uintptr_t i0 = (uintptr_t)d_in, o0 = (uintptr_t)d_out, y0 = (uintptr_t)d_y;
+  if (i0 != o0 && i0 < o0 + bytes && o0 < i0 + bytes)
+    return fail(EQ_ERR_INVALID, "eq_project_hodge: d_in and d_out overlap without being equal");
+  if ((y0 < i0 + bytes && i0 < y0 + ybytes) || (y0 < o0 + bytes && o0 < y0 + ybytes))
+    return fail(EQ_ERR_INVALID, "eq_project_hodge: d_y overlaps d_in or d_out");
+  if ((i0 % p->esize) || (o0 % p->esize) || (y0 % p->esize))
+    return fail(EQ_ERR_INVALID, "eq_project_hodge: buffers not aligned to the element size");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device) return fail(EQ_ERR_INVALID, "eq_project_hodge: current device differs from the plan's");
+  return run(p, d_in, d_out, static_cast<cudaStream_t>(stream), d_y);
 }
 
 eq_status eq_project_host(eq_plan* p, const void* h_in, void* h_out, void* stream) {

@@ -12,6 +12,11 @@ template <typename T, int N> struct Inst {
       fn = reinterpret_cast<const void*>(&k_xproj<T, N>);
       out->threads = C::X_THREADS;
       out->smem = C::X_SMEM;
+      // the potential x pass has the same shape
+      cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_xpot<T, N>),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)out->smem);
+      if (e != cudaSuccess) return e;
     } else {
       fn = kind == PASS_STRIDED_INV ? reinterpret_cast<const void*>(&k_strided<T, N, true>)
                                     : reinterpret_cast<const void*>(&k_strided<T, N, false>);
@@ -33,6 +38,11 @@ template <typename T, int N> struct Inst {
   static cudaError_t xproj(const XArgs& a, dim3 grid, cudaStream_t s) {
     using C = Cfg<T, N>;
     k_xproj<T, N><<<grid, C::X_THREADS, C::X_SMEM, s>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t xpot(const XArgs& a, dim3 grid, cudaStream_t s) {
+    using C = Cfg<T, N>;
+    k_xpot<T, N><<<grid, C::X_THREADS, C::X_SMEM, s>>>(a);
     return cudaGetLastError();
   }
 };
@@ -197,6 +207,14 @@ template <typename T>
 cudaError_t strided_t(int n, bool inv, const StridedArgs& a, dim3 grid, cudaStream_t s) {
   switch (n) {
 #define EQ_CASE(N) case N: return Inst<T, N>::strided(inv, a, grid, s);
+    EQ_FOR_LENGTHS(EQ_CASE)
+#undef EQ_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T> cudaError_t xpot_t(int n, const XArgs& a, dim3 grid, cudaStream_t s) {
+  switch (n) {
+#define EQ_CASE(N) case N: return Inst<T, N>::xpot(a, grid, s);
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;

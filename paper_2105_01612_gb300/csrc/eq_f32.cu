@@ -9,6 +9,9 @@ cudaError_t launch_strided_f32(int n, bool inv, const StridedArgs& a, dim3 grid,
 cudaError_t launch_xproj_f32(int n, const XArgs& a, dim3 grid, cudaStream_t s) {
   return xproj_t<float>(n, a, grid, s);
 }
+cudaError_t launch_xpot_f32(int n, const XArgs& a, dim3 grid, cudaStream_t s) {
+  return xpot_t<float>(n, a, grid, s);
+}
 cudaError_t tma_info_f32(int n, int v, TmaInfo* out) { return tma_info_t<float>(n, v, out); }
 cudaError_t launch_tma_f32(int n, int v, bool inv, const CUtensorMap& map, const CUtensorMap& refmap,
                            const CUtensorMap& outmap, const TmaArgs& a, dim3 grid, cudaStream_t s) {

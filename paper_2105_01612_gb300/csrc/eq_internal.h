@@ -29,6 +29,9 @@ cudaError_t launch_strided_f32(int n, bool inv, const StridedArgs& a, dim3 grid,
 cudaError_t launch_strided_f64(int n, bool inv, const StridedArgs& a, dim3 grid, cudaStream_t s);
 cudaError_t launch_xproj_f32(int n, const XArgs& a, dim3 grid, cudaStream_t s);
 cudaError_t launch_xproj_f64(int n, const XArgs& a, dim3 grid, cudaStream_t s);
+// potential x pass (reads the stress spectrum, writes the x-inverted y rows; XArgs::ydata)
+cudaError_t launch_xpot_f32(int n, const XArgs& a, dim3 grid, cudaStream_t s);
+cudaError_t launch_xpot_f64(int n, const XArgs& a, dim3 grid, cudaStream_t s);
 
 // TMA-fed strided passes: info returns cudaErrorInvalidValue when no instance exists for n.
 // v selects the shape variant (0: wide tiles, one block per SM; 1: narrow tiles, two blocks).

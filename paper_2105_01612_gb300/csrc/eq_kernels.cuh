@@ -53,6 +53,7 @@ struct StridedArgs {
   long long ntiles;        // ceil(ncols / B)
   double* partials;        // first: [batch][3][grid][4]; last: [batch][3][grid] (linf)
   int mode;                // 0 = middle pass, 1 = first (reductions), 2 = last
+  int ncomp;               // complex fields (pairs of planes) per field: 3 (stress), 2 (potential)
 };
 
 struct XArgs {
@@ -72,6 +73,8 @@ struct XArgs {
   int nyq_zero;
   int compat;              // 1: return the compatible part c0 + (S - S_equil)
   double inv_v;            // 1 / (nx ny nz)
+  void* ydata;             // potential pass: field 0, plane 0 of the 4-plane y buffer
+  long long yfield_stride; // elements between fields of the y buffer (4 V)
 };
 
 // deterministic block sum of K doubles per thread; result valid in thread 0
@@ -138,7 +141,7 @@ k_strided(const StridedArgs a) {
   __syncthreads();
 
   const int b = threadIdx.x % B, t = threadIdx.x / B;
-  const int field = blockIdx.y / 3, comp = blockIdx.y % 3;
+  const int field = blockIdx.y / a.ncomp, comp = blockIdx.y % a.ncomp;
   const long long fbase = field * a.field_stride + (2LL * comp) * a.V;
   const T* in_re = reinterpret_cast<const T*>(a.in) + fbase;
   const T* in_im = in_re + a.V;
@@ -318,6 +321,56 @@ __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T x
   }
 }
 
+// The Hodge potential y of one mode pair (k, -k) (Theorem 2): with n = xi / |xi|, v = S n and
+// s = n . v, sym grad y reaches the part the projector removes when
+// y_hat = -(i / |xi|) (2 v - s n); y_hat = 0 where xi = 0 (k = 0 and the Nyquist corners).
+//   in:  a[c] = Z_c(k), bb[c] = Z_c(-k) of the stress spectrum (c = 0..2), as in project_pair
+//   out: packed y spectra scaled by 1 / V: y01 = y0 + i y1 and y2 at k (yk[0], yk[1]) and at -k
+//        (ym[0], ym[1]); y real gives y_c(-k) = conj(y_c(k)).
+template <typename T, typename T2>
+__device__ __forceinline__ void potential_pair(const T2 (&a)[3], const T2 (&bb)[3], T xi0, T xi1,
+                                               T xi2, T inv_v, T2 (&yk)[2], T2 (&ym)[2]) {
+  const T k2 = xi0 * xi0 + xi1 * xi1 + xi2 * xi2;
+  if (!(k2 > T(0))) {
+    yk[0] = yk[1] = ym[0] = ym[1] = T2{T(0), T(0)};
+    return;
+  }
+  // doubled Voigt components, as in project_pair
+  T sr[6], si[6];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    sr[2 * c] = a[c].x + bb[c].x;
+    si[2 * c] = a[c].y - bb[c].y;
+    sr[2 * c + 1] = a[c].y + bb[c].y;
+    si[2 * c + 1] = bb[c].x - a[c].x;
+  }
+  const T rn = rsqrt_t(k2);
+  const T n0 = xi0 * rn, n1 = xi1 * rn, n2 = xi2 * rn;
+  // with the doubled S: 2 v - s n = V - (n . V / 2) n, V = (2 S) n; y_hat = (w_i - i w_r) / |xi|
+  T wr[3], wi[3];
+#define EQ_W(S, W)                                                              \
+  {                                                                            \
+    const T v0 = S[0] * n0 + S[5] * n1 + S[4] * n2;                            \
+    const T v1 = S[5] * n0 + S[1] * n1 + S[3] * n2;                            \
+    const T v2 = S[4] * n0 + S[3] * n1 + S[2] * n2;                            \
+    const T hs = T(0.5) * (n0 * v0 + n1 * v1 + n2 * v2);                       \
+    W[0] = v0 - hs * n0;                                                       \
+    W[1] = v1 - hs * n1;                                                       \
+    W[2] = v2 - hs * n2;                                                       \
+  }
+  EQ_W(sr, wr)
+  EQ_W(si, wi)
+#undef EQ_W
+  const T f = rn * inv_v;                           // 1 / (|xi| V)
+  T2 y[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) y[c] = T2{wi[c] * f, -wr[c] * f};
+  yk[0] = T2{y[0].x - y[1].y, y[0].y + y[1].x};     // y0 + i y1 at k
+  ym[0] = T2{y[0].x + y[1].y, y[1].x - y[0].y};     // conj(y0) + i conj(y1) at -k
+  yk[1] = y[2];
+  ym[1] = T2{y[2].x, -y[2].y};
+}
+
 // Fused x pass: forward transform of row pairs (k_y, k_z) and (-k_y, -k_z), projector on every
 // mode pair (k, -k), inverse transform, store.  grid = (G, batch); block = Cfg::X_THREADS.
 template <typename T, int N>
@@ -423,6 +476,109 @@ k_xproj(const XArgs a) {
   if (threadIdx.x == 0) {
     double* q = a.partials + ((long long)field * gridDim.x + blockIdx.x) * 4;
     q[0] = v[0]; q[1] = v[1]; q[2] = v[2]; q[3] = v[3];
+  }
+}
+
+
+// Potential x pass: reads the stress spectrum after the z and y forward passes (not modifying
+// it), takes the forward x transform of each row pair, forms the packed y spectra per mode pair
+// (potential_pair) and writes their inverse x transforms into the 4-plane y buffer (y0 + i y1 in
+// planes 0/1, y2 + i 0 in planes 2/3).  Same row-pair layout as k_xproj; only the columns of
+// components 0 and 1 of each side carry y back out.
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<T, N>::X_THREADS)
+k_xpot(const XArgs a) {
+  using C = Cfg<T, N>;
+  using T2 = typename C::T2;
+  constexpr int E = C::E, TPC = C::TPC, P = C::P, PITCH = C::PITCH;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* tw = reinterpret_cast<T2*>(smem_raw);
+  T2* buf = tw + N;
+  T* xix = reinterpret_cast<T*>(buf + C::XCOLS * PITCH);
+
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    tw[i] = reinterpret_cast<const T2*>(a.tw)[i];
+    xix[i] = reinterpret_cast<const T*>(a.xi_x)[i];
+  }
+  __syncthreads();
+  const T* xiy = reinterpret_cast<const T*>(a.xi_y);
+  const T* xiz = reinterpret_cast<const T*>(a.xi_z);
+
+  const int col = threadIdx.x / TPC, t = threadIdx.x % TPC;
+  const int slot = col / 6, side = (col % 6) / 3, comp = col % 3;
+  const int field = blockIdx.y;
+  const T* fdata = reinterpret_cast<const T*>(a.data) + field * a.field_stride;
+  const T* pre = fdata + (2LL * comp) * a.V;
+  const T* pim = pre + a.V;
+  T* yre = reinterpret_cast<T*>(a.ydata) + field * a.yfield_stride + (2LL * (comp & 1)) * a.V;
+  T* yim = yre + a.V;
+  const IdxRow idx{col * PITCH};
+  const T inv_v = T(a.inv_v);
+
+  for (int g = blockIdx.x; g < a.ngroups; g += gridDim.x) {
+    const int p = g * P + slot;
+    const bool valid = p < a.npairs;
+    int rowA = 0, rowB = 0;
+    if (valid) {
+      rowA = a.pairs[p];
+      const int kz = rowA / a.ny, ky = rowA - kz * a.ny;
+      const int mz = kz == 0 ? 0 : a.nz - kz, my = ky == 0 ? 0 : a.ny - ky;
+      rowB = mz * a.ny + my;
+    }
+    const bool selfrow = rowA == rowB;
+    const bool active = valid && !(side == 1 && selfrow);
+    const long long roff = (long long)(side == 0 ? rowA : rowB) * N;
+    T2 x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const long long off = roff + t + TPC * e;
+      x[e] = active ? T2{pre[off], pim[off]} : T2{T(0), T(0)};
+    }
+    fft_column<N, E, false>(x, t, buf, idx, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) buf[idx(t + TPC * e)] = x[e];
+    __syncthreads();
+
+    for (int item = threadIdx.x; item < P * N; item += blockDim.x) {
+      const int s2 = item / N, kx = item - s2 * N;
+      const int p2 = g * P + s2;
+      if (p2 >= a.npairs) continue;
+      const int rA = a.pairs[p2];
+      const int kz = rA / a.ny, ky = rA - kz * a.ny;
+      const int mz = kz == 0 ? 0 : a.nz - kz, my = ky == 0 ? 0 : a.ny - ky;
+      const bool self2 = (mz * a.ny + my) == rA;
+      const int kxm = kx == 0 ? 0 : N - kx;
+      if (self2 && kx > kxm) continue;
+      const int colA = s2 * 6, colB = self2 ? s2 * 6 : s2 * 6 + 3;
+      T2 av[3], bv[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        av[c] = buf[(colA + c) * PITCH + kx + (kx >> 3)];
+        bv[c] = buf[(colB + c) * PITCH + kxm + (kxm >> 3)];
+      }
+      T2 yk[2], ym[2];
+      potential_pair<T>(av, bv, xix[kx], xiy[ky], xiz[kz], inv_v, yk, ym);
+      // this mode pair owns (row A, kx) and (row B, kxm) of every column: store in place
+      const bool selfmode = self2 && kx == kxm;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        buf[(colA + c) * PITCH + kx + (kx >> 3)] = yk[c];
+        if (!selfmode) buf[(colB + c) * PITCH + kxm + (kxm >> 3)] = ym[c];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = buf[idx(t + TPC * e)];
+    __syncthreads();
+    fft_column<N, E, true>(x, t, buf, idx, tw);
+    if (active && comp < 2) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const long long off = roff + t + TPC * e;
+        yre[off] = x[e].x;
+        yim[off] = x[e].y;
+      }
+    }
   }
 }
 

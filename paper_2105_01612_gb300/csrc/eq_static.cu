@@ -175,14 +175,14 @@ extern "C" eq_status eq_project_static(int nx, int ny, int nz, const eq_plan_opt
   a.V = V;
   a.in = d_in; a.out = d_out; a.ref = nullptr; a.tw = twz;
   a.nstride = (long long)nx * ny; a.inner = a.nstride; a.outer_stride = 0; a.ncols = a.inner;
-  a.ntiles = tz; a.partials = part1; a.mode = 1;
+  a.ntiles = tz; a.partials = part1; a.mode = 1; a.ncomp = 3;
   if ((e = eqk::launch_strided_f32(nz, false, a, dim3(g1, 3), s)) != cudaSuccess)
     return sfail(EQ_ERR_CUDA, std::string("eq_project_static: z forward: ") + cudaGetErrorString(e));
   eqk::finalize_mean(part1, g1, 1, double(V), mean, instats, s);
   eqk::StridedArgs ay{};
   ay.field_stride = 6 * V; ay.V = V; ay.in = d_out; ay.out = d_out; ay.tw = twy;
   ay.nstride = nx; ay.inner = nx; ay.outer_stride = (long long)nx * ny; ay.ncols = (long long)nz * nx;
-  ay.ntiles = ty; ay.mode = 0;
+  ay.ntiles = ty; ay.mode = 0; ay.ncomp = 3;
   if ((e = eqk::launch_strided_f32(ny, false, ay, dim3(gy, 3), s)) != cudaSuccess)
     return sfail(EQ_ERR_CUDA, std::string("eq_project_static: y forward: ") + cudaGetErrorString(e));
   eqk::XArgs x{};

@@ -101,6 +101,7 @@ struct TmaArgs {
   int axis;                // 2 = z, 1 = y
   int mode;                // 0 middle, 1 first (statistics), 2 last
   int tma_store;           // 1: store tiles by TMA through the exchange buffer
+  int ncomp;               // complex fields (pairs of planes) per field: 3 (stress), 2 (potential)
   long long ntiles;        // tiles per (field, component)
 };
 
@@ -132,8 +133,8 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
 
   const int tid = threadIdx.x;
   const int b = tid % B, t = tid / B;
-  const int field = blockIdx.y / 3, comp = blockIdx.y % 3;
-  const int plane_re = field * 6 + 2 * comp;
+  const int field = blockIdx.y / a.ncomp, comp = blockIdx.y % a.ncomp;
+  const int plane_re = field * 2 * a.ncomp + 2 * comp;
   const int tiles_x = a.nx / B;
   const int ntiles = (int)a.ntiles;
 
@@ -358,8 +359,8 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
   const int tid = threadIdx.x;
   const int b = tid % B, t = tid / B;
   const int kap = t >> 1, h = t & 1;
-  const int field = blockIdx.y / 3, comp = blockIdx.y % 3;
-  const int plane_re = field * 6 + 2 * comp;
+  const int field = blockIdx.y / a.ncomp, comp = blockIdx.y % a.ncomp;
+  const int plane_re = field * 2 * a.ncomp + 2 * comp;
   const int tiles_x = a.nx / B;
   const int ntiles = (int)a.ntiles;
 
