@@ -211,6 +211,30 @@ eq_status eq_serve_poll(eq_server* server, unsigned long long ticket, int timeou
  * every resource is released.  The server and its tickets are invalid afterwards. */
 void eq_server_destroy(eq_server* server);
 
+/* ---- Grain averaging (Sec. 5.1) -----------------------------------------------------------
+ * The synthetic measurement of Sec. 5.1 / Table 1 averages a stress field over each grain of a
+ * polycrystal, as a grain-resolved diffraction reconstruction reports it.  A grain map is fixed
+ * across the fields averaged with it, so it becomes an object once. */
+typedef struct eq_grains eq_grains;
+
+/* grain_map: host array of nx*ny*nz grain ids in [0, ngrains), x fastest (any id outside that
+ * range: EQ_ERR_INVALID, before any device work).  Sorts the voxels by grain on the host (a
+ * counting sort that keeps voxel order within a grain) and uploads the per-grain voxel lists and
+ * the map to the current device: about 12 bytes per voxel of device memory, owned by the object. */
+eq_status eq_grains_create(const int* grain_map, int nx, int ny, int nz, int ngrains,
+                           eq_grains** out);
+
+/* For `batch` fields d_in (device, dtype, layout [batch][6][nz][ny][nx]) write the per-grain means
+ * of the six Voigt components to d_means (device, FP64, [batch][ngrains][6]; a grain with no voxel
+ * gets 0) and, when d_avg is not NULL, the grain-averaged fields (every voxel carries its grain's
+ * mean; same layout and dtype as d_in; d_avg may equal d_in).  Sums run in FP64 in a fixed order:
+ * results do not depend on timing.  Only enqueues work on cuda_stream. */
+eq_status eq_grain_average(eq_grains* grains, eq_dtype dtype, int batch, const void* d_in,
+                           double* d_means, void* d_avg, void* cuda_stream);
+
+/* Release the object's device memory (NULL: no-op).  Work using it must have completed. */
+void eq_grains_destroy(eq_grains* grains);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char* eq_last_error(void);
 

@@ -316,6 +316,60 @@ def _numel(shape):
     return n
 
 
+class Grains:
+    """A fixed grain map for grain averaging (Sec. 5.1): ``gmap`` is a CPU int tensor or array of
+    shape (nz, ny, nx) with ids in [0, ngrains)."""
+
+    def __init__(self, gmap, ngrains: int, device=None):
+        g = torch.as_tensor(gmap).to(torch.int32).contiguous()
+        if g.dim() != 3 or g.is_cuda:
+            raise ValueError("gmap must be a host (nz, ny, nx) integer map")
+        self.shape = tuple(g.shape)
+        self.ngrains = int(ngrains)
+        self.device = _cuda_device(device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = _lib.load().eq_grains_create(
+                ctypes.cast(g.data_ptr(), ctypes.POINTER(ctypes.c_int)), self.shape[2],
+                self.shape[1], self.shape[0], self.ngrains, ctypes.byref(h))
+        _lib.check(st, "eq_grains_create")
+        self.handle = h.value
+
+    def average(self, x: torch.Tensor, means: torch.Tensor | None = None,
+                out: torch.Tensor | None = None, want_field: bool = True, stream=None):
+        """x: (B, 6, nz, ny, nx) CUDA float32/float64.  Returns (means, field): means (B, ngrains,
+        6) float64 and, with want_field, the grain-averaged field (may be x itself via out=x)."""
+        if not x.is_cuda or x.device != self.device or x.dim() != 5 or x.shape[1] != 6 \
+                or tuple(x.shape[2:]) != self.shape or not x.is_contiguous() \
+                or x.dtype not in _DT:
+            raise ValueError(f"x must be a contiguous (B, 6) + {self.shape} CUDA tensor")
+        b = x.shape[0]
+        if means is None:
+            means = torch.empty((b, self.ngrains, 6), dtype=torch.float64, device=self.device)
+        if want_field and out is None:
+            out = torch.empty_like(x)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            st = _lib.load().eq_grain_average(
+                ctypes.c_void_p(self.handle), _DT[x.dtype], b, ctypes.c_void_p(x.data_ptr()),
+                ctypes.c_void_p(means.data_ptr()),
+                ctypes.c_void_p(out.data_ptr() if want_field else None),
+                ctypes.c_void_p(s.cuda_stream))
+        _lib.check(st, "eq_grain_average")
+        return means, (out if want_field else None)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.load().eq_grains_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def project(x: torch.Tensor, op="ddo", h=(1.0, 1.0, 1.0), nyq="keep", out=None,
             target="equilibrium"):
     """Project a (6, nz, ny, nx) or (B, 6, nz, ny, nx) CUDA tensor; returns (out, norms).

@@ -12,7 +12,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeq.so")
 
-SOURCES = ["eq_f32.cu", "eq_f64.cu", "eq_gen_f32.cu", "eq_gen_f64.cu", "eq_gen_host.cu", "eq_api.cu", "eq_serve.cu", "eq_static.cu"]
+SOURCES = ["eq_f32.cu", "eq_f64.cu", "eq_gen_f32.cu", "eq_gen_f64.cu", "eq_gen_host.cu", "eq_api.cu", "eq_serve.cu", "eq_static.cu",
+           "eq_grains.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -65,6 +65,10 @@ SIGNATURES = [
     ("eq_serve_poll", c_int, [c_void_p, ctypes.c_ulonglong, c_int, ctypes.POINTER(EqNorms),
                               ctypes.POINTER(c_double)]),
     ("eq_server_destroy", None, [c_void_p]),
+    ("eq_grains_create", c_int, [ctypes.POINTER(c_int), c_int, c_int, c_int, c_int,
+                                 ctypes.POINTER(c_void_p)]),
+    ("eq_grain_average", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("eq_grains_destroy", None, [c_void_p]),
     ("eq_last_error", ctypes.c_char_p, []),
 ]
 

@@ -107,3 +107,15 @@ def test_product_path_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, flags=re.M), f
                 assert "oracle/" not in txt, f
+
+
+def test_grain_map_validation_without_a_gpu(lib):
+    from paper_2105_01612_gb300._lib import EQ_ERR_INVALID
+    h = ctypes.c_void_p()
+    ids = (ctypes.c_int * 8)(0, 1, 2, 3, 0, 1, 2, 9)
+    assert lib.eq_grains_create(ids, 2, 2, 2, 4, ctypes.byref(h)) == EQ_ERR_INVALID
+    assert b"outside" in lib.eq_last_error()
+    assert lib.eq_grains_create(None, 2, 2, 2, 4, ctypes.byref(h)) == EQ_ERR_INVALID
+    assert lib.eq_grains_create(ids, 2, 2, 2, 0, ctypes.byref(h)) == EQ_ERR_INVALID
+    assert lib.eq_grain_average(None, 0, 1, None, None, None, None) == EQ_ERR_INVALID
+    lib.eq_grains_destroy(None)
