@@ -25,6 +25,7 @@ from .fields import beltrami_field, symgrad_field, smooth_potential, inc_central
 from .brute import project_bruteforce
 from .hodge import project_compat, hodge_potential
 from .grains import grain_means, grain_average
+from .padding import project_padded
 
 __all__ = [
     "dft_axis_direct", "dft3_direct", "dft3_naive", "fft3", "ifft3",
@@ -32,5 +33,5 @@ __all__ = [
     "stencil25_apply", "project", "project_literal", "project_spectrum", "divergence",
     "divergence_central_diff", "norms", "inner", "frob2", "beltrami_field", "symgrad_field",
     "smooth_potential", "inc_central_diff", "project_bruteforce", "project_compat",
-    "hodge_potential", "grain_means", "grain_average",
+    "hodge_potential", "grain_means", "grain_average", "project_padded",
 ]
