@@ -128,6 +128,18 @@ eq_status eq_project(eq_plan* plan, const void* d_in, void* d_out, void* cuda_st
 eq_status eq_project_hodge(eq_plan* plan, const void* d_in, void* d_out, void* d_y,
                            void* cuda_stream);
 
+/* A non-periodic specimen (Sec. 5.2): d_in holds batch fields of sx * sy * sz voxels (layout
+ * [batch][6][sz][sy][sx], the plan's dtype); each is placed at the origin corner of the plan's
+ * periodic grid (nx, ny, nz) >= (sx, sy, sz) with zero stress in the rest of the grid (the
+ * buffer region of free surfaces; on a periodic grid the corner placement equals a buffer on
+ * both sides, and an axis with no padding stays periodically connected), the whole grid is
+ * projected, and the specimen region is written to d_out (same layout as d_in; may equal d_in).
+ * The norms are those of the padded grid except resid_linf, taken over the specimen.  Power-of-
+ * two plans only.  The first call allocates the padded workspace (plan-owned, one grid per
+ * field); the padding and the cut run as their own kernels around the plan's passes. */
+eq_status eq_project_padded(eq_plan* plan, int sx, int sy, int sz, const void* d_in, void* d_out,
+                            void* cuda_stream);
+
 /* Same as eq_project with host buffers: copies host_in to a plan-owned device buffer
  * (allocated on first use, 2 x field bytes), projects, copies back to host_out, and waits for
  * completion.  Host buffers should be pinned for full copy bandwidth. */

@@ -162,6 +162,29 @@ class Plan:
             eq_project_hodge(self.handle, x.data_ptr(), out.data_ptr(), y.data_ptr(), s.cuda_stream)
         return out, y
 
+    def project_padded(self, x: torch.Tensor, out: torch.Tensor | None = None,
+                       stream=None) -> torch.Tensor:
+        """x: specimen fields (batch, 6, sz, sy, sx) on the plan's device, no larger than the
+        plan's grid; projected inside a zero-stress buffer filling the grid, cut back out."""
+        b, _, nz, ny, nx = self.shape
+        if not x.is_cuda or x.device != self.device or x.dtype != self.dtype or x.dim() != 5 \
+                or x.shape[0] != b or x.shape[1] != 6 or not x.is_contiguous():
+            raise ValueError(f"x must be a contiguous ({b}, 6, sz, sy, sx) {self.dtype} tensor")
+        sz, sy, sx = x.shape[2:]
+        if out is None:
+            out = torch.empty_like(x)
+        if out.shape != x.shape or out.dtype != x.dtype or not out.is_contiguous() \
+                or out.device != x.device:
+            raise ValueError("out must match x")
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.load().eq_project_padded(ctypes.c_void_p(self.handle), sx, sy, sz,
+                                                     ctypes.c_void_p(x.data_ptr()),
+                                                     ctypes.c_void_p(out.data_ptr()),
+                                                     ctypes.c_void_p(s.cuda_stream)),
+                       "eq_project_padded")
+        return out
+
     def project_host(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
         """Host tensors in and out (pinned for full bandwidth); blocks until done."""
         for t, n in ((x, "x"), (out, "out")):

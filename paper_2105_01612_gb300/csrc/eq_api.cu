@@ -97,6 +97,93 @@ __global__ void k_finalize_norms(const double* __restrict__ partx, int gridx,
   }
 }
 
+// ---- non-periodic specimens in a zero-stress buffer (Sec. 5.2) ---------------------------------
+
+constexpr int PAD_GRID = 1216;  // blocks per field of the crop pass (8 x 152 SMs)
+
+// Copy the specimen planes (sx, sy, sz) into the corner of the grid planes (nx, ny, nz) and zero
+// the rest.  One warp per grid row (plane, z, y), lanes along x, four loads in flight per lane.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_pad(const T* __restrict__ in, T* __restrict__ out, int sx, int sy, int sz, int nx, int ny, int nz,
+      long long rows) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long r = w0; r < rows; r += nw) {
+    const long long pl = r / ((long long)ny * nz);
+    const int zy = (int)(r - pl * ny * nz), z = zy / ny, y = zy - z * ny;
+    T* o = out + r * nx;
+    const int lim = (z < sz && y < sy) ? sx : 0;     // specimen columns of this row
+    const T* src = in + ((pl * sz + z) * sy + y) * sx;
+    for (int x0 = lane; x0 < nx; x0 += 128) {
+      T v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int x = x0 + 32 * k;
+        v[k] = x < lim ? src[x] : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (x0 + 32 * k < nx) o[x0 + 32 * k] = v[k];
+    }
+  }
+}
+
+// Cut the specimen region of the projected grid into out, and the largest |in - out| over it per
+// block (grid (PAD_GRID, batch): warps of a field's blocks walk its 6 sz sy specimen rows, four
+// loads of each kind in flight per lane).  `in` may equal `out`: each element is read before it
+// is written, by the same thread.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_crop_linf(const T* __restrict__ work, const T* in, T* out, int sx, int sy, int sz, int nx, int ny,
+            int nz, double* __restrict__ partials) {
+  __shared__ double red[32];
+  const int f = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const long long rows = 6LL * sz * sy;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  T m = T(0);                 // in the working precision, as the last pass of eq_project
+  for (long long r = w0; r < rows; r += nw) {
+    const int pl = (int)(r / ((long long)sz * sy));
+    const int zy = (int)(r - (long long)pl * sz * sy), z = zy / sy, y = zy - z * sy;
+    const long long splane = (long long)f * 6 + pl;
+    const T* wr = work + ((splane * nz + z) * ny + y) * nx;
+    const long long so = ((splane * sz + z) * sy + y) * sx;
+    for (int x0 = lane; x0 < sx; x0 += 128) {
+      T v[4], ref[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int x = x0 + 32 * k;
+        v[k] = x < sx ? wr[x] : T(0);
+        ref[k] = x < sx ? in[so + x] : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int x = x0 + 32 * k;
+        if (x < sx) {
+          m = fmax(m, fabs(ref[k] - v[k]));
+          out[so + x] = v[k];
+        }
+      }
+    }
+  }
+  const double mb = eqk::block_max(double(m), red);
+  if (threadIdx.x == 0) partials[(long long)f * gridDim.x + blockIdx.x] = mb;
+}
+
+// L-inf of each field into its norms (fixed order), clearing the no-L-inf flag of the in-place run
+__global__ void k_pad_linf(const double* __restrict__ partials, int grid, int batch,
+                           eq_norms_t* __restrict__ norms) {
+  for (int f = threadIdx.x; f < batch; f += blockDim.x) {
+    double m = 0.0;
+    for (int g = 0; g < grid; ++g) m = fmax(m, partials[(long long)f * grid + g]);
+    norms[f].resid_linf = m;
+    norms[f].flags &= ~EQ_FLAG_NO_LINF;
+  }
+}
+
 namespace eqk {
 void finalize_mean(const double* part, int grid, int batch, double vol, double* mean,
                    double* instats, cudaStream_t s) {
@@ -149,6 +236,9 @@ struct eq_plan {
   // staging for eq_project_host
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  // workspace of eq_project_padded: the padded fields, then one L-inf partial per block and field
+  void* pad_ws = nullptr;
+  double* pad_part = nullptr;
   // optional per-pass timing: one set of EQ_NUM_PASSES + 1 events per timed call
   std::vector<cudaEvent_t> tev;
   int tcap = 0, tused = 0;
@@ -555,6 +645,7 @@ void release(eq_plan* p) {
   if (p->done) cudaEventDestroy(p->done);
   if (p->dmem) cudaFree(p->dmem);
   if (p->stage) cudaFree(p->stage);
+  if (p->pad_ws) cudaFree(p->pad_ws);
   if (p->gen) eqg::gen_destroy(p->gen);
   delete p;
 }
@@ -830,6 +921,64 @@ eq_status eq_project_hodge(eq_plan* p, const void* d_in, void* d_out, void* d_y,
   cudaGetDevice(&dev);
   if (dev != p->device) return fail(EQ_ERR_INVALID, "eq_project_hodge: current device differs from the plan's");
   return run(p, d_in, d_out, static_cast<cudaStream_t>(stream), d_y);
+}
+
+eq_status eq_project_padded(eq_plan* p, int sx, int sy, int sz, const void* d_in, void* d_out,
+                            void* stream) {
+  if (!p || !d_in || !d_out) return fail(EQ_ERR_INVALID, "eq_project_padded: NULL argument");
+  if (p->gen)
+    return fail(EQ_ERR_INVALID, "eq_project_padded: needs a plan with power-of-two axis lengths");
+  if (sx < 1 || sy < 1 || sz < 1 || sx > p->nx || sy > p->ny || sz > p->nz)
+    return fail(EQ_ERR_INVALID, "eq_project_padded: the specimen must fit the plan's grid");
+  const size_t sbytes = (size_t)p->batch * 6 * sx * sy * sz * p->esize;
+  const uintptr_t i0 = (uintptr_t)d_in, o0 = (uintptr_t)d_out;
+  if (i0 != o0 && i0 < o0 + sbytes && o0 < i0 + sbytes)
+    return fail(EQ_ERR_INVALID, "eq_project_padded: d_in and d_out overlap without being equal");
+  if ((i0 % p->esize) || (o0 % p->esize))
+    return fail(EQ_ERR_INVALID, "eq_project_padded: buffers not aligned to the element size");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device) return fail(EQ_ERR_INVALID, "eq_project_padded: current device differs from the plan's");
+  cudaError_t e;
+  const size_t wbytes = (size_t)p->total_elems * p->esize;
+  if (!p->pad_ws) {
+    const size_t pbytes = sizeof(double) * (size_t)p->batch * PAD_GRID;
+    if ((e = cudaMalloc(&p->pad_ws, wbytes + pbytes)) != cudaSuccess) {
+      p->pad_ws = nullptr;
+      cudaGetLastError();
+      return fail(EQ_ERR_OOM, std::string("eq_project_padded: cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    p->pad_part = reinterpret_cast<double*>(static_cast<unsigned char*>(p->pad_ws) + wbytes);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long rows = 6LL * p->batch * p->nz * p->ny;
+  const int pgrid = (int)std::min<long long>((rows + 7) / 8, (long long)p->sms * 8);
+  if (p->dtype == EQ_F32)
+    k_pad<float><<<pgrid, 256, 0, s>>>(static_cast<const float*>(d_in), static_cast<float*>(p->pad_ws),
+                                        sx, sy, sz, p->nx, p->ny, p->nz, rows);
+  else
+    k_pad<double><<<pgrid, 256, 0, s>>>(static_cast<const double*>(d_in), static_cast<double*>(p->pad_ws),
+                                         sx, sy, sz, p->nx, p->ny, p->nz, rows);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "eq_project_padded: pad");
+  eq_status st = run(p, p->pad_ws, p->pad_ws, s);
+  if (st != EQ_OK) return st;
+  dim3 cgrid(PAD_GRID, p->batch);
+  if (p->dtype == EQ_F32)
+    k_crop_linf<float><<<cgrid, 256, 0, s>>>(static_cast<const float*>(p->pad_ws),
+                                              static_cast<const float*>(d_in), static_cast<float*>(d_out),
+                                              sx, sy, sz, p->nx, p->ny, p->nz, p->pad_part);
+  else
+    k_crop_linf<double><<<cgrid, 256, 0, s>>>(static_cast<const double*>(p->pad_ws),
+                                               static_cast<const double*>(d_in), static_cast<double*>(d_out),
+                                               sx, sy, sz, p->nx, p->ny, p->nz, p->pad_part);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "eq_project_padded: crop");
+  if (p->opts.want_linf) {
+    k_pad_linf<<<1, 128, 0, s>>>(p->pad_part, PAD_GRID, p->batch, p->norms);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "eq_project_padded: L-inf");
+  }
+  // eq_norms waits for the last kernel of this call
+  if ((e = cudaEventRecord(p->done, s)) != cudaSuccess) return fail_cuda(e, "event record");
+  return EQ_OK;
 }
 
 eq_status eq_project_host(eq_plan* p, const void* h_in, void* h_out, void* stream) {
