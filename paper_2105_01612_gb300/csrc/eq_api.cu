@@ -501,8 +501,27 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, voi
     if (e != cudaSuccess) return fail_cuda(e, "y forward pass");
   }
   mark(3);
-  // potential x pass (reads the spectrum before the projector rewrites it)
-  if (d_y) {
+  // potential x pass (reads the spectrum before the projector rewrites it): the warp-per-row
+  // kernel when the x pass runs it and the buffers allow bulk copies, else the plain-load kernel
+  const bool pot_warp = d_y && p->tma_x && (p->vx == 2 || p->vx == 3) &&
+                        !(reinterpret_cast<uintptr_t>(d_out) & 15) &&
+                        !(reinterpret_cast<uintptr_t>(d_y) & 15);
+  if (pot_warp) {
+    eqk::XTmaArgs x{};
+    x.data = d_out; x.tws = p->twst;
+    x.xi_x = p->xi[0]; x.xi_y = p->xi[1]; x.xi_z = p->xi[2];
+    x.pairs = p->pairs; x.err = p->err;
+    x.field_stride = fstride; x.V = V;
+    x.nx = p->nx; x.ny = p->ny; x.nz = p->nz;
+    x.npairs = p->npairs;
+    x.ngroups = (p->npairs + p->tx.cols - 1) / p->tx.cols;
+    x.inv_v = 1.0 / double(V);
+    x.ydata = d_y; x.yfield_stride = 4 * V;
+    dim3 grid(p->gtx, p->batch);
+    e = f32 ? eqk::launch_xpot_warp_f32(p->nx, p->vx, x, grid, s)
+            : eqk::launch_xpot_warp_f64(p->nx, p->vx, x, grid, s);
+    if (e != cudaSuccess) return fail_cuda(e, "potential x pass");
+  } else if (d_y) {
     eqk::XArgs x{};
     x.data = d_out; x.tw = p->tw[0];
     x.xi_x = p->xi[0]; x.xi_y = p->xi[1]; x.xi_z = p->xi[2];

@@ -165,23 +165,29 @@ template <typename T, int N, int MINB> struct XwInst {
       out->cols = 1;
       out->box = 0;
       out->smem = C::SMEM;
-      const void* f = reinterpret_cast<const void*>(&k_xproj_warp<T, N, MINB>);
-      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
+      const void* f = reinterpret_cast<const void*>(&k_xproj_warp<T, N, MINB, false>);
+      const void* fp = reinterpret_cast<const void*>(&k_xproj_warp<T, N, MINB, true>);
+      cudaError_t e = cudaSuccess;
+      for (const void* g : {f, fp}) {
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(g, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared);
+      }
       int bl = 0;
       if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, f, C::THREADS, C::SMEM);
       out->blocks_per_sm = bl;
       return e;
     }
   }
-  static cudaError_t launch(const XTmaArgs& a, dim3 grid, cudaStream_t s) {
+  static cudaError_t launch(const XTmaArgs& a, dim3 grid, cudaStream_t s, bool pot = false) {
     using C = XwCfg<T, N, MINB>;
     if constexpr (!C::OK) {
       return cudaErrorInvalidValue;
     } else {
-      k_xproj_warp<T, N, MINB><<<grid, C::THREADS, C::SMEM, s>>>(a);
+      if (pot) k_xproj_warp<T, N, MINB, true><<<grid, C::THREADS, C::SMEM, s>>>(a);
+      else k_xproj_warp<T, N, MINB, false><<<grid, C::THREADS, C::SMEM, s>>>(a);
       return cudaGetLastError();
     }
   }
@@ -270,6 +276,19 @@ template <typename T> cudaError_t xtma_info_t(int n, int v, TmaInfo* out) {
     return v == 3   ? XwInst<T, N, XW_MINB<T>(4)>::info(out)                  \
            : v == 2 ? XwInst<T, N, XW_MINB<T>(3)>::info(out)                  \
                     : (v ? XTmaInst<T, N, 1>::info(out) : XTmaInst<T, N, 0>::info(out));
+    EQ_FOR_LENGTHS(EQ_CASE)
+#undef EQ_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+// potential x pass in the warp-per-row kernel (variants 2 and 3 only)
+template <typename T> cudaError_t xpot_warp_t(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s) {
+  if (v != 2 && v != 3) return cudaErrorInvalidValue;
+  switch (n) {
+#define EQ_CASE(N)                                                                     \
+  case N:                                                                                \
+    return v == 3 ? XwInst<T, N, XW_MINB<T>(4)>::launch(a, grid, s, true)               \
+                  : XwInst<T, N, XW_MINB<T>(3)>::launch(a, grid, s, true);
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;

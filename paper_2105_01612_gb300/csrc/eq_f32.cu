@@ -9,6 +9,9 @@ cudaError_t launch_strided_f32(int n, bool inv, const StridedArgs& a, dim3 grid,
 cudaError_t launch_xproj_f32(int n, const XArgs& a, dim3 grid, cudaStream_t s) {
   return xproj_t<float>(n, a, grid, s);
 }
+cudaError_t launch_xpot_warp_f32(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s) {
+  return xpot_warp_t<float>(n, v, a, grid, s);
+}
 cudaError_t launch_xpot_f32(int n, const XArgs& a, dim3 grid, cudaStream_t s) {
   return xpot_t<float>(n, a, grid, s);
 }

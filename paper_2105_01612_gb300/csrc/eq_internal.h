@@ -32,6 +32,9 @@ cudaError_t launch_xproj_f64(int n, const XArgs& a, dim3 grid, cudaStream_t s);
 // potential x pass (reads the stress spectrum, writes the x-inverted y rows; XArgs::ydata)
 cudaError_t launch_xpot_f32(int n, const XArgs& a, dim3 grid, cudaStream_t s);
 cudaError_t launch_xpot_f64(int n, const XArgs& a, dim3 grid, cudaStream_t s);
+// the same in the warp-per-row kernel (x variants 2 and 3; XTmaArgs::ydata)
+cudaError_t launch_xpot_warp_f32(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s);
+cudaError_t launch_xpot_warp_f64(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s);
 
 // TMA-fed strided passes: info returns cudaErrorInvalidValue when no instance exists for n.
 // v selects the shape variant (0: wide tiles, one block per SM; 1: narrow tiles, two blocks).

@@ -615,6 +615,8 @@ struct XTmaArgs {
   int nyq_zero;
   int compat;              // 1: return the compatible part c0 + (S - S_equil)
   double inv_v;
+  void* ydata;             // potential mode: field 0, plane 0 of the 4-plane y buffer
+  long long yfield_stride; // elements between fields of the y buffer (4 V)
 };
 
 template <typename T, int N, int V>
@@ -858,7 +860,10 @@ template <typename T, int N, int MINB = 1> struct XwCfg {
   static constexpr bool OK = (N == 256 || N == 512) && SMEM <= 227 * 1024;
 };
 
-template <typename T, int N, int MINB>
+// POT: the potential x pass of eq_project_hodge instead (reads the spectrum rows, forms the packed
+// y spectra per mode pair with potential_pair in the rows of components 0 and 1, and those two
+// warps of each side store their inverse transforms into the y buffer; nothing else is written).
+template <typename T, int N, int MINB, bool POT>
 __global__ void __launch_bounds__(XwCfg<T, N, MINB>::THREADS, MINB)
 k_xproj_warp(const XTmaArgs a) {
   using C = XwCfg<T, N, MINB>;
@@ -991,10 +996,21 @@ k_xproj_warp(const XTmaArgs a) {
         }
       }
       const bool selfmode = self && kx == kxm;
-      project_pair<T>(av, bv, xix[kx], rxi[s][0], rxi[s][1], rA == 0 && kx == 0, mean, vol,
-                      a.nyq_zero != 0, a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
+      if constexpr (POT) {
+        T2 yk[2], ym[2];
+        potential_pair<T>(av, bv, xix[kx], rxi[s][0], rxi[s][1], inv_v, yk, ym);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < 2; ++c) {
+          av[c] = yk[c];
+          bv[c] = ym[c];
+        }
+      } else {
+        project_pair<T>(av, bv, xix[kx], rxi[s][0], rxi[s][1], rA == 0 && kx == 0, mean, vol,
+                        a.nyq_zero != 0, a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2, di2,
+                        do2, o2);
+      }
+#pragma unroll
+      for (int c = 0; c < (POT ? 2 : 3); ++c) {
         T* ra = rows + (2 * c) * N;
         T* rb = rows + (2 * (self ? c : 3 + c)) * N;
         if constexpr (F16) {
@@ -1011,6 +1027,7 @@ k_xproj_warp(const XTmaArgs a) {
       }
     }
     __syncthreads();
+    if (POT && comp == 2) continue;                    // no y row for this warp (warp-uniform)
     if constexpr (F16) {
       T2* wrow = reinterpret_cast<T2*>(wre);
 #pragma unroll
@@ -1039,8 +1056,9 @@ k_xproj_warp(const XTmaArgs a) {
     __syncwarp();
     if (lane == 0 && active) {
       const int row = side == 0 ? rA : rinfo[s][1];
-      bulk_store(fdata + (2LL * comp) * a.V + (long long)row * N, wre, N * sizeof(T));
-      bulk_store(fdata + (2LL * comp + 1) * a.V + (long long)row * N, wim, N * sizeof(T));
+      T* dst = POT ? reinterpret_cast<T*>(a.ydata) + field * a.yfield_stride : fdata;
+      bulk_store(dst + (2LL * comp) * a.V + (long long)row * N, wre, N * sizeof(T));
+      bulk_store(dst + (2LL * comp + 1) * a.V + (long long)row * N, wim, N * sizeof(T));
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
   }
@@ -1050,11 +1068,13 @@ k_xproj_warp(const XTmaArgs a) {
     __syncthreads();
     return;
   }
-  double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
-  block_sum<4>(v, red);
-  if (tid == 0) {
-    double* q = a.partials + ((long long)field * gridDim.x + blockIdx.x) * 4;
-    q[0] = v[0]; q[1] = v[1]; q[2] = v[2]; q[3] = v[3];
+  if constexpr (!POT) {
+    double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
+    block_sum<4>(v, red);
+    if (tid == 0) {
+      double* q = a.partials + ((long long)field * gridDim.x + blockIdx.x) * 4;
+      q[0] = v[0]; q[1] = v[1]; q[2] = v[2]; q[3] = v[3];
+    }
   }
 }
 

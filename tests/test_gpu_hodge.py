@@ -75,6 +75,16 @@ def test_fp32_against_the_oracle_and_real_space(shape):
     assert err <= 5e-6
 
 
+@pytest.mark.parametrize("shape,dtype", [((8, 16, 512), torch.float64), ((8, 16, 256), torch.float32),
+                                         ((8, 16, 256), torch.float64)])
+def test_warp_kernel_rows(shape, dtype):
+    # x rows of 256 and 512 points run the potential in the warp-per-row x kernel
+    s = field(shape, 40 + shape[2])
+    out, y, plain = run_hodge(s, dtype)
+    assert np.array_equal(out, plain)
+    assert vrel(y[0, :3], oracle.hodge_potential(s, "ddo")) <= TOL[dtype]
+
+
 def test_batch_spacing_and_compatibility_target_fp64():
     h = (1.0, 0.8, 1.25)
     s = np.stack([field((16, 32, 8), 21), field((16, 32, 8), 22)])
