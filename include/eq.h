@@ -239,8 +239,10 @@ eq_status eq_grains_create(const int* grain_map, int nx, int ny, int nz, int ngr
 /* For `batch` fields d_in (device, dtype, layout [batch][6][nz][ny][nx]) write the per-grain means
  * of the six Voigt components to d_means (device, FP64, [batch][ngrains][6]; a grain with no voxel
  * gets 0) and, when d_avg is not NULL, the grain-averaged fields (every voxel carries its grain's
- * mean; same layout and dtype as d_in; d_avg may equal d_in).  Sums run in FP64 in a fixed order:
- * results do not depend on timing.  Only enqueues work on cuda_stream. */
+ * mean; same layout and dtype as d_in; d_avg may equal d_in).  Sums run in a fixed order (FP64;
+ * FP32 data: compensated FP32 per thread, FP64 across threads): results do not depend on timing.
+ * Only enqueues work on cuda_stream; a call with d_avg and a larger batch (or dtype) than before
+ * first allocates the object's copy of the means in the fields' dtype. */
 eq_status eq_grain_average(eq_grains* grains, eq_dtype dtype, int batch, const void* d_in,
                            double* d_means, void* d_avg, void* cuda_stream);
 

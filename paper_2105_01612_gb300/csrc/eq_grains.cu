@@ -23,6 +23,8 @@ struct eq_grains {
   long long* d_off = nullptr;   // [ngrains + 1] start of each grain's voxel list
   int* d_vox = nullptr;         // [V] voxel indices grouped by grain, increasing within a grain
   int* d_map = nullptr;         // [V] grain id of each voxel
+  void* d_mt = nullptr;         // means in the fields' dtype for the fill, [cap][ngrains][6]
+  size_t mt_bytes = 0;
 };
 
 namespace {
@@ -37,47 +39,103 @@ void release(eq_grains* g) {
   if (g->d_off) cudaFree(g->d_off);
   if (g->d_vox) cudaFree(g->d_vox);
   if (g->d_map) cudaFree(g->d_map);
+  if (g->d_mt) cudaFree(g->d_mt);
   delete g;
 }
+
+// Per-thread running sum: FP64 for FP64 data; for FP32 data a compensated FP32 sum (error about
+// 2 eps of the summed magnitudes, whatever the count; FP64 arithmetic is scarce on GB300).
+template <typename T> struct GrainAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T v) { s += double(v); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct GrainAcc<float> {
+  eqk::Kahan<float> k;
+  __device__ __forceinline__ void add(float v) { k.add(v); }
+  __device__ __forceinline__ double value() const { return k.value(); }
+};
 
 // grid (ngrains, batch), 256 threads: means[f][g][c] = (sum over grain g of field f, plane c) / n_g
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_grain_means(const T* __restrict__ in, long long field_stride, long long V,
               const long long* __restrict__ off, const int* __restrict__ vox, int ngrains,
-              double* __restrict__ means) {
+              double* __restrict__ means, T* __restrict__ means_t) {
   __shared__ double red[32 * 6];
   const int g = blockIdx.x, f = blockIdx.y;
   const T* s = in + f * field_stride;
   const long long b = off[g], e = off[g + 1];
-  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
+  GrainAcc<T> acc[6];
+  // four list entries per step (their loads in flight together), in list order per thread
+  const long long bs = blockDim.x;
+  long long i = b + threadIdx.x;
+  for (; i + 3 * bs < e; i += 4 * bs) {
+    long long p[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p[k] = vox[i + k * bs];
+    T x[4][6];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) x[k][c] = s[c * V + p[k]];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[c].add(x[k][c]);
+  }
+  for (; i < e; i += bs) {
     const long long p = vox[i];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) v[c] += double(s[c * V + p]);
+    for (int c = 0; c < 6; ++c) acc[c].add(s[c * V + p]);
   }
+  double v[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) v[c] = acc[c].value();
   eqk::block_sum<6>(v, red);
   if (threadIdx.x == 0) {
     const double n = double(e - b);
     double* m = means + ((long long)f * ngrains + g) * 6;
+    T* mt = means_t ? means_t + ((long long)f * ngrains + g) * 6 : nullptr;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) m[c] = n > 0.0 ? v[c] / n : 0.0;
+    for (int c = 0; c < 6; ++c) {
+      m[c] = n > 0.0 ? v[c] / n : 0.0;
+      if (mt) mt[c] = T(m[c]);
+    }
   }
 }
 
-// out[f][c][p] = means[f][map[p]][c], grid-stride over (field, voxel)
+// out[f][c][p] = means[f][map[p]][c]; grid (blocks, batch).  Each warp takes chunks of 128
+// consecutive voxels, lane l the voxels l + 32 k (k < 4): every load and store instruction covers
+// 32 consecutive voxels, four in flight per lane.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_grain_fill(T* __restrict__ out, long long field_stride, long long V, int batch,
-             const int* __restrict__ map, int ngrains, const double* __restrict__ means) {
-  const long long total = (long long)batch * V;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long f = i / V, p = i - f * V;
-    const double* m = means + (f * ngrains + map[p]) * 6;
-    T* o = out + f * field_stride + p;
+k_grain_fill(T* __restrict__ out, long long field_stride, long long V, const int* __restrict__ map,
+             int ngrains, const T* __restrict__ means_t) {
+  const int f = blockIdx.y;
+  const T* mf = means_t + (long long)f * ngrains * 6;
+  T* of = out + f * field_stride;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = w0 * 128; base < V; base += nw * 128) {
+    int gs[4];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) o[c * V] = T(m[c]);
+    for (int k = 0; k < 4; ++k) {
+      const long long p = base + lane + 32 * k;
+      gs[k] = p < V ? map[p] : 0;
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      T v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = mf[gs[k] * 6 + c];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const long long p = base + lane + 32 * k;
+        if (p < V) of[c * V + p] = v[k];
+      }
+    }
   }
 }
 
@@ -144,24 +202,45 @@ extern "C" eq_status eq_grain_average(eq_grains* g, eq_dtype dtype, int batch, c
     return gfail(EQ_ERR_INVALID, "eq_grain_average: current device differs from the grain map's");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long fs = 6 * g->V;
+  cudaError_t e;
+  if (d_avg) {
+    // the fill reads the means in the fields' dtype (converted once per grain, not per voxel):
+    // an object-owned buffer, grown on a call with a larger batch or dtype
+    const size_t need = (size_t)batch * g->ngrains * 6 * (dtype == EQ_F32 ? 4 : 8);
+    if (need > g->mt_bytes) {
+      if (g->d_mt) cudaFree(g->d_mt);
+      g->d_mt = nullptr;
+      g->mt_bytes = 0;
+      if ((e = cudaMalloc(&g->d_mt, need)) != cudaSuccess) {
+        g->d_mt = nullptr;
+        cudaGetLastError();
+        return gfail(EQ_ERR_OOM, std::string("eq_grain_average: cudaMalloc: ") + cudaGetErrorString(e));
+      }
+      g->mt_bytes = need;
+    }
+  }
   dim3 grid((unsigned)g->ngrains, (unsigned)batch);
   if (dtype == EQ_F32)
     k_grain_means<float><<<grid, 256, 0, s>>>(static_cast<const float*>(d_in), fs, g->V, g->d_off,
-                                                g->d_vox, g->ngrains, d_means);
+                                                g->d_vox, g->ngrains, d_means,
+                                                d_avg ? static_cast<float*>(g->d_mt) : nullptr);
   else
     k_grain_means<double><<<grid, 256, 0, s>>>(static_cast<const double*>(d_in), fs, g->V, g->d_off,
-                                                 g->d_vox, g->ngrains, d_means);
-  cudaError_t e = cudaGetLastError();
+                                                 g->d_vox, g->ngrains, d_means,
+                                                 d_avg ? static_cast<double*>(g->d_mt) : nullptr);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return gfail(EQ_ERR_CUDA, std::string("eq_grain_average: means: ") + cudaGetErrorString(e));
   if (d_avg) {
-    const long long work = (long long)batch * g->V;
-    const int blocks = (int)std::min<long long>((long long)g->sms * 8, (work + 255) / 256);
+    const long long chunks = (g->V + 127) / 128;              // one warp each
+    dim3 fgrid((unsigned)std::max<long long>(1, std::min<long long>((long long)g->sms * 8 / batch + 1,
+                                                                    (chunks + 7) / 8)),
+               (unsigned)batch);
     if (dtype == EQ_F32)
-      k_grain_fill<float><<<blocks, 256, 0, s>>>(static_cast<float*>(d_avg), fs, g->V, batch,
-                                                  g->d_map, g->ngrains, d_means);
+      k_grain_fill<float><<<fgrid, 256, 0, s>>>(static_cast<float*>(d_avg), fs, g->V, g->d_map,
+                                                 g->ngrains, static_cast<const float*>(g->d_mt));
     else
-      k_grain_fill<double><<<blocks, 256, 0, s>>>(static_cast<double*>(d_avg), fs, g->V, batch,
-                                                   g->d_map, g->ngrains, d_means);
+      k_grain_fill<double><<<fgrid, 256, 0, s>>>(static_cast<double*>(d_avg), fs, g->V, g->d_map,
+                                                  g->ngrains, static_cast<const double*>(g->d_mt));
     if ((e = cudaGetLastError()) != cudaSuccess)
       return gfail(EQ_ERR_CUDA, std::string("eq_grain_average: fill: ") + cudaGetErrorString(e));
   }

@@ -38,10 +38,12 @@ def test_means_and_field_match_the_oracle_batch_of_two(dtype):
     for f in range(2):
         want = oracle.grain_means(xs[f], gmap, 41)
         got = means[f].cpu().numpy()
-        assert np.allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+        # FP64 data: FP64 sums; FP32 data: compensated FP32 per thread, FP64 across threads
+        mtol = 1e-12 if dtype == torch.float64 else 2e-6
+        assert np.abs(got - want).max() <= mtol * np.abs(want).max()
         assert np.all(got[7] == 0.0) and np.all(got[40] == 0.0)
         ref = oracle.grain_average(xs[f], gmap, 41)
-        tol = 1e-13 if dtype == torch.float64 else 1e-7
+        tol = 1e-13 if dtype == torch.float64 else 2e-6
         assert np.abs(avg[f].double().cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
     # fixed-order sums: a second call gives the same bits; in place gives the same field
     means2, _ = gr.average(x)
