@@ -145,6 +145,13 @@ eq_status eq_project_padded(eq_plan* plan, int sx, int sy, int sz, const void* d
  * completion.  Host buffers should be pinned for full copy bandwidth. */
 eq_status eq_project_host(eq_plan* plan, const void* host_in, void* host_out, void* cuda_stream);
 
+/* eq_project_host without the final wait: the copy in, the projection and the copy out are only
+ * enqueued on cuda_stream (done when the stream reaches that point; eq_norms waits for it).  The
+ * host buffers must stay valid and untouched until then, and calls on one plan share its device
+ * staging buffer, so they must be ordered.  Two plans on two streams keep two fields in flight:
+ * one field's copy in overlaps another's projection and copy out. */
+eq_status eq_project_host_async(eq_plan* plan, const void* host_in, void* host_out, void* cuda_stream);
+
 /* Wait for the plan's last eq_project and copy its `batch` diagnostics to host_out. */
 eq_status eq_norms(eq_plan* plan, eq_norms_t* host_out);
 
@@ -172,7 +179,9 @@ void eq_plan_destroy(eq_plan* plan);
 eq_status eq_plan_set_timing(eq_plan* plan, int max_calls);
 
 /* Wait for the timed calls and return, per pass, the summed device time in milliseconds over
- * them (ms_out: EQ_NUM_PASSES entries) and their number; then reset the counters. */
+ * them (ms_out: EQ_NUM_PASSES entries) and their number; then turn timing off (timed calls are
+ * launched pass by pass instead of replaying the plan's graph; eq_plan_set_timing again to time
+ * more calls). */
 eq_status eq_plan_pass_ms(eq_plan* plan, double* ms_out, int* ncalls_out);
 
 /* ---- projection without any allocation ------------------------------------------------

@@ -100,7 +100,7 @@ def eq_plan_set_timing(plan: int, max_calls: int) -> None:
 
 
 def eq_plan_pass_ms(plan: int):
-    """(dict pass name -> summed ms, number of timed calls) since the last query."""
+    """(dict pass name -> summed ms, number of timed calls); timing is off afterwards."""
     ms = (ctypes.c_double * _lib.EQ_NUM_PASSES)()
     n = ctypes.c_int()
     _lib.check(_lib.load().eq_plan_pass_ms(plan, ms, ctypes.byref(n)), "eq_plan_pass_ms")
@@ -185,15 +185,24 @@ class Plan:
                        "eq_project_padded")
         return out
 
-    def project_host(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
-        """Host tensors in and out (pinned for full bandwidth); blocks until done."""
+    def project_host(self, x: torch.Tensor, out: torch.Tensor, stream=None,
+                     wait: bool = True) -> torch.Tensor:
+        """Host tensors in and out (pinned for full bandwidth).  wait=True blocks until done;
+        wait=False only enqueues on the stream (eq_project_host_async): keep x and out untouched
+        until the stream or norms() says the call has finished."""
         for t, n in ((x, "x"), (out, "out")):
             if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() \
                     or t.numel() != self.numel:
                 raise ValueError(f"{n} must be a contiguous host {self.dtype} tensor of shape {self.shape}")
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         with torch.cuda.device(self.device):
-            eq_project_host(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
+            if wait:
+                eq_project_host(self.handle, x.data_ptr(), out.data_ptr(), s.cuda_stream)
+            else:
+                _lib.check(_lib.load().eq_project_host_async(
+                    ctypes.c_void_p(self.handle), ctypes.c_void_p(x.data_ptr()),
+                    ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream)),
+                    "eq_project_host_async")
         return out
 
     def norms(self) -> list:

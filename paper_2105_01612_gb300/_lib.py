@@ -50,6 +50,7 @@ SIGNATURES = [
                                       ctypes.POINTER(EqPlanOpts), ctypes.POINTER(c_void_p)]),
     ("eq_project", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("eq_project_host", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("eq_project_host_async", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("eq_project_hodge", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("eq_project_padded", c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("eq_norms", c_int, [c_void_p, ctypes.POINTER(EqNorms)]),

@@ -131,3 +131,22 @@ def test_autotune_keeps_results_and_writes_the_cache(tmp_path, monkeypatch):
     p2.project(x, y)
     assert rel(y[0].double().cpu().numpy(), oracle.project(x[0].double().cpu().numpy(), "ddo")) <= 2e-6
     p2.close()
+
+
+@pytest.mark.parametrize("dims", [(32, 32, 32), (30, 20, 18)])
+def test_pass_timing_covers_the_asked_calls_then_turns_off(dims):
+    nx, ny, nz = dims
+    x = torch.randn(1, 6, nz, ny, nx, device="cuda")
+    plan = eq.Plan(nx, ny, nz, torch.float32, 1)
+    ref = plan.project(x)
+    plan.set_timing(2)
+    for _ in range(2):
+        out = plan.project(x)
+    ms, n = plan.pass_ms()
+    assert n == 2 and all(v >= 0.0 for v in ms.values()) and sum(ms.values()) > 0.0
+    plan.project(x, out)                              # after pass_ms: untimed again
+    _, n2 = plan.pass_ms()
+    assert n2 == 0
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    plan.close()

@@ -166,6 +166,19 @@ def test_batch_inplace_and_host_entry():
     hout = torch.empty_like(hin).pin_memory()
     plan.project_host(hin, hout)
     torch.testing.assert_close(hout, out.cpu(), rtol=0, atol=0)
+    # asynchronous host entry: two plans on two streams, two fields in flight
+    plan2 = eq.Plan(64, 32, 16, torch.float64, 3, "ddo")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = [torch.empty_like(hin).pin_memory() for _ in range(4)]
+    for k in range(4):
+        (plan if k % 2 == 0 else plan2).project_host(hin, outs[k], stream=s1 if k % 2 == 0 else s2,
+                                                    wait=False)
+    nrm2 = plan2.norms()                                        # waits for plan2's last call
+    torch.cuda.synchronize()
+    for k in range(4):
+        torch.testing.assert_close(outs[k], out.cpu(), rtol=0, atol=0)
+    assert nrm2[0]["norm_out"] == nrm[0]["norm_out"]
+    plan2.close()
     plan.close()
 
 
