@@ -251,6 +251,7 @@ struct eq_plan {
   const void* g_in = nullptr;
   void* g_out = nullptr;
   void* g_y = nullptr;
+  int g_spec[3] = {0, 0, 0};
 };
 
 namespace {
@@ -340,14 +341,17 @@ EncodeTiled encode_fn() {
 
 // 4-D view (x, y, z, plane) of a buffer of `planes` planes (6 per stress field, 4 per potential
 // field); box of `cols` x values and `box` points along the transformed axis (2 = z, 1 = y).
+// `spec` (nullable): the buffer holds specimen-sized planes (sx, sy, sz) instead of the plan's grid;
+// a copy that reaches past them reads zeros and a store there is cut off.
 bool make_map(CUtensorMap* m, const void* base, const eq_plan* p, int axis, int cols, int box,
-              int planes) {
+              int planes, const int* spec = nullptr) {
   EncodeTiled enc = encode_fn();
   if (!enc || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
   const cuuint64_t es = p->esize;
-  const cuuint64_t dims[4] = {(cuuint64_t)p->nx, (cuuint64_t)p->ny, (cuuint64_t)p->nz,
-                              (cuuint64_t)planes};
-  const cuuint64_t strides[3] = {p->nx * es, (cuuint64_t)p->nx * p->ny * es, (cuuint64_t)p->V * es};
+  const cuuint64_t dx = spec ? spec[0] : p->nx, dy = spec ? spec[1] : p->ny, dz = spec ? spec[2] : p->nz;
+  if ((dx * es) % 16) return false;
+  const cuuint64_t dims[4] = {dx, dy, dz, (cuuint64_t)planes};
+  const cuuint64_t strides[3] = {dx * es, dx * dy * es, dx * dy * dz * es};
   const cuuint32_t boxd[4] = {(cuuint32_t)cols, axis == 1 ? (cuuint32_t)box : 1u,
                               axis == 2 ? (cuuint32_t)box : 1u, 1u};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
@@ -394,17 +398,34 @@ void tma_setup(eq_plan* p, int vz, int vy, int vx) {
   p->avail_z = p->tma_z; p->avail_y = p->tma_y; p->avail_x = p->tma_x;
 }
 
+// TMA stores through the exchange buffer: measured faster for the z passes (the 16 x 32 kernel:
+// both; the wide tiles: the last one) and slower for the y passes.  EQ_TMA_STORE overrides for
+// measurements (0 never, 1 last z pass, 2 every z pass, 3 every pass).
+bool tma_store_for(const eq_plan* p, int axis, int mode) {
+  static const int ts = [] {
+    const char* e = getenv("EQ_TMA_STORE");
+    return e && e[0] >= '0' && e[0] <= '3' ? e[0] - '0' : -1;
+  }();
+  if (ts < 0) return axis == 2 && (p->vz == 2 || mode == 2);
+  return ts == 3 || (axis == 2 && (ts == 2 || (ts == 1 && mode == 2)));
+}
+
 // Strided pass along `axis` through the TMA kernel; false if not applicable for these buffers.
 // ncomp: complex fields per field of the buffers (3 for stress fields, 2 for the potential).
+// spec (nullable): specimen size (sx, sy, sz) of the source (spec_src) and of the reference and
+// destination (spec_dst) buffers, inside the plan's grid (eq_project_padded fused into the passes).
 bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src, void* dst,
-             const void* ref, double* partials, cudaStream_t s, cudaError_t* e, int ncomp = 3) {
+             const void* ref, double* partials, cudaStream_t s, cudaError_t* e, int ncomp = 3,
+             const int* spec = nullptr, bool spec_src = false, bool spec_dst = false) {
   if (!on) return false;
   const eqk::TmaInfo& ti = axis == 2 ? p->tz : p->ty;
   CUtensorMap map, refmap, outmap;
   const int planes = 2 * ncomp * p->batch;
-  if (!make_map(&map, src, p, axis, ti.cols, ti.box, planes) ||
-      (ref && !make_map(&refmap, ref, p, axis, ti.cols, ti.box, planes)) ||
-      (dst != src && !make_map(&outmap, dst, p, axis, ti.cols, ti.box, planes))) {
+  const int* ss = spec_src ? spec : nullptr;
+  const int* sd = spec_dst ? spec : nullptr;
+  if (!make_map(&map, src, p, axis, ti.cols, ti.box, planes, ss) ||
+      (ref && !make_map(&refmap, ref, p, axis, ti.cols, ti.box, planes, sd)) ||
+      (dst != src && !make_map(&outmap, dst, p, axis, ti.cols, ti.box, planes, sd))) {
     *e = cudaErrorInvalidValue;
     return true;
   }
@@ -415,16 +436,14 @@ bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src,
   t.field_stride = 2LL * ncomp * p->V; t.V = p->V;
   t.nx = p->nx; t.ny = p->ny; t.nz = p->nz;
   t.axis = axis; t.mode = mode; t.ncomp = ncomp;
-  // TMA stores through the exchange buffer: measured faster for the z passes (the 16 x 32
-  // kernel: both; the wide tiles: the last one) and slower for the y passes.  EQ_TMA_STORE
-  // overrides for measurements (0 never, 1 last z pass, 2 every z pass, 3 every pass).
-  {
-    static const int ts = [] {
-      const char* e = getenv("EQ_TMA_STORE");
-      return e && e[0] >= '0' && e[0] <= '3' ? e[0] - '0' : -1;
-    }();
-    if (ts < 0) t.tma_store = axis == 2 && (p->vz == 2 || mode == 2);
-    else t.tma_store = ts == 3 || (axis == 2 && (ts == 2 || (ts == 1 && mode == 2)));
+  t.tma_store = tma_store_for(p, axis, mode);
+  if (sd) {                                 // cut the stores and the residual to the specimen
+    t.lim_x = sd[0]; t.lim_y = sd[1]; t.lim_z = sd[2];
+    if (mode == 2) t.mode = 3;
+    if (!t.tma_store) {                     // the per-thread stores do not cut
+      *e = cudaErrorInvalidValue;
+      return true;
+    }
   }
   t.ntiles = (axis == 2 ? (long long)p->ny : (long long)p->nz) * (p->nx / ti.cols);
   // one resident wave over (field, component) pairs: the plan's grid is sized for three
@@ -440,8 +459,14 @@ bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src,
 
 // d_y (nullable): also write the Hodge potential y into this 4-plane-per-field buffer (a
 // potential x pass before the projector, then y and z inverse passes over the buffer).
-eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, void* d_y = nullptr) {
+// spec (nullable): d_in and d_final are specimens of (sx, sy, sz) inside the plan's grid
+// (eq_project_padded): the first z pass reads d_in with zeros past its edges into the plan's
+// padded workspace, the middle passes work there, and the last z pass writes the specimen region
+// of the result into d_final.  Needs the TMA z passes with tiled stores (checked by the caller).
+eq_status enqueue(eq_plan* p, const void* d_in, void* d_final, cudaStream_t s, void* d_y = nullptr,
+                  const int* spec = nullptr) {
   const bool f32 = p->dtype == EQ_F32;
+  void* d_out = spec ? p->pad_ws : d_final;
   cudaEvent_t* ev = nullptr;
   if (p->tused < p->tcap) ev = &p->tev[(size_t)p->tused++ * (EQ_NUM_PASSES + 1)];
   if (p->gen) {
@@ -454,7 +479,8 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, voi
   mark(0);
   // the TMA passes need 16-byte aligned buffers; decide once per call so the reductions and
   // their finalisation agree on the grid
-  const bool aligned = !(reinterpret_cast<uintptr_t>(d_in) & 15) && !(reinterpret_cast<uintptr_t>(d_out) & 15);
+  const bool aligned = !(reinterpret_cast<uintptr_t>(d_in) & 15) && !(reinterpret_cast<uintptr_t>(d_out) & 15) &&
+                       !(reinterpret_cast<uintptr_t>(d_final) & 15);
   const bool on_z = p->tma_z && aligned, on_y = p->tma_y && aligned;
   const int gz_used = on_z ? p->gtz : p->g1, gl_used = on_z ? p->gtz : p->gl;
   const long long V = p->V;
@@ -472,9 +498,13 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, voi
     a.ntiles = (a.ncols + B - 1) / B;
     a.partials = p->part1; a.mode = 1; a.ncomp = 3;
     dim3 grid(p->g1, p->batch * 3);
-    if (!try_tma(p, on_z, 2, false, 1, d_in, d_out, nullptr, p->part1, s, &e))
+    if (spec) {
+      if (!try_tma(p, on_z, 2, false, 1, d_in, d_out, nullptr, p->part1, s, &e, 3, spec, true, false))
+        return fail(EQ_ERR_INVALID, "padded projection: the z passes need the TMA kernels");
+    } else if (!try_tma(p, on_z, 2, false, 1, d_in, d_out, nullptr, p->part1, s, &e)) {
       e = f32 ? eqk::launch_strided_f32(p->nz, false, a, grid, s)
               : eqk::launch_strided_f64(p->nz, false, a, grid, s);
+    }
     if (e != cudaSuccess) return fail_cuda(e, "z forward pass");
   }
   mark(1);
@@ -575,7 +605,7 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, voi
     if (e != cudaSuccess) return fail_cuda(e, "x projection pass");
   }
   mark(4);
-  const bool linf = p->opts.want_linf && d_in != d_out;
+  const bool linf = p->opts.want_linf && d_in != d_out && d_in != d_final;
   // pass 4: y inverse
   {
     dim3 grid(p->gy, p->batch * 3);
@@ -591,9 +621,14 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, voi
     az.in = d_out; az.out = d_out; az.ref = linf ? d_in : nullptr;
     az.partials = p->partl; az.mode = 2;
     dim3 grid(p->gl, p->batch * 3);
-    if (!try_tma(p, on_z, 2, true, 2, d_out, d_out, linf ? d_in : nullptr, p->partl, s, &e))
+    if (spec) {
+      if (!try_tma(p, on_z, 2, true, 2, d_out, d_final, linf ? d_in : nullptr, p->partl, s, &e, 3,
+                   spec, false, true))
+        return fail(EQ_ERR_INVALID, "padded projection: the z passes need the TMA kernels");
+    } else if (!try_tma(p, on_z, 2, true, 2, d_out, d_out, linf ? d_in : nullptr, p->partl, s, &e)) {
       e = f32 ? eqk::launch_strided_f32(p->nz, true, az, grid, s)
               : eqk::launch_strided_f64(p->nz, true, az, grid, s);
+    }
     if (e != cudaSuccess) return fail_cuda(e, "z inverse pass");
   }
   // potential: y and z inverse over the y buffer (two complex fields per field), in place
@@ -624,17 +659,20 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, voi
 
 // Enqueue one projection: replay the plan's captured CUDA graph when the buffers are the ones it
 // was captured with (capturing it first if not), or launch the passes directly when timing.
-eq_status run(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, void* d_y = nullptr) {
+eq_status run(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, void* d_y = nullptr,
+              const int* spec = nullptr) {
   cudaError_t e;
   const bool timed = p->tused < p->tcap;
+  const int sp[3] = {spec ? spec[0] : 0, spec ? spec[1] : 0, spec ? spec[2] : 0};
   if (p->opts.graph && !timed) {
-    if (!p->gexec || p->g_in != d_in || p->g_out != d_out || p->g_y != d_y) {
+    if (!p->gexec || p->g_in != d_in || p->g_out != d_out || p->g_y != d_y ||
+        p->g_spec[0] != sp[0] || p->g_spec[1] != sp[1] || p->g_spec[2] != sp[2]) {
       if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
       if (!p->cap && (e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess)
         return fail_cuda(e, "capture stream");
       if ((e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return fail_cuda(e, "begin capture");
-      eq_status st = enqueue(p, d_in, d_out, p->cap, d_y);
+      eq_status st = enqueue(p, d_in, d_out, p->cap, d_y, spec);
       cudaGraph_t graph = nullptr;
       e = cudaStreamEndCapture(p->cap, &graph);
       if (st != EQ_OK) { if (graph) cudaGraphDestroy(graph); return st; }
@@ -645,10 +683,11 @@ eq_status run(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, void* d
       p->g_in = d_in;
       p->g_out = d_out;
       p->g_y = d_y;
+      for (int i = 0; i < 3; ++i) p->g_spec[i] = sp[i];
     }
     if ((e = cudaGraphLaunch(p->gexec, s)) != cudaSuccess) return fail_cuda(e, "graph launch");
   } else {
-    eq_status st = enqueue(p, d_in, d_out, s, d_y);
+    eq_status st = enqueue(p, d_in, d_out, s, d_y, spec);
     if (st != EQ_OK) return st;
   }
   if ((e = cudaEventRecord(p->done, s)) != cudaSuccess) return fail_cuda(e, "event record");
@@ -970,6 +1009,19 @@ eq_status eq_project_padded(eq_plan* p, int sx, int sy, int sz, const void* d_in
     p->pad_part = reinterpret_cast<double*>(static_cast<unsigned char*>(p->pad_ws) + wbytes);
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // fused: the first z pass reads the specimen (zeros past its edges, from the copy engine) and
+  // the last z pass writes it back cut out, with no pass of its own for either.  Needs the TMA z
+  // passes with tiled stores on 16-byte aligned specimen rows; EQ_PAD_UNFUSED=1 forces the
+  // separate pad and cut kernels (for measurements).
+  {
+    const char* uf = getenv("EQ_PAD_UNFUSED");
+    const bool fused = !(uf && uf[0] == '1') && p->tma_z && tma_store_for(p, 2, 2) &&
+                       ((size_t)sx * p->esize) % 16 == 0 && !(i0 & 15) && !(o0 & 15);
+    if (fused) {
+      const int spec[3] = {sx, sy, sz};
+      return run(p, d_in, d_out, s, nullptr, spec);
+    }
+  }
   const long long rows = 6LL * p->batch * p->nz * p->ny;
   const int pgrid = (int)std::min<long long>((rows + 7) / 8, (long long)p->sms * 8);
   if (p->dtype == EQ_F32)

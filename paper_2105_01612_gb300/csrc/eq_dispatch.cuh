@@ -57,10 +57,11 @@ template <typename T, int N, int V> struct TmaInst {
       out->cols = C::B;
       out->box = C::BOX;
       out->smem = C::SMEM;
-      const void* fns[4] = {reinterpret_cast<const void*>(&k_strided_tma<T, N, false, 1, V>),
+      const void* fns[5] = {reinterpret_cast<const void*>(&k_strided_tma<T, N, false, 1, V>),
                             reinterpret_cast<const void*>(&k_strided_tma<T, N, false, 0, V>),
                             reinterpret_cast<const void*>(&k_strided_tma<T, N, true, 0, V>),
-                            reinterpret_cast<const void*>(&k_strided_tma<T, N, true, 2, V>)};
+                            reinterpret_cast<const void*>(&k_strided_tma<T, N, true, 2, V>),
+                            reinterpret_cast<const void*>(&k_strided_tma<T, N, true, 3, V>)};
       cudaError_t e = cudaSuccess;
       for (const void* f : fns)
         if (e == cudaSuccess)
@@ -83,6 +84,8 @@ template <typename T, int N, int V> struct TmaInst {
         k_strided_tma<T, N, false, 0, V><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
       else if (a.mode == 2)
         k_strided_tma<T, N, true, 2, V><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
+      else if (a.mode == 3)
+        k_strided_tma<T, N, true, 3, V><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
       else
         k_strided_tma<T, N, true, 0, V><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
       return cudaGetLastError();
@@ -98,10 +101,11 @@ struct Tma16Inst {
     out->cols = C::B;
     out->box = C::BOX;
     out->smem = C::SMEM;
-    const void* fns[4] = {reinterpret_cast<const void*>(&k_strided16<false, 1>),
+    const void* fns[5] = {reinterpret_cast<const void*>(&k_strided16<false, 1>),
                           reinterpret_cast<const void*>(&k_strided16<false, 0>),
                           reinterpret_cast<const void*>(&k_strided16<true, 0>),
-                          reinterpret_cast<const void*>(&k_strided16<true, 2>)};
+                          reinterpret_cast<const void*>(&k_strided16<true, 2>),
+                          reinterpret_cast<const void*>(&k_strided16<true, 3>)};
     cudaError_t e = cudaSuccess;
     for (const void* f : fns)
       if (e == cudaSuccess)
@@ -120,6 +124,8 @@ struct Tma16Inst {
       k_strided16<false, 0><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
     else if (a.mode == 2)
       k_strided16<true, 2><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
+    else if (a.mode == 3)
+      k_strided16<true, 3><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
     else
       k_strided16<true, 0><<<grid, C::THREADS, C::SMEM, s>>>(map, refmap, outmap, a);
     return cudaGetLastError();

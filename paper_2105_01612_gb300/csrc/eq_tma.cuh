@@ -102,11 +102,19 @@ struct TmaArgs {
   int mode;                // 0 middle, 1 first (statistics), 2 last
   int tma_store;           // 1: store tiles by TMA through the exchange buffer
   int ncomp;               // complex fields (pairs of planes) per field: 3 (stress), 2 (potential)
+  int lim_x, lim_y, lim_z; // > 0: the destination and reference hold only this specimen region
+                           // (TMA stores only; boxes outside it are skipped, L-inf is cut to it)
   long long ntiles;        // tiles per (field, component)
 };
 
+// Inside the specimen limits of a TmaArgs (no limits: always); x column, y row, z point.
+__device__ __forceinline__ bool in_spec(const TmaArgs& a, int x, int y, int z) {
+  return a.lim_x == 0 || (x < a.lim_x && y < a.lim_y && z < a.lim_z);
+}
+
 // MODE: 0 middle pass, 1 first pass (input statistics), 2 last pass (L-inf against a.ref, whose
-// tile streams through `refmap` into the stage the transform has just read, while it computes).
+// tile streams through `refmap` into the stage the transform has just read, while it computes),
+// 3 the last pass of a specimen inside the grid (as 2, with the L-inf cut to the specimen).
 // At 1024 threads a thread has 64 registers; the running statistics of MODE 1 (three compensated
 // sums) and the L-inf of MODE 2 live in a per-thread slot of shared memory instead, so that no
 // register spills to local memory (whose reloads would go to L2 every tile).  The transformed
@@ -200,7 +208,7 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
     __syncthreads();                                   // stage s is free again
     if (tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (MODE == 2 && a.ref) issue(u, s, &refmap);    // this tile's input, for the residual
+      if (MODE >= 2 && a.ref) issue(u, s, &refmap);    // this tile's input, for the residual
       else if (u + 2 * step < ntiles) issue(u + 2 * step, s, &map);
     }
     if constexpr (MODE == 1) {
@@ -256,6 +264,11 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
         for (int p = 0; p < 2; ++p)
 #pragma unroll
           for (int q = 0; q < NBOX; ++q) {
+            // a box starting outside the specimen region (when one is set) is skipped; one that
+            // reaches past its edge is cut by the copy
+            if (a.lim_x && (x0 >= a.lim_x || row >= (a.axis == 2 ? a.lim_y : a.lim_z) ||
+                            q * BOX >= (a.axis == 2 ? a.lim_z : a.lim_y)))
+              continue;
             const T* src = ore + p * N * B + q * BOX * B;
             if (a.axis == 2) tma_store_4d(&outmap, src, x0, row, q * BOX, plane_re + p);
             else tma_store_4d(&outmap, src, x0, q * BOX, row, plane_re + p);
@@ -263,7 +276,7 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     }
-    if constexpr (MODE == 2) {
+    if constexpr (MODE >= 2) {
       if (a.ref) {
         if (tid == 0 && !mbar_wait(&bar[s], (unsigned)((s ? ph1 : ph0) & 1))) {
           atomicOr(a.err, 1);
@@ -274,10 +287,13 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
         if (abort_flag) break;
         const T* sre = stage0 + s * 2 * N * B;
         T linf = acc[tid];
+        const int x0 = (u % tiles_x) * B + b, row = u / tiles_x;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          linf = fmax(linf, fabs(sre[(t + TPC * e) * B + b] - x[e].x));
-          linf = fmax(linf, fabs(sre[N * B + (t + TPC * e) * B + b] - x[e].y));
+          const int pt = t + TPC * e;
+          if (MODE == 3 && !in_spec(a, x0, a.axis == 2 ? row : pt, a.axis == 2 ? pt : row)) continue;
+          linf = fmax(linf, fabs(sre[pt * B + b] - x[e].x));
+          linf = fmax(linf, fabs(sre[N * B + pt * B + b] - x[e].y));
         }
         acc[tid] = linf;
         __syncthreads();                               // stage s read: refill with tile k + 2
@@ -310,7 +326,7 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
       double* p = a.partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 4;
       p[0] = v[0]; p[1] = v[1]; p[2] = v[2]; p[3] = nonfinite ? 1.0 : 0.0;
     }
-  } else if constexpr (MODE == 2) {
+  } else if constexpr (MODE >= 2) {
     if (a.ref) {
       double m = block_max(double(acc[tid]), red);
       if (tid == 0) a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = m;
@@ -454,7 +470,7 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
     __syncthreads();                                 // exchange written; stage s fully read
     if (tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (MODE == 2 && a.ref) issue(u, s, &refmap);  // this tile's input, for the residual
+      if (MODE >= 2 && a.ref) issue(u, s, &refmap);  // this tile's input, for the residual
       else if (u + 2 * step < ntiles) issue(u + 2 * step, s, &map);
     }
 #pragma unroll
@@ -502,6 +518,11 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
         for (int p = 0; p < 2; ++p)
 #pragma unroll
           for (int q = 0; q < NBOX; ++q) {
+            // a box starting outside the specimen region (when one is set) is skipped; one that
+            // reaches past its edge is cut by the copy
+            if (a.lim_x && (x0 >= a.lim_x || row >= (a.axis == 2 ? a.lim_y : a.lim_z) ||
+                            q * BOX >= (a.axis == 2 ? a.lim_z : a.lim_y)))
+              continue;
             const T* src = ore + p * N * B + q * BOX * B;
             if (a.axis == 2) tma_store_4d(&outmap, src, x0, row, q * BOX, plane_re + p);
             else tma_store_4d(&outmap, src, x0, q * BOX, row, plane_re + p);
@@ -509,7 +530,7 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     }
-    if constexpr (MODE == 2) {
+    if constexpr (MODE >= 2) {
       if (a.ref) {
         if (tid == 0 && !mbar_wait(&bar[s], (unsigned)((s ? ph1 : ph0) & 1))) {
           atomicOr(a.err, 1);
@@ -520,9 +541,12 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
         if (abort_flag) break;
         const T* sre = stage0 + s * 2 * N * B;
         T linf = acc[tid];
+        const int x0 = (u % tiles_x) * B + b, row = u / tiles_x;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const int pnt = (kap + 16 * q + 256 * h) * B + b;
+          const int pt = kap + 16 * q + 256 * h;
+          if (MODE == 3 && !in_spec(a, x0, a.axis == 2 ? row : pt, a.axis == 2 ? pt : row)) continue;
+          const int pnt = pt * B + b;
           linf = fmax(linf, fabs(sre[pnt] - v[q].x));
           linf = fmax(linf, fabs(sre[N * B + pnt] - v[q].y));
         }
@@ -555,7 +579,7 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
       double* p = a.partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 4;
       p[0] = r[0]; p[1] = r[1]; p[2] = r[2]; p[3] = nonfinite ? 1.0 : 0.0;
     }
-  } else if constexpr (MODE == 2) {
+  } else if constexpr (MODE >= 2) {
     if (a.ref) {
       double m = block_max(double(acc[tid]), red);
       if (tid == 0) a.partials[(long long)blockIdx.y * gridDim.x + blockIdx.x] = m;

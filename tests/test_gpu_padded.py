@@ -87,3 +87,20 @@ def test_rejections():
                                ctypes.c_void_p(x.data_ptr()), None)
     assert st == _lib.EQ_ERR_INVALID and b"fit" in lib.eq_last_error()
     plan.close()
+
+
+@pytest.mark.parametrize("spec,grid,dtype", [
+    ((100, 120, 92), (128, 128, 128), torch.float32),     # fused: TMA z passes, 16-byte rows
+    ((40, 50, 36), (64, 64, 64), torch.float64),
+    ((64, 40, 28), (64, 64, 64), torch.float32),          # no padding along z
+    ((30, 64, 64), (64, 64, 64), torch.float64),          # padding along z only
+])
+def test_fused_padding_matches_the_separate_kernels_and_the_oracle(spec, grid, dtype, monkeypatch):
+    s = voronoi_stress_field(spec, 20, 150.0, 15.0, 80 + spec[0]).numpy()
+    fused, nf = run(s, grid, dtype)
+    monkeypatch.setenv("EQ_PAD_UNFUSED", "1")
+    sep, ns = run(s, grid, dtype)
+    assert np.array_equal(fused, sep)
+    for k in ("norm_in", "norm_out", "resid_l2", "resid_linf", "div_in_l2"):
+        assert nf[0][k] == ns[0][k], k
+    assert rel(fused, oracle.project_padded(s, grid)) <= (1e-12 if dtype == torch.float64 else 2e-6)
