@@ -119,3 +119,11 @@ def test_grain_map_validation_without_a_gpu(lib):
     assert lib.eq_grains_create(ids, 2, 2, 2, 0, ctypes.byref(h)) == EQ_ERR_INVALID
     assert lib.eq_grain_average(None, 0, 1, None, None, None, None) == EQ_ERR_INVALID
     lib.eq_grains_destroy(None)
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
+    from paper_2105_01612_gb300._lib import EQ_ERR_INVALID
+    assert lib.eq_project_hodge(None, None, None, None, None) == EQ_ERR_INVALID
+    assert lib.eq_project_padded(None, 8, 8, 8, None, None, None) == EQ_ERR_INVALID
+    assert lib.eq_project_host_async(None, None, None, None) == EQ_ERR_INVALID
+    assert b"NULL" in lib.eq_last_error()
