@@ -35,6 +35,8 @@ struct AxisPlan {
   int tw;             // offset (complex entries) of exp(-2 pi i j / m), j < m, in the pool
   int chirp;          // Bluestein: n entries c_j = exp(-pi i j^2 / n)
   int bhat;           // Bluestein: m entries DFT_m(conj c, wrapped) / m
+  int fast;           // 1: m is a power of two served by the fixed-size register FFT when the
+                      //    pass shape gives it a compiled (m, points per thread) instance
 };
 
 struct FieldDesc {
@@ -166,12 +168,65 @@ __device__ __forceinline__ void load_tables(const AxisPlan& ap, const T2* __rest
     for (int i = threadIdx.x; i < ap.n; i += blockDim.x) chs[i] = cpool[ap.chirp + i];
 }
 
+// Power-of-two length M with the fixed-size register FFT of the compile-time passes: thread
+// (col, t) = (tid % C, tid / C) holds elements t + (M / E) e of column col (E per thread, so
+// blockDim = C M / E), exchanging through b.  Bluestein: forward, times the chirp transform,
+// inverse (the inverse direction is handled by the caller's conjugation); otherwise one transform.
+// Leaves the outputs in a (natural order) behind a barrier and returns a.
+template <int M, int E, typename T2>
+__device__ __noinline__ T2* fast_transform(T2* a, T2* b, int C, int pitch, const T2* tws,
+                                           const T2* bhs, bool blue, bool inv) {
+  constexpr int TPC = M / E;
+  const int col = threadIdx.x % C, t = threadIdx.x / C;
+  T2 x[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) x[e] = a[(t + TPC * e) * pitch + col];
+  const eqk::IdxStrided idx{col, pitch};
+  if (blue) {
+    eqk::fft_column<M, E, false>(x, t, b, idx, tws);
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = cmul(x[e], bhs[t + TPC * e]);
+    eqk::fft_column<M, E, true>(x, t, b, idx, tws);
+  } else if (inv) {
+    eqk::fft_column<M, E, true>(x, t, b, idx, tws);
+  } else {
+    eqk::fft_column<M, E, false>(x, t, b, idx, tws);
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) a[(t + TPC * e) * pitch + col] = x[e];
+  __syncthreads();
+  return a;
+}
+
+// The compiled (M, E) instances; nullptr when the pass shape has none (runtime stages then).
+template <typename T2>
+__device__ __forceinline__ T2* fast_dispatch(T2* a, T2* b, const AxisPlan& ap, int C, int pitch,
+                                             const T2* tws, const T2* bhs, bool inv) {
+  const int tpc = blockDim.x / C;
+  const int e = ap.m / tpc;
+  if (tpc * C != (int)blockDim.x || e * tpc != ap.m) return nullptr;
+  const bool blue = ap.blue != 0;
+  switch (ap.m * 64 + e) {
+    case 128 * 64 + 8: return fast_transform<128, 8>(a, b, C, pitch, tws, bhs, blue, inv);
+    case 256 * 64 + 8: return fast_transform<256, 8>(a, b, C, pitch, tws, bhs, blue, inv);
+    case 256 * 64 + 16: return fast_transform<256, 16>(a, b, C, pitch, tws, bhs, blue, inv);
+    case 512 * 64 + 8: return fast_transform<512, 8>(a, b, C, pitch, tws, bhs, blue, inv);
+    case 512 * 64 + 16: return fast_transform<512, 16>(a, b, C, pitch, tws, bhs, blue, inv);
+    case 1024 * 64 + 16: return fast_transform<1024, 16>(a, b, C, pitch, tws, bhs, blue, inv);
+    default: return nullptr;
+  }
+}
+
 // Full axis transform of the C columns held in `a` (element-major, pitch `pitch`).  For Bluestein
 // the caller has already multiplied by the chirp and zero-filled [n, m).  Returns the buffer with
 // the outputs (before the Bluestein post-chirp, see post()).
 template <typename T2>
 __device__ T2* axis_transform(T2* a, T2* b, const AxisPlan& ap, int C, int pitch, const T2* tws,
                               const T2* bhs, bool inv) {
+  if (ap.fast) {
+    T2* r = fast_dispatch(a, b, ap, C, pitch, tws, bhs, inv);
+    if (r) return r;
+  }
   if (!ap.blue) return inv ? gen_fft<true>(a, b, ap, C, pitch, tws) : gen_fft<false>(a, b, ap, C, pitch, tws);
   T2* r = gen_fft<false>(a, b, ap, C, pitch, tws);
   T2* o = (r == a) ? b : a;

@@ -235,9 +235,21 @@ void build_tables(GenPlan* g, const std::vector<int>& lens, std::vector<unsigned
     if (factorize(n, r)) {
       ap.m = n;
       ap.blue = 0;
+      ap.fast = (n >= 128 && n <= 1024 && (n & (n - 1)) == 0) ? 1 : 0;
     } else {
+      // Bluestein: up to n = 256 a power-of-two length (served by the register FFT) although a
+      // smooth length can be shorter; beyond, the smallest smooth length (shared memory)
       int m = 2 * n - 1;
-      while (!factorize(m, r)) ++m;
+      int p2 = 1;
+      while (p2 < m) p2 <<= 1;
+      if (p2 <= 512) {
+        m = p2;
+        factorize(m, r);
+        ap.fast = 1;
+      } else {
+        while (!factorize(m, r)) ++m;
+        ap.fast = 0;
+      }
       ap.m = m;
       ap.blue = 1;
     }

@@ -32,7 +32,12 @@ def as_dtype(s, dtype):
 
 
 @pytest.mark.parametrize("shape", [(3, 5, 7), (6, 10, 9), (26, 13, 11), (23, 19, 17), (4, 34, 67),
-                                   (2, 3, 97), (5, 2, 250), (37, 31, 33), (1, 1, 7), (7, 1, 1)])
+                                   (2, 3, 97), (5, 2, 250), (37, 31, 33), (1, 1, 7), (7, 1, 1),
+                                   # power-of-two transform lengths (the fixed-size register
+                                   # FFT): Bluestein convolutions of 128, 256 and 512 points on
+                                   # each axis, and direct transforms of 128 and 256 points
+                                   (139, 3, 5), (4, 151, 6), (3, 2, 179), (47, 90, 5), (256, 6, 5),
+                                   (3, 128, 4), (5, 3, 256)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_any_size_matches_oracle(shape, dtype):
     s = as_dtype(voronoi_stress_field(shape, 5, 100.0, 10.0, sum(shape)).numpy(), dtype)
