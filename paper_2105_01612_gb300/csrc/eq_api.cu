@@ -97,6 +97,19 @@ __global__ void k_finalize_norms(const double* __restrict__ partx, int gridx,
   }
 }
 
+// The plan's norms and error flag into its mapped host mirror, last on the stream of every call:
+// eq_norms then waits for the call's event and reads host memory, with no copy of its own that
+// could queue behind another stream's transfers on a copy engine.
+static_assert(sizeof(eq_norms_t) % 8 == 0, "eq_norms_t is copied as 8-byte words");
+__global__ void k_publish(const eq_norms_t* __restrict__ src, int batch, const int* err,
+                          eq_norms_t* hdst, int* herr) {
+  const unsigned long long* a = reinterpret_cast<const unsigned long long*>(src);
+  unsigned long long* b = reinterpret_cast<unsigned long long*>(hdst);
+  const int words = batch * (int)(sizeof(eq_norms_t) / 8);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) b[i] = a[i];
+  if (threadIdx.x == 0) *herr = err ? *err : 0;
+}
+
 // ---- non-periodic specimens in a zero-stress buffer (Sec. 5.2) ---------------------------------
 
 constexpr int PAD_GRID = 1216;  // blocks per field of the crop pass (8 x 152 SMs)
@@ -232,6 +245,12 @@ struct eq_plan {
   int gtz = 1, gty = 1, gtx = 1, gtz_max = 1, gtx_max = 1;
   int* err = nullptr;          // raised by a kernel whose bounded wait ran out
   cudaEvent_t done = nullptr;
+  // mapped pinned host mirror of the norms ([batch]) and of the error flag, written by k_publish
+  void* mirror = nullptr;
+  eq_norms_t* hnorms = nullptr;
+  int* herr = nullptr;
+  eq_norms_t* hnorms_dev = nullptr;   // the same memory as the device addresses it
+  int* herr_dev = nullptr;
   bool have_result = false;
   // staging for eq_project_host
   void* stage = nullptr;
@@ -463,8 +482,8 @@ bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src,
 // (eq_project_padded): the first z pass reads d_in with zeros past its edges into the plan's
 // padded workspace, the middle passes work there, and the last z pass writes the specimen region
 // of the result into d_final.  Needs the TMA z passes with tiled stores (checked by the caller).
-eq_status enqueue(eq_plan* p, const void* d_in, void* d_final, cudaStream_t s, void* d_y = nullptr,
-                  const int* spec = nullptr) {
+eq_status enqueue_passes(eq_plan* p, const void* d_in, void* d_final, cudaStream_t s, void* d_y,
+                         const int* spec) {
   const bool f32 = p->dtype == EQ_F32;
   void* d_out = spec ? p->pad_ws : d_final;
   cudaEvent_t* ev = nullptr;
@@ -657,6 +676,40 @@ eq_status enqueue(eq_plan* p, const void* d_in, void* d_final, cudaStream_t s, v
   return EQ_OK;
 }
 
+// The norms of the last call (and the error flag) into the plan's host mirror.
+eq_status publish(eq_plan* p, cudaStream_t s) {
+  const eq_norms_t* src = p->gen ? eqg::gen_norms_device(p->gen) : p->norms;
+  k_publish<<<1, 128, 0, s>>>(src, p->batch, p->err, p->hnorms_dev, p->herr_dev);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? EQ_OK : fail_cuda(e, "norms publish");
+}
+
+// All passes of one projection, then the norms into the host mirror.
+eq_status enqueue(eq_plan* p, const void* d_in, void* d_final, cudaStream_t s, void* d_y = nullptr,
+                  const int* spec = nullptr) {
+  eq_status st = enqueue_passes(p, d_in, d_final, s, d_y, spec);
+  return st == EQ_OK ? publish(p, s) : st;
+}
+
+// Mapped pinned memory for the host mirror of the norms and the error flag.
+eq_status alloc_mirror(eq_plan* p) {
+  const size_t nb = sizeof(eq_norms_t) * (size_t)p->batch;
+  cudaError_t e = cudaHostAlloc(&p->mirror, nb + 64, cudaHostAllocMapped);
+  if (e != cudaSuccess) {
+    p->mirror = nullptr;
+    return fail_cuda(e, "cudaHostAlloc (norms mirror)");
+  }
+  std::memset(p->mirror, 0, nb + 64);
+  void* dev = nullptr;
+  if ((e = cudaHostGetDevicePointer(&dev, p->mirror, 0)) != cudaSuccess)
+    return fail_cuda(e, "cudaHostGetDevicePointer (norms mirror)");
+  p->hnorms = static_cast<eq_norms_t*>(p->mirror);
+  p->herr = reinterpret_cast<int*>(static_cast<unsigned char*>(p->mirror) + nb);
+  p->hnorms_dev = static_cast<eq_norms_t*>(dev);
+  p->herr_dev = reinterpret_cast<int*>(static_cast<unsigned char*>(dev) + nb);
+  return EQ_OK;
+}
+
 // Enqueue one projection: replay the plan's captured CUDA graph when the buffers are the ones it
 // was captured with (capturing it first if not), or launch the passes directly when timing.
 eq_status run(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, void* d_y = nullptr,
@@ -701,6 +754,7 @@ void release(eq_plan* p) {
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->cap) cudaStreamDestroy(p->cap);
   if (p->done) cudaEventDestroy(p->done);
+  if (p->mirror) cudaFreeHost(p->mirror);
   if (p->dmem) cudaFree(p->dmem);
   if (p->stage) cudaFree(p->stage);
   if (p->pad_ws) cudaFree(p->pad_ws);
@@ -756,6 +810,10 @@ static eq_status create_generic(const int* dims, int count, eq_dtype dtype, cons
   if (st != EQ_OK) { release(p); return fail(st, "eq_plan_create: " + err); }
   p->total_elems = eqg::gen_total_elems(p->gen);
   p->dbytes = eqg::gen_device_bytes(p->gen);
+  if (alloc_mirror(p) != EQ_OK) {
+    release(p);
+    return EQ_ERR_CUDA;
+  }
   if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess) {
     release(p);
     return fail_cuda(e, "cudaEventCreate");
@@ -924,6 +982,10 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
     release(p);
     return fail_cuda(e, "pair table upload");
   }
+  if (alloc_mirror(p) != EQ_OK) {
+    release(p);
+    return EQ_ERR_CUDA;
+  }
   if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess) {
     release(p);
     return fail_cuda(e, "cudaEventCreate");
@@ -1046,6 +1108,8 @@ eq_status eq_project_padded(eq_plan* p, int sx, int sy, int sz, const void* d_in
   if (p->opts.want_linf) {
     k_pad_linf<<<1, 128, 0, s>>>(p->pad_part, PAD_GRID, p->batch, p->norms);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "eq_project_padded: L-inf");
+    eq_status pst = publish(p, s);
+    if (pst != EQ_OK) return pst;
   }
   // eq_norms waits for the last kernel of this call
   if ((e = cudaEventRecord(p->done, s)) != cudaSuccess) return fail_cuda(e, "event record");
@@ -1108,18 +1172,15 @@ eq_status eq_norms(eq_plan* p, eq_norms_t* host_out) {
   if (!p->have_result) return fail(EQ_ERR_INVALID, "eq_norms: no projection enqueued yet");
   cudaError_t e;
   if ((e = cudaEventSynchronize(p->done)) != cudaSuccess) return fail_cuda(e, "eq_norms: wait");
-  if (p->err) {
-    int flag = 0;
-    if ((e = cudaMemcpy(&flag, p->err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+  // the call's last kernel has written the host mirror
+  volatile int* herr = p->herr;
+  if (*herr) {
+    *herr = 0;
+    if (p->err && (e = cudaMemset(p->err, 0, sizeof(int))) != cudaSuccess)
       return fail_cuda(e, "eq_norms: error flag");
-    if (flag) {
-      cudaMemset(p->err, 0, sizeof(int));
-      return fail(EQ_ERR_TIMEOUT, "eq_norms: a bounded wait inside a kernel ran out; results are invalid");
-    }
+    return fail(EQ_ERR_TIMEOUT, "eq_norms: a bounded wait inside a kernel ran out; results are invalid");
   }
-  const eq_norms_t* src = p->gen ? eqg::gen_norms_device(p->gen) : p->norms;
-  if ((e = cudaMemcpy(host_out, src, sizeof(eq_norms_t) * p->batch, cudaMemcpyDeviceToHost)) != cudaSuccess)
-    return fail_cuda(e, "eq_norms: copy");
+  std::memcpy(host_out, p->hnorms, sizeof(eq_norms_t) * p->batch);
   return EQ_OK;
 }
 

@@ -217,12 +217,15 @@ k_strided_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ C
       // type's range, which the flag then reports as well)
       const T wa = comp == 2 ? T(2) : T(1), wb = comp == 0 ? T(1) : T(2);
       T tsum[3] = {T(0), T(0), T(0)};
+      T sx2 = T(0), sy2 = T(0);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         tsum[0] += x[e].x;
         tsum[1] += x[e].y;
-        tsum[2] += wa * x[e].x * x[e].x + wb * x[e].y * x[e].y;
+        sx2 = fma(x[e].x, x[e].x, sx2);
+        sy2 = fma(x[e].y, x[e].y, sy2);
       }
+      tsum[2] = wa * sx2 + wb * sy2;
       if (!isfinite(tsum[0]) || !isfinite(tsum[1])) nonfinite = 1;
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
@@ -438,15 +441,32 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
       for (int e = 0; e < 16; ++e)
         v[e] = T2{sre[(t + 32 * e) * B + b], sre[N * B + (t + 32 * e) * B + b]};
     }
+    // last pass: stage s is read, so this tile's input (for the residual) can start loading into
+    // it now rather than behind the exchange; the other passes refill it there instead (an extra
+    // barrier measured slower for them)
+    constexpr bool EARLY = MODE >= 2;
+    if (EARLY && a.ref) {
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(u, s, &refmap);
+      }
+    }
+    T sx2 = T(0), sy2 = T(0);
     if constexpr (MODE == 1) {
-      const T wa = comp == 2 ? T(2) : T(1), wb = comp == 0 ? T(1) : T(2);
-      T tsum[3] = {T(0), T(0), T(0)};
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
-        tsum[0] += v[e].x;
-        tsum[1] += v[e].y;
-        tsum[2] += wa * v[e].x * v[e].x + wb * v[e].y * v[e].y;
+        sx2 = fma(v[e].x, v[e].x, sx2);
+        sy2 = fma(v[e].y, v[e].y, sy2);
       }
+    }
+    // transform: 16-point DFT over e, twiddle, exchange
+    dft16<INV>(v);
+    if constexpr (MODE == 1) {
+      // statistics of the 16 points: sums from the DFT's zero-frequency output (their plain sum),
+      // squares weighted by the Voigt multiplicity of each plane (xx yy | zz yz | xz xy)
+      const T wa = comp == 2 ? T(2) : T(1), wb = comp == 0 ? T(1) : T(2);
+      const T tsum[3] = {v[0].x, v[0].y, wa * sx2 + wb * sy2};
       if (!isfinite(tsum[0]) || !isfinite(tsum[1])) nonfinite = 1;
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
@@ -456,8 +476,6 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
         acc[(2 * j + 1) * THREADS + tid] = kh.c;
       }
     }
-    // transform: 16-point DFT over e, twiddle, exchange
-    dft16<INV>(v);
 #pragma unroll
     for (int k1 = 1; k1 < 16; ++k1) {
       T2 w = tw[k1 * 32 + t];
@@ -468,10 +486,9 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) xc[k1 * 32 + (t ^ (2 * k1))] = v[k1];
     __syncthreads();                                 // exchange written; stage s fully read
-    if (tid == 0) {
+    if (tid == 0 && !(EARLY && a.ref) && u + 2 * step < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (MODE >= 2 && a.ref) issue(u, s, &refmap);  // this tile's input, for the residual
-      else if (u + 2 * step < ntiles) issue(u + 2 * step, s, &map);
+      issue(u + 2 * step, s, &map);
     }
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = xc[kap * 32 + h + 2 * (m ^ kap)];
