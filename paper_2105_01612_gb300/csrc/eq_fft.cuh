@@ -21,6 +21,24 @@ template <> struct V2<double> { using t = double2; };
 
 template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return {a.x + b.x, a.y + b.y}; }
 template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { return {a.x - b.x, a.y - b.y}; }
+// FP32: one packed two-lane instruction (sm_100 and later) for both parts, rounded like the
+// scalar operations
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+// r + s * v for a real s, both parts
+template <typename T2, typename T> __device__ __forceinline__ T2 cfma_s(T s, T2 v, T2 r) {
+  return {r.x + s * v.x, r.y + s * v.y};
+}
+__device__ __forceinline__ float2 cfma_s(float s, float2 v, float2 r) {
+  return __ffma2_rn(make_float2(s, s), v, r);
+}
 template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
   return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
@@ -353,7 +371,7 @@ __device__ __forceinline__ void fft512_warp(T2 (&v)[16], int lane, T2* buf,
     T2 recv;
     recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
     recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
-    v[q] = T2{recv.x + sg * send.x, recv.y + sg * send.y};
+    v[q] = cfma_s(sg, send, recv);
   }
 }
 

@@ -500,7 +500,7 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
       T2 recv;
       recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
       recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
-      v[q] = T2{recv.x + sg * send.x, recv.y + sg * send.y};
+      v[q] = cfma_s(sg, send, recv);
     }
     // slot q holds point kap + 16 q + 256 h of column b
     if (!a.tma_store) {
