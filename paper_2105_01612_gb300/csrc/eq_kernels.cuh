@@ -217,107 +217,206 @@ __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
 // norm weights).  With n = xi / |xi|, v = S n and s = n . v, the projector removes
 // D = n (x) v + v (x) n - s n (x) n, whose squared Frobenius norm is 2 |v|^2 - s^2 (no
 // cancellation: |v|^2 >= s^2), and |xi . S|^2 = |xi|^2 |v|^2.
-template <typename T, typename T2>
-__device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T xi1, T xi2,
-                                             bool zero_mode, const double* mean, double vol,
-                                             bool nyq_zero, bool compat, T inv_v, T mult,
-                                             Kahan<T>& r2, Kahan<T>& di2, Kahan<T>& do2,
-                                             Kahan<T>& o2) {
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+
+// FP32 form of project_pair below, the same arithmetic with the real and imaginary parts of each
+// doubled Voigt component held as one pair P_j = {Re, Im} and worked by packed two-lane
+// instructions (one instruction for both parts wherever they meet the same real factor).
+__device__ __forceinline__ void project_pair_f32x2(float2 (&a)[3], float2 (&bb)[3], float xi0,
+                                                   float xi1, float xi2, bool zero_mode,
+                                                   const double* mean, double vol, bool nyq_zero,
+                                                   bool compat, float inv_v, float mult,
+                                                   Kahan<float>& r2, Kahan<float>& di2,
+                                                   Kahan<float>& do2, Kahan<float>& o2) {
   // 2 S_2c = A + conj B, 2 S_2c+1 = -i (A - conj B)
-  T sr[6], si[6];
+  float2 P[6];
+  const float2 pm = make_float2(1.f, -1.f);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    sr[2 * c] = a[c].x + bb[c].x;
-    si[2 * c] = a[c].y - bb[c].y;
-    sr[2 * c + 1] = a[c].y + bb[c].y;
-    si[2 * c + 1] = bb[c].x - a[c].x;
+    P[2 * c] = __ffma2_rn(bb[c], pm, a[c]);
+    P[2 * c + 1] = make_float2(a[c].y + bb[c].y, bb[c].x - a[c].x);
   }
   if (zero_mode && mean) {
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      sr[j] = T(2.0 * mean[j] * vol);
-      si[j] = T(0);
-    }
+    for (int j = 0; j < 6; ++j) P[j] = make_float2(float(2.0 * mean[j] * vol), 0.f);
   }
-  const T k2 = xi0 * xi0 + xi1 * xi1 + xi2 * xi2;
-  T orr[6], oi[6];
-  T rr = T(0), din = T(0);
-  if (k2 > T(0)) {
-    const T rn = rsqrt_t(k2);
-    const T n0 = xi0 * rn, n1 = xi1 * rn, n2 = xi2 * rn;
-    // Voigt slots: 0 xx, 1 yy, 2 zz, 3 yz, 4 xz, 5 xy
-#define EQ_PROJ(S, O)                                                         \
-    {                                                                          \
-      const T v0 = S[0] * n0 + S[5] * n1 + S[4] * n2;                          \
-      const T v1 = S[5] * n0 + S[1] * n1 + S[3] * n2;                          \
-      const T v2 = S[4] * n0 + S[3] * n1 + S[2] * n2;                          \
-      const T s = n0 * v0 + n1 * v1 + n2 * v2;                                 \
-      const T vv = v0 * v0 + v1 * v1 + v2 * v2;                               \
-      rr += T(2) * vv - s * s;                                                 \
-      din += k2 * vv;                                                          \
-      O[0] = S[0] - T(2) * n0 * v0 + s * n0 * n0;                              \
-      O[1] = S[1] - T(2) * n1 * v1 + s * n1 * n1;                              \
-      O[2] = S[2] - T(2) * n2 * v2 + s * n2 * n2;                              \
-      O[3] = S[3] - n1 * v2 - v1 * n2 + s * n1 * n2;                           \
-      O[4] = S[4] - n0 * v2 - v0 * n2 + s * n0 * n2;                           \
-      O[5] = S[5] - n0 * v1 - v0 * n1 + s * n0 * n1;                           \
-    }
-    EQ_PROJ(sr, orr)
-    EQ_PROJ(si, oi)
-#undef EQ_PROJ
+  const float k2 = xi0 * xi0 + xi1 * xi1 + xi2 * xi2;
+  float2 O[6];
+  float rr = 0.f, din = 0.f;
+  if (k2 > 0.f) {
+    const float rn = rsqrtf(k2);
+    const float n0 = xi0 * rn, n1 = xi1 * rn, n2 = xi2 * rn;
+    const float2 N0 = bc2(n0), N1 = bc2(n1), N2 = bc2(n2);
+    // v = S n, s = n . v (Voigt slots: 0 xx, 1 yy, 2 zz, 3 yz, 4 xz, 5 xy)
+    const float2 V0 = __ffma2_rn(P[4], N2, __ffma2_rn(P[5], N1, __fmul2_rn(P[0], N0)));
+    const float2 V1 = __ffma2_rn(P[3], N2, __ffma2_rn(P[1], N1, __fmul2_rn(P[5], N0)));
+    const float2 V2 = __ffma2_rn(P[2], N2, __ffma2_rn(P[3], N1, __fmul2_rn(P[4], N0)));
+    const float2 S = __ffma2_rn(N2, V2, __ffma2_rn(N1, V1, __fmul2_rn(N0, V0)));
+    const float2 VV = __ffma2_rn(V2, V2, __ffma2_rn(V1, V1, __fmul2_rn(V0, V0)));
+    const float2 R = __ffma2_rn(__fmul2_rn(S, bc2(-1.f)), S, __fadd2_rn(VV, VV));   // 2|v|^2 - s^2
+    rr = R.x + R.y;
+    din = k2 * (VV.x + VV.y);
+    O[0] = __ffma2_rn(S, bc2(n0 * n0), __ffma2_rn(V0, bc2(-2.f * n0), P[0]));
+    O[1] = __ffma2_rn(S, bc2(n1 * n1), __ffma2_rn(V1, bc2(-2.f * n1), P[1]));
+    O[2] = __ffma2_rn(S, bc2(n2 * n2), __ffma2_rn(V2, bc2(-2.f * n2), P[2]));
+    O[3] = __ffma2_rn(S, bc2(n1 * n2), __ffma2_rn(V1, bc2(-n2), __ffma2_rn(V2, bc2(-n1), P[3])));
+    O[4] = __ffma2_rn(S, bc2(n0 * n2), __ffma2_rn(V0, bc2(-n2), __ffma2_rn(V2, bc2(-n0), P[4])));
+    O[5] = __ffma2_rn(S, bc2(n0 * n1), __ffma2_rn(V0, bc2(-n1), __ffma2_rn(V1, bc2(-n0), P[5])));
   } else {
     // the zero mode and the all-Nyquist corners: kept, or dropped (literal route, not the mean)
     const bool drop = nyq_zero && !zero_mode;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-      const T w = j < 3 ? T(1) : T(2);
-      if (drop) rr += w * (sr[j] * sr[j] + si[j] * si[j]);
-      orr[j] = drop ? T(0) : sr[j];
-      oi[j] = drop ? T(0) : si[j];
+      const float w = j < 3 ? 1.f : 2.f;
+      if (drop) rr += w * (P[j].x * P[j].x + P[j].y * P[j].y);
+      O[j] = drop ? make_float2(0.f, 0.f) : P[j];
     }
   }
+  // sum over j of w_j |X_j|^2 (w = 1 for the normal, 2 for the shear slots), both parts
+  auto wnorm = [](const float2 (&X)[6]) {
+    const float2 d = __ffma2_rn(X[2], X[2], __ffma2_rn(X[1], X[1], __fmul2_rn(X[0], X[0])));
+    const float2 o = __ffma2_rn(X[5], X[5], __ffma2_rn(X[4], X[4], __fmul2_rn(X[3], X[3])));
+    const float2 q = __ffma2_rn(o, bc2(2.f), d);
+    return q.x + q.y;
+  };
   // compatible part: out = S - O away from k = 0; the residual S - out is then O
   if (compat && !zero_mode) {
-    T o2n = T(0);
+    const float o2n = wnorm(O);
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const T w = j < 3 ? T(1) : T(2);
-      o2n += w * (orr[j] * orr[j] + oi[j] * oi[j]);
-      orr[j] = sr[j] - orr[j];
-      oi[j] = si[j] - oi[j];
-    }
+    for (int j = 0; j < 6; ++j) O[j] = csub(P[j], O[j]);
     rr = o2n;
   }
   // norm terms (sums of |.|^2 over modes; Parseval turns them into voxel means)
   {
-    T oo = T(0), dout = T(0);
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const T w = j < 3 ? T(1) : T(2);
-      oo += w * (orr[j] * orr[j] + oi[j] * oi[j]);
-    }
-#define EQ_DIV(S, ACC)                                                          \
-    {                                                                          \
-      const T d0 = xi0 * S[0] + xi1 * S[5] + xi2 * S[4];                       \
-      const T d1 = xi0 * S[5] + xi1 * S[1] + xi2 * S[3];                       \
-      const T d2 = xi0 * S[4] + xi1 * S[3] + xi2 * S[2];                       \
-      ACC += d0 * d0 + d1 * d1 + d2 * d2;                                      \
-    }
-    EQ_DIV(orr, dout) EQ_DIV(oi, dout)
-#undef EQ_DIV
-    const T m4 = T(0.25) * mult;                      // (1/2)^2 of the doubled components
+    const float oo = wnorm(O);
+    const float2 X0 = bc2(xi0), X1 = bc2(xi1), X2 = bc2(xi2);
+    const float2 D0 = __ffma2_rn(X2, O[4], __ffma2_rn(X1, O[5], __fmul2_rn(X0, O[0])));
+    const float2 D1 = __ffma2_rn(X2, O[3], __ffma2_rn(X1, O[1], __fmul2_rn(X0, O[5])));
+    const float2 D2 = __ffma2_rn(X2, O[2], __ffma2_rn(X1, O[3], __fmul2_rn(X0, O[4])));
+    const float2 DD = __ffma2_rn(D2, D2, __ffma2_rn(D1, D1, __fmul2_rn(D0, D0)));
+    const float dout = DD.x + DD.y;
+    const float m4 = 0.25f * mult;                    // (1/2)^2 of the doubled components
     r2.add(m4 * rr);
     o2.add(m4 * oo);
     di2.add(m4 * din);
     do2.add(m4 * dout);
   }
   // repack: Zout_c(k) = O_2c + i O_2c+1, Zout_c(-k) = conj(O_2c) + i conj(O_2c+1), halved
-  const T hv = T(0.5) * inv_v;
+  const float2 hv = bc2(0.5f * inv_v);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const T or_ = orr[2 * c], oi_ = oi[2 * c], pr = orr[2 * c + 1], pi_ = oi[2 * c + 1];
-    a[c] = T2{(or_ - pi_) * hv, (oi_ + pr) * hv};
-    bb[c] = T2{(or_ + pi_) * hv, (pr - oi_) * hv};
+    const float2 A = O[2 * c], B = O[2 * c + 1];
+    a[c] = __fmul2_rn(make_float2(A.x - B.y, A.y + B.x), hv);
+    bb[c] = __fmul2_rn(make_float2(A.x + B.y, B.x - A.y), hv);
+  }
+}
+
+template <typename T, typename T2>
+__device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T xi1, T xi2,
+                                             bool zero_mode, const double* mean, double vol,
+                                             bool nyq_zero, bool compat, T inv_v, T mult,
+                                             Kahan<T>& r2, Kahan<T>& di2, Kahan<T>& do2,
+                                             Kahan<T>& o2) {
+  if constexpr (sizeof(T) == 4) {
+    project_pair_f32x2(a, bb, xi0, xi1, xi2, zero_mode, mean, vol, nyq_zero, compat, inv_v, mult,
+                       r2, di2, do2, o2);
+  } else {
+    // 2 S_2c = A + conj B, 2 S_2c+1 = -i (A - conj B)
+    T sr[6], si[6];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      sr[2 * c] = a[c].x + bb[c].x;
+      si[2 * c] = a[c].y - bb[c].y;
+      sr[2 * c + 1] = a[c].y + bb[c].y;
+      si[2 * c + 1] = bb[c].x - a[c].x;
+    }
+    if (zero_mode && mean) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        sr[j] = T(2.0 * mean[j] * vol);
+        si[j] = T(0);
+      }
+    }
+    const T k2 = xi0 * xi0 + xi1 * xi1 + xi2 * xi2;
+    T orr[6], oi[6];
+    T rr = T(0), din = T(0);
+    if (k2 > T(0)) {
+      const T rn = rsqrt_t(k2);
+      const T n0 = xi0 * rn, n1 = xi1 * rn, n2 = xi2 * rn;
+      // Voigt slots: 0 xx, 1 yy, 2 zz, 3 yz, 4 xz, 5 xy
+  #define EQ_PROJ(S, O)                                                         \
+      {                                                                          \
+        const T v0 = S[0] * n0 + S[5] * n1 + S[4] * n2;                          \
+        const T v1 = S[5] * n0 + S[1] * n1 + S[3] * n2;                          \
+        const T v2 = S[4] * n0 + S[3] * n1 + S[2] * n2;                          \
+        const T s = n0 * v0 + n1 * v1 + n2 * v2;                                 \
+        const T vv = v0 * v0 + v1 * v1 + v2 * v2;                               \
+        rr += T(2) * vv - s * s;                                                 \
+        din += k2 * vv;                                                          \
+        O[0] = S[0] - T(2) * n0 * v0 + s * n0 * n0;                              \
+        O[1] = S[1] - T(2) * n1 * v1 + s * n1 * n1;                              \
+        O[2] = S[2] - T(2) * n2 * v2 + s * n2 * n2;                              \
+        O[3] = S[3] - n1 * v2 - v1 * n2 + s * n1 * n2;                           \
+        O[4] = S[4] - n0 * v2 - v0 * n2 + s * n0 * n2;                           \
+        O[5] = S[5] - n0 * v1 - v0 * n1 + s * n0 * n1;                           \
+      }
+      EQ_PROJ(sr, orr)
+      EQ_PROJ(si, oi)
+  #undef EQ_PROJ
+    } else {
+      // the zero mode and the all-Nyquist corners: kept, or dropped (literal route, not the mean)
+      const bool drop = nyq_zero && !zero_mode;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const T w = j < 3 ? T(1) : T(2);
+        if (drop) rr += w * (sr[j] * sr[j] + si[j] * si[j]);
+        orr[j] = drop ? T(0) : sr[j];
+        oi[j] = drop ? T(0) : si[j];
+      }
+    }
+    // compatible part: out = S - O away from k = 0; the residual S - out is then O
+    if (compat && !zero_mode) {
+      T o2n = T(0);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const T w = j < 3 ? T(1) : T(2);
+        o2n += w * (orr[j] * orr[j] + oi[j] * oi[j]);
+        orr[j] = sr[j] - orr[j];
+        oi[j] = si[j] - oi[j];
+      }
+      rr = o2n;
+    }
+    // norm terms (sums of |.|^2 over modes; Parseval turns them into voxel means)
+    {
+      T oo = T(0), dout = T(0);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const T w = j < 3 ? T(1) : T(2);
+        oo += w * (orr[j] * orr[j] + oi[j] * oi[j]);
+      }
+  #define EQ_DIV(S, ACC)                                                          \
+      {                                                                          \
+        const T d0 = xi0 * S[0] + xi1 * S[5] + xi2 * S[4];                       \
+        const T d1 = xi0 * S[5] + xi1 * S[1] + xi2 * S[3];                       \
+        const T d2 = xi0 * S[4] + xi1 * S[3] + xi2 * S[2];                       \
+        ACC += d0 * d0 + d1 * d1 + d2 * d2;                                      \
+      }
+      EQ_DIV(orr, dout) EQ_DIV(oi, dout)
+  #undef EQ_DIV
+      const T m4 = T(0.25) * mult;                      // (1/2)^2 of the doubled components
+      r2.add(m4 * rr);
+      o2.add(m4 * oo);
+      di2.add(m4 * din);
+      do2.add(m4 * dout);
+    }
+    // repack: Zout_c(k) = O_2c + i O_2c+1, Zout_c(-k) = conj(O_2c) + i conj(O_2c+1), halved
+    const T hv = T(0.5) * inv_v;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T or_ = orr[2 * c], oi_ = oi[2 * c], pr = orr[2 * c + 1], pi_ = oi[2 * c + 1];
+      a[c] = T2{(or_ - pi_) * hv, (oi_ + pr) * hv};
+      bb[c] = T2{(or_ + pi_) * hv, (pr - oi_) * hv};
+    }
   }
 }
 
