@@ -152,8 +152,20 @@ eq_status eq_project_host(eq_plan* plan, const void* host_in, void* host_out, vo
  * one field's copy in overlaps another's projection and copy out. */
 eq_status eq_project_host_async(eq_plan* plan, const void* host_in, void* host_out, void* cuda_stream);
 
-/* Wait for the plan's last eq_project and copy its `batch` diagnostics to host_out. */
+/* Wait for the plan's last eq_project and copy its `batch` diagnostics to host_out.  The call's
+ * last kernel has written them, with the plan's error flag, into mapped pinned host memory, so
+ * this waits for the call's event and issues no copy of its own.  EQ_ERR_TIMEOUT (and the flag
+ * cleared): a bounded wait inside one of the call's kernels ran out; its results are invalid. */
 eq_status eq_norms(eq_plan* plan, eq_norms_t* host_out);
+
+/* Failure-detection self-test (the paper has no counterpart): enqueue on cuda_stream one kernel
+ * that runs the bounded mbarrier wait of the TMA passes, limited to `polls` polls (about 64 ns
+ * each after the first 64), on a barrier that nothing completes, and raises the plan's error
+ * flag when it runs out, as a pass would.  The wait always ends: no fault, no hang.  The next
+ * eq_norms then returns EQ_ERR_TIMEOUT and clears the flag, after which the plan works as
+ * before.  EQ_ERR_INVALID: NULL plan, polls outside 1..2^24, or a runtime-length plan (whose
+ * kernels have no waits). */
+eq_status eq_selftest_wait_timeout(eq_plan* plan, long long polls, void* cuda_stream);
 
 /* Autotune the plan on the caller's buffers (d_in is only read; d_out is overwritten; work is
  * enqueued on cuda_stream and the call waits for it).  Runtime-length plans time candidate

@@ -209,6 +209,16 @@ class Plan:
         with torch.cuda.device(self.device):
             return eq_norms(self.handle, self.shape[0])
 
+    def selftest_wait_timeout(self, polls: int = 1024, stream=None) -> None:
+        """Enqueue the failure-detection self-test: a bounded wait that runs out after `polls`
+        polls and raises the plan's error flag, so that the next norms() raises EqError with
+        EQ_ERR_TIMEOUT (and clears the flag)."""
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.load().eq_selftest_wait_timeout(ctypes.c_void_p(self.handle),
+                                                            int(polls), s.cuda_stream),
+                       "eq_selftest_wait_timeout")
+
     def autotune(self, x: torch.Tensor, out: torch.Tensor, stream=None) -> None:
         """Pick the fastest pass shapes on these buffers (out is overwritten)."""
         self._check(x, "x")

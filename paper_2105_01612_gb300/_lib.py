@@ -54,6 +54,7 @@ SIGNATURES = [
     ("eq_project_hodge", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("eq_project_padded", c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("eq_norms", c_int, [c_void_p, ctypes.POINTER(EqNorms)]),
+    ("eq_selftest_wait_timeout", c_int, [c_void_p, ctypes.c_longlong, c_void_p]),
     ("eq_plan_workspace_bytes", c_size_t, [c_void_p]),
     ("eq_plan_autotune", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     ("eq_plan_set_timing", c_int, [c_void_p, c_int]),

@@ -110,6 +110,19 @@ __global__ void k_publish(const eq_norms_t* __restrict__ src, int batch, const i
   if (threadIdx.x == 0) *herr = err ? *err : 0;
 }
 
+// Failure-detection self-test: the bounded mbarrier wait of the TMA passes, on a barrier that no
+// copy and no thread ever completes, with a short limit; when it runs out the kernel raises the
+// plan's error flag exactly as a pass does, and returns.
+__global__ void k_wait_selftest(int* err, long long polls) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    eqk::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !eqk::mbar_wait(&bar, 0u, polls)) atomicOr(err, 1);
+}
+
 // ---- non-periodic specimens in a zero-stress buffer (Sec. 5.2) ---------------------------------
 
 constexpr int PAD_GRID = 1216;  // blocks per field of the crop pass (8 x 152 SMs)
@@ -1181,6 +1194,22 @@ eq_status eq_norms(eq_plan* p, eq_norms_t* host_out) {
     return fail(EQ_ERR_TIMEOUT, "eq_norms: a bounded wait inside a kernel ran out; results are invalid");
   }
   std::memcpy(host_out, p->hnorms, sizeof(eq_norms_t) * p->batch);
+  return EQ_OK;
+}
+
+eq_status eq_selftest_wait_timeout(eq_plan* p, long long polls, void* stream) {
+  if (!p || polls < 1 || polls > (1LL << 24))
+    return fail(EQ_ERR_INVALID, "eq_selftest_wait_timeout: NULL plan or polls outside 1..2^24");
+  if (!p->err)
+    return fail(EQ_ERR_INVALID, "eq_selftest_wait_timeout: this plan's kernels have no bounded waits");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_wait_selftest<<<1, 32, 0, s>>>(p->err, polls);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(e, "eq_selftest_wait_timeout: launch");
+  eq_status st = publish(p, s);
+  if (st != EQ_OK) return st;
+  if ((e = cudaEventRecord(p->done, s)) != cudaSuccess) return fail_cuda(e, "event record");
+  p->have_result = true;
   return EQ_OK;
 }
 

@@ -26,10 +26,11 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
-// true once the phase with the given parity has completed; false after TMA_WAIT_LIMIT polls
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// true once the phase with the given parity has completed; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          long long limit = TMA_WAIT_LIMIT) {
   const unsigned a = smem_u32(bar);
-  for (long long i = 0; i < TMA_WAIT_LIMIT; ++i) {
+  for (long long i = 0; i < limit; ++i) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"

@@ -127,3 +127,9 @@ def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
     assert lib.eq_project_padded(None, 8, 8, 8, None, None, None) == EQ_ERR_INVALID
     assert lib.eq_project_host_async(None, None, None, None) == EQ_ERR_INVALID
     assert b"NULL" in lib.eq_last_error()
+
+
+def test_wait_selftest_rejects_bad_arguments_without_a_gpu(lib):
+    from paper_2105_01612_gb300._lib import EQ_ERR_INVALID
+    assert lib.eq_selftest_wait_timeout(None, 1024, None) == EQ_ERR_INVALID
+    assert b"NULL plan" in lib.eq_last_error()
