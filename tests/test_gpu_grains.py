@@ -25,10 +25,18 @@ def _map(shape, n, seed, empty=None):
     return g
 
 
+def _scattered_map(shape, n, seed, empty):
+    # an independent id per voxel: no spatial coherence at all (Voronoi grains are compact)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = rng.integers(0, n, size=shape).astype(np.int32)
+    return np.where(g == empty, (empty + 1) % n, g)
+
+
+@pytest.mark.parametrize("kind", ["voronoi", "scattered"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_means_and_field_match_the_oracle_batch_of_two(dtype):
+def test_means_and_field_match_the_oracle_batch_of_two(dtype, kind):
     shape = (24, 20, 28)
-    gmap = _map(shape, 40, 12, empty=7)
+    gmap = _map(shape, 40, 12, empty=7) if kind == "voronoi" else _scattered_map(shape, 40, 12, 7)
     s = np.stack([voronoi_stress_field(shape, 30, 100.0, 10.0, 31 + f).numpy() for f in range(2)])
     gr = eq.Grains(gmap, 41)                       # ids 7 and 40 have no voxel
     x = torch.as_tensor(s).to(dtype).cuda().contiguous()
