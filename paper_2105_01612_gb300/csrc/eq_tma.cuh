@@ -431,8 +431,12 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
       abort_flag = 1;
     }
     if (s) ++ph1; else ++ph0;
-    // the last tile's TMA stores must have read the exchange buffer before it is rewritten
-    if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    // first pass with tiled stores: the tile's output leaves from its own load stage (free once
+    // the exchange is written), so no later tile waits for the stores before its exchange; the
+    // stage is refilled one tile later, once those stores have read it.  Otherwise the stores
+    // leave from the exchange buffer, which the last tile's stores must have read by now.
+    const bool OS = MODE == 1 && a.tma_store;
+    if (tid == 0 && !OS) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     __syncthreads();                                 // stage s ready; the last tile fully done
     if (abort_flag) break;
     T2 v[16];
@@ -487,9 +491,15 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) xc[k1 * 32 + (t ^ (2 * k1))] = v[k1];
     __syncthreads();                                 // exchange written; stage s fully read
-    if (tid == 0 && !(EARLY && a.ref) && u + 2 * step < ntiles) {
+    if (tid == 0 && !OS && !(EARLY && a.ref) && u + 2 * step < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(u + 2 * step, s, &map);
+    }
+    // stage s ^ 1 takes tile u + step once the last tile's stores have read it
+    if (tid == 0 && OS && k >= 1 && u + step < ntiles) {
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(u + step, s ^ 1, &map);
     }
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = xc[kap * 32 + h + 2 * (m ^ kap)];
@@ -517,10 +527,11 @@ k_strided16(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUt
         out_re[a.V + off] = v[q].y;
       }
     } else {
-      // the tile in box layout ([point][column], re plane then im plane) into the exchange
-      // buffer (every read of it is behind the barrier below), then out by tiled stores
-      __syncthreads();
-      T* ore = reinterpret_cast<T*>(xbuf);
+      // the tile in box layout ([point][column], re plane then im plane) into the tile's load
+      // stage (first pass) or the exchange buffer (every read of it is behind the barrier
+      // below), then out by tiled stores
+      if (!OS) __syncthreads();
+      T* ore = OS ? stage0 + s * 2 * N * B : reinterpret_cast<T*>(xbuf);
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int pnt = (kap + 16 * q + 256 * h) * B + b;
