@@ -224,6 +224,20 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def job_timing(ms_local: float, voxels_per_rank: int, steps: int, world: int, device=None):
+    """The whole job's timed region and throughput.  Every rank projects its own field (replicas,
+    no data exchanged), so the job takes the slowest rank's time (a MAX all-reduce over the
+    default process group) and processes world x voxels x steps voxels in it."""
+    ms_total = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    return ms_total, world * voxels_per_rank * steps / (ms_total / 1e3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -270,15 +284,10 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total, value = job_timing(e0.elapsed_time(e1), vox, args.steps, world, dev)
     per_pass, ncalls = plan.pass_ms()
     nrm = plan.norms()[0]
     ms_step = ms_total / args.steps
-    value = world * vox * args.steps / (ms_total / 1e3)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
     peak, peak_kind = measured_peaks()
