@@ -206,8 +206,9 @@ eq_status eq_plan_pass_ms(eq_plan* plan, double* ms_out, int* ncalls_out);
  * EQ_STATIC_SCRATCH_BYTES array in device memory that the library declares; every GPU that loads
  * the library holds it until the process exits.  The call makes no cudaMalloc/cudaFree and calls
  * no allocating library routine; it enqueues work on cuda_stream and returns.  The first call on
- * each device (with that device current) looks up the array's device address; make that first
- * call before any stream capture.  All calls share the array: calls whose work overlaps on the
+ * each device (with that device current) looks up the array's device address and remembers the
+ * context it belongs to; a call that finds another context current (after cudaDeviceReset, for
+ * one) looks it up again.  Make those first calls before any stream capture.  All calls share the array: calls whose work overlaps on the
  * GPU race on it, so order them (one stream, or synchronise).  Grids whose scratch would not fit
  * are rejected with EQ_ERR_INVALID.  Results equal eq_project's for the same field. */
 #define EQ_STATIC_SCRATCH_BYTES (1u << 20)

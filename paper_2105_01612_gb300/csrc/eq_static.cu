@@ -10,8 +10,11 @@
 // The scratch array is a file-scope __device__ variable of EQ_STATIC_SCRATCH_BYTES bytes.  Every
 // GPU that loads the library holds it until the process exits.  Host code cannot use the array's
 // name as a device address (it is a host-side shadow), so on the first call on each device, with
-// that device current, the address is looked up once with cudaGetSymbolAddress and cached.  That
-// first call should come before any stream capture.  All calls share the array and it keeps the
+// that device current, the address is looked up with cudaGetSymbolAddress and cached together with
+// the identity of the CUDA context it belongs to.  A later call that finds another context current
+// (after cudaDeviceReset, or another driver context made current) looks the address up again, so
+// a stale address is never used.  That first call (and the first one after a context change)
+// should come before any stream capture.  All calls share the array and it keeps the
 // last call's contents: every call writes all the tables and reduction partials it later reads
 // (no part of it has to start at zero).  Calls whose work overlaps on the GPU (different streams,
 // or several host threads without ordering) race on the array; order them.
@@ -26,7 +29,34 @@ static __device__ __align__(256) unsigned char eq_static_scratch[EQ_STATIC_SCRAT
 namespace {
 
 std::mutex g_static_mu;
-void* g_static_ptr[64] = {nullptr};
+// per device: the context the cached address belongs to (its process-unique id) and the address
+struct StaticSlot {
+  unsigned long long ctx_id = 0;
+  void* ptr = nullptr;
+};
+StaticSlot g_static_slot[64];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+template <typename F> F driver_fn(const char* name) {
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return reinterpret_cast<F>(f);
+}
+
+// Process-unique id of the calling thread's current context (0 when none is current yet).
+unsigned long long current_ctx_id() {
+  static const CtxGetCurrentFn get = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+  static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (!get || !get_id || get(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 eq_status sfail(eq_status st, const std::string& m) {
   eqk::set_last_error(m);
@@ -101,18 +131,22 @@ extern "C" eq_status eq_project_static(int nx, int ny, int nz, const eq_plan_opt
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess || dev < 0 || dev >= 64)
     return sfail(EQ_ERR_CUDA, "eq_project_static: no current device");
-  // set-up once per device, with that device current: the scratch array's device address
+  // set-up once per device and context, with that device current: the scratch array's device
+  // address (looked up again when the current context is not the one it was taken in)
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    StaticSlot& slot = g_static_slot[dev];
+    const unsigned long long ctx = current_ctx_id();
+    if (!slot.ptr || ctx == 0 || ctx != slot.ctx_id) {
       void* ptr = nullptr;
       if ((e = cudaGetSymbolAddress(&ptr, eq_static_scratch)) != cudaSuccess)
         return sfail(EQ_ERR_CUDA, std::string("eq_project_static: cudaGetSymbolAddress: ") +
                                       cudaGetErrorString(e));
-      g_static_ptr[dev] = ptr;
+      slot.ptr = ptr;
+      slot.ctx_id = current_ctx_id();   // the lookup made the device's context current
     }
-    scratch = g_static_ptr[dev];
+    scratch = slot.ptr;
   }
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return sfail(EQ_ERR_CUDA, "eq_project_static: device attribute");
@@ -179,6 +213,9 @@ extern "C" eq_status eq_project_static(int nx, int ny, int nz, const eq_plan_opt
   if ((e = eqk::launch_strided_f32(nz, false, a, dim3(g1, 3), s)) != cudaSuccess)
     return sfail(EQ_ERR_CUDA, std::string("eq_project_static: z forward: ") + cudaGetErrorString(e));
   eqk::finalize_mean(part1, g1, 1, double(V), mean, instats, s);
+  if ((e = cudaGetLastError()) != cudaSuccess)
+    return sfail(EQ_ERR_CUDA, std::string("eq_project_static: mean finalisation: ") +
+                                  cudaGetErrorString(e));
   eqk::StridedArgs ay{};
   ay.field_stride = 6 * V; ay.V = V; ay.in = d_out; ay.out = d_out; ay.tw = twy;
   ay.nstride = nx; ay.inner = nx; ay.outer_stride = (long long)nx * ny; ay.ncols = (long long)nz * nx;
