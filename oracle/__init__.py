@@ -19,8 +19,8 @@ real-space central differences, closed forms, invariants, an independent library
 from .transforms import dft_axis_direct, dft3_direct, dft3_naive, fft3, ifft3
 from .operators import (wavevector, wavevector_grids, biharmonic_symbol_paper,
                         central_diff, stencil25_apply)
-from .projection import (project, project_literal, project_spectrum, divergence,
-                         divergence_central_diff, norms, inner, frob2)
+from .projection import (project, project_large, project_literal, project_spectrum, divergence,
+                         divergence_central_diff, norms, norms_large, inner, frob2)
 from .fields import beltrami_field, symgrad_field, smooth_potential, inc_central_diff
 from .brute import project_bruteforce
 from .hodge import project_compat, hodge_potential
@@ -30,7 +30,8 @@ from .padding import project_padded
 __all__ = [
     "dft_axis_direct", "dft3_direct", "dft3_naive", "fft3", "ifft3",
     "wavevector", "wavevector_grids", "biharmonic_symbol_paper", "central_diff",
-    "stencil25_apply", "project", "project_literal", "project_spectrum", "divergence",
+    "stencil25_apply", "project", "project_large", "norms_large", "project_literal",
+    "project_spectrum", "divergence",
     "divergence_central_diff", "norms", "inner", "frob2", "beltrami_field", "symgrad_field",
     "smooth_potential", "inc_central_diff", "project_bruteforce", "project_compat",
     "hodge_potential", "grain_means", "grain_average", "project_padded",

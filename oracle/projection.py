@@ -15,6 +15,9 @@ Readings where the paper is silent (each listed in the design notes):
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 from .operators import wavevector_grids, biharmonic_symbol_paper, central_diff
@@ -74,15 +77,23 @@ def _xi_full(shape, h, op):
     return [np.broadcast_to(a, shape) for a in xi]
 
 
-def project_spectrum(shat6: np.ndarray, h, op: str, nyq: str = "keep") -> np.ndarray:
+def project_spectrum(shat6: np.ndarray, h, op: str, nyq: str = "keep", grid=None,
+                     z0: int = 0) -> np.ndarray:
     """Apply the per-mode projector to a Voigt spectrum ``(6, nz, ny, nx)`` (complex).
 
     At every mode with Xi != 0: S_hat <- Q S_hat Q, Q = I - n n^T, n = Xi / |Xi| (the orthogonal
     projection, under A:B, onto matrices with S_hat n = 0).  Xi = 0: identity at k = 0; at k != 0
     identity (``keep``) or zero (``zero``).
+
+    ``grid``/``z0``: ``shat6`` is the slab of z indices z0, z0 + 1, ... of the spectrum of a grid
+    ``(nz, ny, nx)`` (default: the whole spectrum); each mode gets the Xi of its own index.
     """
     shape = shat6.shape[1:]
-    xi = _xi_full(shape, h, op)
+    if grid is None:
+        xi = _xi_full(shape, h, op)
+    else:
+        xi_x, xi_y, xi_z = wavevector_grids(tuple(grid), h, op)
+        xi = [np.broadcast_to(a, shape) for a in (xi_x, xi_y, xi_z[z0:z0 + shape[0]])]
     k2 = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
     degenerate = k2 == 0.0
     inv = np.where(degenerate, 0.0, 1.0 / np.sqrt(np.where(degenerate, 1.0, k2)))
@@ -94,7 +105,8 @@ def project_spectrum(shat6: np.ndarray, h, op: str, nyq: str = "keep") -> np.nda
         out = np.where(degenerate[None, None], t, out)
     elif nyq == "zero":
         out = np.where(degenerate[None, None], 0.0, out)
-        out[:, :, 0, 0, 0] = t[:, :, 0, 0, 0]
+        if z0 == 0:
+            out[:, :, 0, 0, 0] = t[:, :, 0, 0, 0]
     else:
         raise ValueError(nyq)
     return to_voigt(out)
@@ -115,6 +127,36 @@ def project(s6: np.ndarray, op: str = "ddo", h=(1.0, 1.0, 1.0), nyq: str = "keep
     shat = _forward(st, transform)
     out = project_spectrum(shat, h, op, nyq)
     return np.real(_inverse(out, transform)) + c0[:, None, None, None]
+
+
+def project_large(s6: np.ndarray, op: str = "ddo", h=(1.0, 1.0, 1.0), nyq: str = "keep",
+                  slab: int = 2) -> np.ndarray:
+    """``project`` for grids whose whole (3, 3)-tensor spectrum does not fit in host memory
+    (512^3: about 20 GB for one complex tensor array, several of them alive at once).
+
+    The same four steps of Sec. 3.2-3.3 with the same arithmetic per mode: the mean and the
+    transforms run one Voigt component at a time, and ``project_spectrum`` runs on z-slabs of
+    ``slab`` planes of the spectrum, each with the Xi of its own modes.  Only the grouping of modes
+    into arrays differs from ``project`` (the per-mode projector has no coupling between modes).
+    ``s6`` may be float32; it is read one component at a time in float64.
+    """
+    nz, ny, nx = s6.shape[1:]
+    c0 = np.array([np.asarray(s6[c], dtype=np.float64).mean() for c in range(6)])
+    shat = np.empty((6, nz, ny, nx), dtype=np.complex128)
+    for c in range(6):
+        shat[c] = fft3(np.asarray(s6[c], dtype=np.float64) - c0[c])
+
+    def one_slab(z0):
+        z1 = min(nz, z0 + slab)
+        shat[:, z0:z1] = project_spectrum(shat[:, z0:z1], h, op, nyq, grid=(nz, ny, nx), z0=z0)
+
+    # slabs are independent (disjoint modes), so they may run on the host cores side by side
+    with ThreadPoolExecutor(max_workers=max(1, os.cpu_count() or 1)) as ex:
+        list(ex.map(one_slab, range(0, nz, slab)))
+    out = np.empty((6, nz, ny, nx), dtype=np.float64)
+    for c in range(6):
+        out[c] = np.real(ifft3(shat[c])) + c0[c]
+    return out
 
 
 _EPS = np.zeros((3, 3, 3))
@@ -193,4 +235,52 @@ def norms(s_in: np.ndarray, s_out: np.ndarray, op: str = "ddo", h=(1.0, 1.0, 1.0
         "resid_linf": float(np.abs(resid).max()),
         "div_in_l2": float(np.sqrt((d_in ** 2).sum(axis=0).mean())),
         "div_out_l2": float(np.sqrt((d_out ** 2).sum(axis=0).mean())),
+    }
+
+
+def _div2_sum(s6: np.ndarray, op: str, h) -> float:
+    """Sum over voxels of |div S|^2 with the operator of ``divergence``, one row
+    (div S)_i = sum_j d_j S_ij at a time, each S_ij transformed on its own."""
+    shape = s6.shape[1:]
+    xi = _xi_full(shape, h, op)
+    total = 0.0
+    for i in range(3):
+        dhat = np.zeros(shape, dtype=np.complex128)
+        for j in range(3):
+            c = VOIGT_IJ.index((min(i, j), max(i, j)))
+            dhat += 1j * xi[j] * fft3(np.asarray(s6[c], dtype=np.float64))
+        d = np.real(ifft3(dhat))
+        total += float((d * d).sum())
+    return total
+
+
+def norms_large(s_in: np.ndarray, s_out: np.ndarray, op: str = "ddo", h=(1.0, 1.0, 1.0),
+                div_out: bool = True) -> dict:
+    """``norms`` for grids too large for whole-field tensor arrays: the same definitions,
+    evaluated one Voigt component (real-space terms) or one row of the divergence at a time.
+    ``div_out=False`` leaves the output divergence out (reported as NaN)."""
+    nv = float(np.prod(s_in.shape[1:]))
+    mean = np.empty(6)
+    a2 = b2 = r2 = 0.0
+    linf = 0.0
+    for c in range(6):
+        a = np.asarray(s_in[c], dtype=np.float64)
+        b = np.asarray(s_out[c], dtype=np.float64)
+        r = a - b
+        mean[c] = a.mean()
+        a2 += VOIGT_W[c] * float((a * a).sum())
+        b2 += VOIGT_W[c] * float((b * b).sum())
+        r2 += VOIGT_W[c] * float((r * r).sum())
+        linf = max(linf, float(np.abs(r).max()))
+    norm_in = float(np.sqrt(a2 / nv))
+    resid = float(np.sqrt(r2 / nv))
+    return {
+        "mean": mean,
+        "norm_in": norm_in,
+        "norm_out": float(np.sqrt(b2 / nv)),
+        "resid_l2": resid,
+        "resid_rel": resid / norm_in if norm_in > 0 else 0.0,
+        "resid_linf": linf,
+        "div_in_l2": float(np.sqrt(_div2_sum(s_in, op, h) / nv)),
+        "div_out_l2": float(np.sqrt(_div2_sum(s_out, op, h) / nv)) if div_out else float("nan"),
     }

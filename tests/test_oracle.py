@@ -312,3 +312,23 @@ def test_voronoi_map_is_periodic_nearest_seed():
                 dist = np.sqrt((d ** 2).sum(1))
                 best = np.flatnonzero(dist <= dist.min() * (1 + 1e-6))
                 assert gm[z, y, x] in best
+
+
+@pytest.mark.parametrize("slab", [1, 3, 7])
+def test_large_grid_projection_and_norms_equal_the_whole_field_ones(slab):
+    """project_large / norms_large (component-at-a-time transforms, projector on z-slabs) give the
+    pinned whole-field project / norms: the same per-mode arithmetic, grouped differently."""
+    s = voronoi_stress_field((10, 12, 8), 5, 100.0, 10.0, 31).numpy()
+    for op in ("ddo", "cdo"):
+        for nyq in ("keep", "zero"):
+            h = (1.0, 0.7, 1.2)
+            a = oracle.project(s, op, h, nyq)
+            b = oracle.project_large(s.astype(np.float32), op, h, nyq, slab=slab)
+            a32 = oracle.project(s.astype(np.float32).astype(np.float64), op, h, nyq)
+            assert np.abs(b - a32).max() <= 1e-13 * np.abs(a32).max(), (op, nyq)
+            assert np.abs(oracle.project_large(s, op, h, nyq, slab=slab) - a).max() <= \
+                1e-13 * np.abs(a).max()
+            n1 = oracle.norms(s, a, op, h)
+            n2 = oracle.norms_large(s, a, op, h)
+            for k in n1:
+                assert np.allclose(n2[k], n1[k], rtol=1e-12, atol=1e-14 * n1["norm_in"]), (k, op)
