@@ -155,46 +155,203 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------ GPU legs
 
-def cufft_baseline(x, steps: int):
-    """Comparison only: torch.fft (cuFFT) r2c/c2r + the projector in torch elementwise ops."""
+# algorithmic flops per voxel of the projection: 3-D complex FFTs of the three complex fields
+# (pairs of Voigt planes) counted as 5 M log2 M per complex transform of M = nx ny nz points,
+# forward and inverse (2 x 3 x 5 x log2 M per voxel; 810 at 512^3), plus about 70 for the per-mode
+# projector and its norm terms
+def flops_per_voxel(vox: int) -> float:
+    return 2 * 3 * 5 * math.log2(vox) + 70.0
+
+
+def fma_peak(dev, dtype_code: int, iters: int, reps: int = 3):
+    """Measured FMA throughput (TFLOP/s) of this GPU: every thread of 8 blocks of 256 threads per
+    SM runs 8 independent FMA chains (eqm_fma_probe); best of `reps` CUDA-event-timed launches."""
     import torch
-    n = x.shape[-1]
-    dev = x.device
-    m = torch.arange(n, device=dev, dtype=torch.float64)
-    s = torch.where(m < n / 2, m, m - n)
-    xi = torch.sin(2 * math.pi * s / n)
-    xi[n // 2] = 0.0
-    xi = xi.float()
-    xz, xy, xx = xi.view(n, 1, 1), xi.view(1, n, 1), xi[: n // 2 + 1].view(1, 1, n // 2 + 1)
-    k2 = xx * xx + xy * xy + xz * xz
-    inv = torch.where(k2 > 0, torch.rsqrt(torch.where(k2 > 0, k2, torch.ones_like(k2))),
-                      torch.zeros_like(k2))
-    n0, n1, n2 = xx * inv, xy * inv, xz * inv
+    from paper_2105_01612_gb300 import _measure
+    props = torch.cuda.get_device_properties(dev)
+    blocks, threads = props.multi_processor_count * 8, 256
+    buf = torch.empty(blocks * threads, dtype=torch.float64 if dtype_code else torch.float32,
+                      device=dev)
+    st = torch.cuda.current_stream(dev)
+    _measure.fma_probe(dtype_code, buf.data_ptr(), blocks, threads, max(1, iters // 10),
+                       st.cuda_stream)
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _measure.fma_probe(dtype_code, buf.data_ptr(), blocks, threads, iters, st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    flops = 16.0 * iters * blocks * threads
+    return flops / (best / 1e3) / 1e12, best
 
-    def step():
-        sh = torch.fft.rfftn(x, dim=(-3, -2, -1))
-        a = sh  # (6, nz, ny, nx/2+1) Voigt xx, yy, zz, yz, xz, xy
-        v0 = a[0] * n0 + a[5] * n1 + a[4] * n2
-        v1 = a[5] * n0 + a[1] * n1 + a[3] * n2
-        v2 = a[4] * n0 + a[3] * n1 + a[2] * n2
-        sc = n0 * v0 + n1 * v1 + n2 * v2
-        o = torch.stack([a[0] - 2 * n0 * v0 + sc * n0 * n0, a[1] - 2 * n1 * v1 + sc * n1 * n1,
-                         a[2] - 2 * n2 * v2 + sc * n2 * n2, a[3] - n1 * v2 - v1 * n2 + sc * n1 * n2,
-                         a[4] - n0 * v2 - v0 * n2 + sc * n0 * n2, a[5] - n0 * v1 - v0 * n1 + sc * n0 * n1])
-        o[:, 0, 0, 0] = a[:, 0, 0, 0]
-        return torch.fft.irfftn(o, s=x.shape[-3:], dim=(-3, -2, -1))
 
-    for _ in range(2):
-        y = step()
+def gpu_numa_node(dev):
+    """NUMA node of the GPU's PCI function as the kernel reports it (None if unknown)."""
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    bdf = "%04x:%02x:%02x.0" % (getattr(p, "pci_domain_id", 0), getattr(p, "pci_bus_id", 0),
+                                getattr(p, "pci_device_id", 0))
+    try:
+        with open(f"/sys/bus/pci/devices/{bdf}/numa_node") as f:
+            return bdf, int(f.read().strip())
+    except (OSError, ValueError):
+        return bdf, None
+
+
+def link_leg(hin, hout, dev, reps: int = 3):
+    """Host link bandwidth measured in the same run with the e2e leg's own pinned buffers: one
+    field's bytes host-to-device, device-to-host, and both directions at once (two streams);
+    best of `reps`, CUDA events.  both_ms_per_field is the copy floor of an end-to-end step."""
+    import torch
+    nbytes = hin.numel() * hin.element_size()
+    da, db = torch.empty(hin.shape, dtype=hin.dtype, device=dev), torch.empty(hin.shape, dtype=hin.dtype, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def timed(fn):
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s1)
+            fn()
+            e1.record(s1)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            da.copy_(hin, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s1):
+            hout.copy_(db, non_blocking=True)
+
+    def both():
+        ev = torch.cuda.Event()
+        ev.record(s1)
+        s2.wait_event(ev)
+        with torch.cuda.stream(s1):
+            da.copy_(hin, non_blocking=True)
+        with torch.cuda.stream(s2):
+            hout.copy_(db, non_blocking=True)
+        ev2 = torch.cuda.Event()
+        ev2.record(s2)
+        s1.wait_event(ev2)
+
+    t_in, t_out, t_both = timed(h2d), timed(d2h), timed(both)
+    bdf, node = gpu_numa_node(dev)
+    del da, db
+    return {"bytes_per_direction": nbytes, "h2d_gbs": nbytes / (t_in / 1e3) / 1e9,
+            "d2h_gbs": nbytes / (t_out / 1e3) / 1e9,
+            "both_gbs_total": 2 * nbytes / (t_both / 1e3) / 1e9,
+            "both_ms_per_field": t_both, "gpu_pci": bdf, "gpu_numa_node": node,
+            "method": "torch copies between the e2e leg's pinned host buffers and device "
+                      "tensors, best of 3, CUDA events"}
+
+
+def fp64_leg(x, out, n, dev, stream):
+    """The FP64 path on the same field: time per projection, its FP32-vs-FP64 difference, and
+    its arithmetic rate against the DFMA rate measured here (FP64 on GB300 is bound by its FP64
+    units, not by HBM)."""
+    import torch
+    import paper_2105_01612_gb300 as eq
+    x64 = x.double()
+    o64 = torch.empty_like(x64)
+    p64 = eq.Plan(n, n, n, torch.float64, 1, "ddo", device=dev)
+    p64.project(x64, o64)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        y = step()
-    e1.record()
+    k64 = 3
+    clk = ClockSampler(str(getattr(torch.cuda.get_device_properties(dev), "uuid", "")))
+    clk.start()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(k64):
+        p64.project(x64, o64)
+    f1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    return y, ms
+    ms64 = f0.elapsed_time(f1) / k64
+    p64.set_timing(1)
+    p64.project(x64, o64)
+    per_pass, _ = p64.pass_ms()
+    peak, probe_ms = fma_peak(dev, 1, 100000)
+    clocks = clk.stop()
+    p64.close()
+    vox = x.numel() // 6
+    w = torch.tensor([1.0, 1, 1, 2, 2, 2], device=dev, dtype=torch.float64).view(1, 6, 1, 1, 1)
+    d = out.double() - o64
+    fp32_err = math.sqrt(float((w * d * d).sum() / (w * o64 * o64).sum()))
+    del d, x64
+    achieved = flops_per_voxel(vox) * vox / (ms64 / 1e3) / 1e12
+    return {"value": vox / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+            "fp32_vs_fp64_rel_l2": fp32_err, "pass_ms": per_pass,
+            "roofline": {"bound": "fp64_alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "flops_per_voxel": flops_per_voxel(vox),
+                         "peak_kind": f"measured here: FP64 FMA probe (8 chains per thread, "
+                                      f"{probe_ms:.1f} ms launch)"},
+            "clocks": clocks}, o64
+
+
+def cufft_leg(x, out, o64, dev, stream, steps: int):
+    """Comparison baseline on the same GPU: torch.fft (cuFFT) r2c / c2r around one hand-written
+    projector kernel over the half spectrum (eqm_project_half, the same per-mode Q S Q), FP32
+    and FP64; and the two transforms alone, the floor of any cuFFT-based projection."""
+    import torch
+    from paper_2105_01612_gb300 import _measure
+    nz, ny, nx = x.shape[-3:]
+    res = {"method": "torch.fft.rfftn over (z, y, x) of the six planes, eqm_project_half in "
+                     "place on the half spectrum, torch.fft.irfftn; norms not computed"}
+    w = torch.tensor([1.0, 1, 1, 2, 2, 2], device=dev, dtype=torch.float64).view(6, 1, 1, 1)
+    for name, dt, code, ref in (("f32", torch.float32, 0, out[0]), ("f64", torch.float64, 1, o64[0])):
+        xs = x[0].to(dt)
+
+        def xi(m):
+            k = torch.arange(m, dtype=torch.float64)
+            sgn = torch.where(k < m / 2, k, k - m)
+            v = torch.sin(2 * math.pi * sgn / m)
+            if m % 2 == 0:
+                v[m // 2] = 0.0
+            return v.to(dt).to(dev)
+        xx, xy, xz = xi(nx)[: nx // 2 + 1].contiguous(), xi(ny), xi(nz)
+
+        def both():
+            sh = torch.fft.rfftn(xs, dim=(-3, -2, -1))
+            _measure.project_half(code, sh.data_ptr(), nz, ny, nx // 2 + 1, xx.data_ptr(),
+                                  xy.data_ptr(), xz.data_ptr(), stream.cuda_stream)
+            return torch.fft.irfftn(sh, s=(nz, ny, nx), dim=(-3, -2, -1))
+
+        def transforms():
+            return torch.fft.irfftn(torch.fft.rfftn(xs, dim=(-3, -2, -1)), s=(nz, ny, nx),
+                                    dim=(-3, -2, -1))
+
+        times = {}
+        for key, fn in (("cufft_plus_kernel_ms", both), ("cufft_only_ms", transforms)):
+            for _ in range(2):
+                y = fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                y = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times[key] = e0.elapsed_time(e1) / steps
+            if key == "cufft_plus_kernel_ms":
+                dd = y.double() - ref.double()
+                times["rel_l2_vs_ours"] = math.sqrt(float((w * dd * dd).sum() /
+                                                          (w * ref.double() ** 2).sum()))
+                del dd
+            del y
+        torch.cuda.empty_cache()
+        res[name] = times
+    vox = nx * ny * nz
+    res["value"] = vox / (res["f32"]["cufft_plus_kernel_ms"] / 1e3)
+    res["unit"] = UNIT
+    res["ms_per_step"] = res["f32"]["cufft_plus_kernel_ms"]
+    return res
 
 
 def kernel_traffic(dominant: str):
@@ -267,7 +424,6 @@ def run_ours(args):
     for _ in range(max(3, args.warmup)):
         plan.project(x, out)
     torch.cuda.synchronize()
-    plan.set_timing(args.steps)
     props = torch.cuda.get_device_properties(dev)
     clk = ClockSampler(str(getattr(props, "uuid", "")))
     clk.start()
@@ -283,7 +439,18 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    # per-pass device times: the same projections again, launched pass by pass with events
+    # between the passes (the timed region above replays the plan's CUDA graph, the default path)
+    kp = max(3, min(args.steps, 20))
+    plan.set_timing(kp)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(kp):
+        plan.project(x, out)
+    p1.record(stream)
+    torch.cuda.synchronize()
     clocks = clk.stop()
+    ms_passes_step = p0.elapsed_time(p1) / kp
     ms_total, value = job_timing(e0.elapsed_time(e1), vox, args.steps, world, dev)
     per_pass, ncalls = plan.pass_ms()
     nrm = plan.norms()[0]
@@ -311,8 +478,13 @@ def run_ours(args):
                      "traffic": traffic,
                      "algorithmic_bytes_per_launch": dom_bytes},
         "pipeline": {"pass_ms": {k: v / max(1, ncalls) for k, v in per_pass.items()},
+                     "pass_timing": f"{ncalls} further projections launched pass by pass with "
+                                    f"events between passes, right after the timed region "
+                                    f"(graph replay there): {ms_passes_step:.3f} ms per step",
                      "algorithmic_frac": BYTES_PER_VOXEL_PASS * vox / (ms_step / 1e3) / 1e9 / peak,
                      "five_pass_frac": 5 * BYTES_PER_VOXEL_PASS * vox / (ms_step / 1e3) / 1e9 / peak},
+        "timing": "CUDA events on the launch stream around K replays of the plan's captured "
+                  "CUDA graph (the default eq_project path)",
         "gpu_launches": 8 * args.steps,
         "clocks": clocks,
         "norms": {k: nrm[k] for k in ("norm_in", "norm_out", "resid_rel", "div_in_l2", "div_out_l2")},
@@ -362,36 +534,17 @@ def run_ours(args):
                                          "method": "eq_project_host (waits for each field)"}}
         for q in plans:
             q.close()
+        link = link_leg(hin, houts[0], dev)
+        link["e2e_frac_of_link_bound"] = link["both_ms_per_field"] / (te * 1e3)
+        line["e2e"]["host_link"] = link
         del hin, houts
-        # the FP64 path on the same field
-        x64 = x.double()
-        o64 = torch.empty_like(x64)
-        p64 = eq.Plan(n, n, n, torch.float64, 1, "ddo", device=dev)
-        p64.project(x64, o64)
-        torch.cuda.synchronize()
-        k64 = max(1, min(args.steps, 3))
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(k64):
-            p64.project(x64, o64)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1) / k64
-        w = torch.tensor([1.0, 1, 1, 2, 2, 2], device=dev, dtype=torch.float64).view(1, 6, 1, 1, 1)
-        d = out.double() - o64
-        fp32_err = math.sqrt(float((w * d * d).sum() / (w * o64 * o64).sum()))
-        del d
-        line["fp64"] = {"value": vox / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
-                        "fp32_vs_fp64_rel_l2": fp32_err}
-        p64.close()
-        del x64, o64
-        # cuFFT + elementwise projector (comparison baseline, library kernels)
-        y, msc = cufft_baseline(x[0], max(1, min(args.steps, 5)))
-        dd = (y.double() - out[0].double())
-        agree = math.sqrt(float((w[0] * dd * dd).sum() / (w[0] * out[0].double() ** 2).sum()))
-        line["cufft_baseline"] = {"value": vox / (msc / 1e3), "unit": UNIT, "ms_per_step": msc,
-                                  "rel_l2_vs_ours": agree}
-        del y, dd
+        # the FP64 path on the same field, against the FP64 FMA rate measured here
+        fp64, o64 = fp64_leg(x, out, n, dev, stream)
+        line["fp64"] = fp64
+        # cuFFT (r2c / c2r) with and without one hand-written projector kernel, FP32 and FP64
+        line["cufft_baseline"] = cufft_leg(x, out, o64, dev, stream, max(1, min(args.steps, 5)))
+        del o64
+        torch.cuda.empty_cache()
         if not args.grid:
             line["grain_average"] = grain_leg(x, out, plan, n, dev, stream, peak)
         line["cpu_baseline"] = cpu_base
@@ -469,6 +622,12 @@ def batch_leg(dev, steps: int):
                                                  device=dev).reshape(-1)
         off += n
     out = torch.empty_like(flat)
+    # radix / tile choices per pass: the plan's autotuner (cached in $EQ_TUNE_CACHE, a file of
+    # the run's temporary directory unless the caller names one)
+    os.environ.setdefault("EQ_TUNE_CACHE", os.path.join("/tmp", f"eq_tune_{os.getpid()}.txt"))
+    t0 = time.perf_counter()
+    plan.autotune(flat, out)
+    tune_s = time.perf_counter() - t0
     for _ in range(3):
         plan.project(flat, out)
     torch.cuda.synchronize()
@@ -489,7 +648,9 @@ def batch_leg(dev, steps: int):
     return {"workload": "64 fields, axes uniform 64..256, 50..2000 Voronoi grains, FP32, DDO; "
                         "one launch per pass over all fields, CUDA graph replay",
             "voxels": vox, "value": vox / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-            "steps": steps, "pass_ms": per_pass,
+            "steps": steps, "pass_ms": per_pass, "autotune_s": tune_s,
+            "pass_frac": {k: BYTES_PER_VOXEL_PASS * vox / (v / 1e3) / 1e9 / peak
+                          for k, v in per_pass.items() if "finalise" not in k and v > 0},
             "algorithmic_frac": BYTES_PER_VOXEL_PASS * vox / (ms / 1e3) / 1e9 / peak}
 
 

@@ -1,4 +1,5 @@
-"""Build libeq.so from csrc/ with nvcc for sm_103a (in-tree, parallel per translation unit)."""
+"""Build libeq.so from csrc/ with nvcc for sm_103a (in-tree, parallel per translation unit), and
+the benchmark's measurement kernels into libeqm.so."""
 from __future__ import annotations
 
 import os
@@ -11,6 +12,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeq.so")
+# measurement kernels of the benchmark (throughput probes, the cuFFT baseline's projector): a
+# library of their own, not on the projection path
+MEASURE_SRC = os.path.join(CSRC, "measure", "eqm.cu")
+MEASURE_LIB = os.path.join(HERE, "libeqm.so")
 
 SOURCES = ["eq_f32.cu", "eq_f64.cu", "eq_gen_f32.cu", "eq_gen_f64.cu", "eq_gen_host.cu", "eq_api.cu", "eq_serve.cu", "eq_static.cu",
            "eq_grains.cu"]
@@ -38,6 +43,10 @@ def build(verbose: bool = False, force: bool = False) -> str:
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(INCLUDE, "eq.h"))
     procs, objs = [], []
+    mp = None
+    if force or _stale(MEASURE_LIB, [MEASURE_SRC]):
+        cmd = [nvcc(), *ARCH, *FLAGS, "-shared", MEASURE_SRC, "-o", MEASURE_LIB]
+        mp = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     for src in SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
@@ -62,6 +71,10 @@ def build(verbose: bool = False, force: bool = False) -> str:
         r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout)
+    if mp is not None:
+        out, _ = mp.communicate()
+        if mp.returncode != 0:
+            raise RuntimeError("nvcc failed (measurement kernels):\n" + out)
     return LIB
 
 
