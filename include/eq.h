@@ -222,8 +222,12 @@ eq_status eq_project_static(int nx, int ny, int nz, const eq_plan_opts* opts, co
  * request's device footprint (input + output field, 2 x 6 nx ny nz x element size) fits in
  * `hbm_budget_bytes` next to the requests in flight; each admitted request runs H2D copy,
  * projection and D2H copy on its slot's stream, so work of different requests overlaps on the
- * device.  Plans are created per grid size on first use and kept for reuse.  Results of a field
- * do not depend on what else is in flight (same kernels, fixed-order reductions).
+ * device.  A plan thread builds the plan of each queued request ahead of its admission (or takes
+ * an idle one of the same grid and options from a least-recently-used cache of at most 64), so
+ * no plan is built on the scheduler's path; the budget covers the buffers in flight and the
+ * plans in flight or cached, whose idle members are released when the queue's head needs the
+ * room.  Results of a field do not depend on what else is in flight (same kernels, fixed-order
+ * reductions).
  * Server calls are thread-safe; the server uses the device current at creation. */
 eq_status eq_server_create(size_t hbm_budget_bytes, int max_inflight, eq_server** out);
 
@@ -240,6 +244,27 @@ eq_status eq_serve_submit(eq_server* server, int nx, int ny, int nz, eq_dtype dt
  * EQ_ERR_NOT_FOUND: unknown or already consumed ticket. */
 eq_status eq_serve_poll(eq_server* server, unsigned long long ticket, int timeout_us,
                         eq_norms_t* out, double* latency_s);
+
+/* Withdraw a request that has not started: EQ_OK (the ticket is consumed; a plan prepared for it
+ * goes back to the server's cache), EQ_ERR_BUSY if it is already on the device or its plan is
+ * being built (poll it instead), EQ_ERR_NOT_FOUND for an unknown or consumed ticket. */
+eq_status eq_serve_cancel(eq_server* server, unsigned long long ticket);
+
+/* Counters of a server since its creation (totals) and its state at the call (current). */
+typedef struct {
+  unsigned long long submitted, admitted, completed, failed; /* totals */
+  unsigned long long rejected;          /* submits refused: EQ_ERR_OOM or EQ_ERR_BUSY */
+  unsigned long long cancelled;         /* eq_serve_cancel successes */
+  unsigned long long plans_created, plans_reused, plans_evicted;
+  double plan_create_seconds;           /* host time spent building plans (on the plan thread) */
+  long long queued, inflight;           /* current */
+  long long inflight_peak;              /* most requests on the device at once */
+  unsigned long long hbm_in_use;        /* current: buffers in flight + live plans' device bytes */
+  unsigned long long hbm_in_use_peak;
+  unsigned long long hbm_budget;
+  long long plans_cached;               /* idle plans kept for reuse */
+} eq_server_stats_t;
+eq_status eq_server_stats(eq_server* server, eq_server_stats_t* out);
 
 /* Stop the server: queued requests are cancelled, requests already on the device complete, then
  * every resource is released.  The server and its tickets are invalid afterwards. */

@@ -321,6 +321,22 @@ class Server:
         _lib.check(st, "eq_serve_poll")
         return n.to_dict(), lat.value
 
+    def cancel(self, ticket: int) -> bool:
+        """Withdraw a request that has not started: True if withdrawn, False if it already runs
+        (EQ_ERR_BUSY: poll it instead).  Raises for an unknown ticket."""
+        st = _lib.load().eq_serve_cancel(self.handle, int(ticket))
+        if st == _lib.EQ_ERR_BUSY:
+            return False
+        _lib.check(st, "eq_serve_cancel")
+        self._keep.pop(ticket, None)
+        return True
+
+    def stats(self) -> dict:
+        """Counters since creation and the current state (eq_server_stats)."""
+        st = _lib.EqServerStats()
+        _lib.check(_lib.load().eq_server_stats(self.handle, ctypes.byref(st)), "eq_server_stats")
+        return st.to_dict()
+
     def wait(self, ticket: int, timeout_s: float = 60.0):
         import time
         t0 = time.monotonic()

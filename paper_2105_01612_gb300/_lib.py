@@ -41,6 +41,21 @@ class EqNorms(ctypes.Structure):
         return d
 
 
+class EqServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_ulonglong), ("admitted", ctypes.c_ulonglong),
+                ("completed", ctypes.c_ulonglong), ("failed", ctypes.c_ulonglong),
+                ("rejected", ctypes.c_ulonglong), ("cancelled", ctypes.c_ulonglong),
+                ("plans_created", ctypes.c_ulonglong), ("plans_reused", ctypes.c_ulonglong),
+                ("plans_evicted", ctypes.c_ulonglong), ("plan_create_seconds", c_double),
+                ("queued", ctypes.c_longlong), ("inflight", ctypes.c_longlong),
+                ("inflight_peak", ctypes.c_longlong), ("hbm_in_use", ctypes.c_ulonglong),
+                ("hbm_in_use_peak", ctypes.c_ulonglong), ("hbm_budget", ctypes.c_ulonglong),
+                ("plans_cached", ctypes.c_longlong)]
+
+    def to_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # (name, restype, argtypes) of every entry point declared in include/eq.h
 SIGNATURES = [
     ("eq_plan_opts_default", None, [ctypes.POINTER(EqPlanOpts)]),
@@ -67,6 +82,8 @@ SIGNATURES = [
                                 c_void_p, c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]),
     ("eq_serve_poll", c_int, [c_void_p, ctypes.c_ulonglong, c_int, ctypes.POINTER(EqNorms),
                               ctypes.POINTER(c_double)]),
+    ("eq_serve_cancel", c_int, [c_void_p, ctypes.c_ulonglong]),
+    ("eq_server_stats", c_int, [c_void_p, ctypes.POINTER(EqServerStats)]),
     ("eq_server_destroy", None, [c_void_p]),
     ("eq_grains_create", c_int, [ctypes.POINTER(c_int), c_int, c_int, c_int, c_int,
                                  ctypes.POINTER(c_void_p)]),

@@ -133,3 +133,22 @@ def test_wait_selftest_rejects_bad_arguments_without_a_gpu(lib):
     from paper_2105_01612_gb300._lib import EQ_ERR_INVALID
     assert lib.eq_selftest_wait_timeout(None, 1024, None) == EQ_ERR_INVALID
     assert b"NULL plan" in lib.eq_last_error()
+
+
+def test_server_stats_layout_matches_the_header(tmp_path):
+    from paper_2105_01612_gb300._lib import EqServerStats
+    src = tmp_path / "stats.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "eq.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(eq_server_stats_t),"
+        " offsetof(eq_server_stats_t, plan_create_seconds), offsetof(eq_server_stats_t, queued),"
+        " offsetof(eq_server_stats_t, hbm_in_use_peak), offsetof(eq_server_stats_t, plans_cached));"
+        " return 0;}\n")
+    exe = tmp_path / "stats"
+    subprocess.run(["gcc", "-I", INCLUDE, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = [ctypes.sizeof(EqServerStats), EqServerStats.plan_create_seconds.offset,
+            EqServerStats.queued.offset, EqServerStats.hbm_in_use_peak.offset,
+            EqServerStats.plans_cached.offset]
+    assert got == want
