@@ -59,20 +59,28 @@ def measured_peaks():
 
 # ------------------------------------------------------------------------------ CPU oracle leg
 
-def cpu_oracle_sample(n_cpu: int = 256):
-    """Time the FP64 oracle on one n_cpu^3 field of the same recipe (grains scaled with volume)."""
+def cpu_oracle_sample(n_cpu: int = N):
+    """Time the FP64 oracle on one n_cpu^3 field of the same recipe (grains scaled with volume):
+    the whole headline field at the default size (project_large / norms_large, the oracle's
+    component-at-a-time forms, so that host memory stays bounded)."""
     import oracle
     from fieldgen import voronoi_stress_field
     grains = max(8, int(round(GRAINS * (n_cpu / N) ** 3)))
-    s = voronoi_stress_field((n_cpu,) * 3, grains, 200.0, 20.0, SEED).numpy()
+    s = voronoi_stress_field((n_cpu,) * 3, grains, 200.0, 20.0, SEED, dtype=torch_f32()).numpy()
     t0 = time.perf_counter()
-    out = oracle.project(s, "ddo")
-    oracle.norms(s, out, "ddo")
+    out = oracle.project_large(s, "ddo")
+    oracle.norms_large(s, out, "ddo")
     dt = time.perf_counter() - t0
     cores = os.cpu_count() or 1
     return {"value": n_cpu ** 3 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one {n_cpu}^3 field ({grains} grains, same recipe), FP64 numpy/scipy "
-                      f"oracle: projection + norms, {dt:.2f} s wall on {cores} host threads"}
+            "sample": f"one {n_cpu}^3 field ({grains} grains, same recipe, FP32 values), FP64 "
+                      f"numpy/scipy oracle: projection + norms (with both divergences), "
+                      f"{dt:.2f} s wall on {cores} host threads"}
+
+
+def torch_f32():
+    import torch
+    return torch.float32
 
 
 def run_reference(args):
@@ -368,8 +376,8 @@ def kernel_traffic(dominant: str):
 
 
 # the sources that define and instantiate the five pass kernels of the fixed-size path
-PASS_KERNEL_SOURCES = ("eq_dispatch.cuh", "eq_f32.cu", "eq_f64.cu", "eq_fft.cuh", "eq_internal.h",
-                       "eq_kernels.cuh", "eq_tma.cuh")
+PASS_KERNEL_SOURCES = ("eq_dispatch.cuh", "eq_f32.cu", "eq_f64.cu", "eq_fft.cuh", "eq_fft_pair.cuh",
+                       "eq_internal.h", "eq_kernels.cuh", "eq_tma.cuh", "eq_xrow.cuh")
 
 
 def source_hash() -> str:
@@ -407,7 +415,7 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     cpu_base = None
     if rank == 0 and not args.no_extras:
-        cpu_base = cpu_oracle_sample(256)          # before any CUDA work on this process
+        cpu_base = cpu_oracle_sample(N)            # before any CUDA work on this process
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -554,6 +562,7 @@ def run_ours(args):
         line["batch"] = batch_leg(dev, max(3, min(args.steps, 10)))
         torch.cuda.empty_cache()
         line["serving"] = serving_leg(dev)
+        line["serving"]["fresh_shapes"] = serving_leg(dev, fresh=True)
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -655,31 +664,51 @@ def batch_leg(dev, steps: int):
 
 
 def serving_leg(dev, rate: float = 200.0, warm: int = 200, measured: int = 2000,
-                pool_size: int = 48):
+                pool_size: int = 48, fresh: bool = False):
     """Poisson arrivals at `rate` req/s of single fields, each axis log-uniform in [32, 256],
-    FP32 Voronoi fields (a pool of `pool_size` pre-generated fields, cycled), admitted by HBM
-    footprint; p50/p99 latency from submit to completion and completed voxels/s."""
+    FP32 Voronoi fields, admitted by HBM footprint; p50/p99 latency from submit to completion
+    and completed voxels/s.  fresh=False: a pool of `pool_size` pre-generated fields, cycled
+    (after warm-up every plan is cached); fresh=True: every request draws its own grid (about
+    10^7 possible shapes, so nearly every request needs a new plan), its values the leading
+    part of one pre-generated 256^3 Voronoi field."""
     import numpy as np
     import torch
     from fieldgen import voronoi_stress_field, log_uniform_int
     import paper_2105_01612_gb300 as eq
-    rng = np.random.Generator(np.random.PCG64(210501612 + 4))
-    pool = []
-    for i in range(pool_size):
-        nx, ny, nz = (log_uniform_int(rng, 32, 256) for _ in range(3))
-        g = int(rng.integers(50, 2001))
-        f = voronoi_stress_field((nz, ny, nx), g, 150.0, 0.0, 210501612 + 4 + i,
-                                 dtype=torch.float32, device=dev).cpu().pin_memory()
-        pool.append((f, torch.empty_like(f).pin_memory()))
+    rng = np.random.Generator(np.random.PCG64(210501612 + 4 + (1000 if fresh else 0)))
+    nreq = warm + measured
+    if fresh:
+        big = voronoi_stress_field((256, 256, 256), 2000, 150.0, 0.0, 210501612 + 4,
+                                   dtype=torch.float32, device=dev).cpu().reshape(-1).pin_memory()
+        shapes = [tuple(log_uniform_int(rng, 32, 256) for _ in range(3)) for _ in range(nreq)]
+        nbuf = 16
+        outs = [torch.empty(big.numel(), dtype=torch.float32).pin_memory() for _ in range(nbuf)]
+
+        def field(i):
+            nx, ny, nz = shapes[i]
+            n = 6 * nx * ny * nz
+            return big[:n].view(6, nz, ny, nx), outs[i % nbuf][:n].view(6, nz, ny, nx), i % nbuf
+    else:
+        pool = []
+        for i in range(pool_size):
+            nx, ny, nz = (log_uniform_int(rng, 32, 256) for _ in range(3))
+            g = int(rng.integers(50, 2001))
+            f = voronoi_stress_field((nz, ny, nx), g, 150.0, 0.0, 210501612 + 4 + i,
+                                     dtype=torch.float32, device=dev).cpu().pin_memory()
+            pool.append((f, torch.empty_like(f).pin_memory()))
+
+        def field(i):
+            f, o = pool[i % pool_size]
+            return f, o, i % pool_size
     srv = eq.Server(64 << 30, max_inflight=8, device=dev)
-    gaps = rng.exponential(1.0 / rate, size=warm + measured)
+    gaps = rng.exponential(1.0 / rate, size=nreq)
     pending = {}
     busy_out = {}
-    lat, vox_done = [], 0
-    t_start = time.perf_counter()
-    t_next = t_start
+    lat, vox_done, offered = [], 0, []
+    t_next = time.perf_counter()
     t_meas0 = None
     t_last = None
+    st0 = None
 
     def drain(block: bool):
         nonlocal vox_done, t_last
@@ -687,14 +716,14 @@ def serving_leg(dev, rate: float = 200.0, warm: int = 200, measured: int = 2000,
             r = srv.poll(tk, 0) if not block else srv.wait(tk)
             if r is None:
                 continue
-            i, nv = pending.pop(tk)
-            busy_out.pop(i % pool_size, None)
+            i, nv, k = pending.pop(tk)
+            busy_out.pop(k, None)
             if i >= warm:
                 lat.append(r[1])
                 vox_done += nv
                 t_last = time.perf_counter()
 
-    for i in range(warm + measured):
+    for i in range(nreq):
         t_next += gaps[i]
         while True:
             now = time.perf_counter()
@@ -704,30 +733,41 @@ def serving_leg(dev, rate: float = 200.0, warm: int = 200, measured: int = 2000,
             time.sleep(min(2e-4, max(0.0, t_next - now)))
         if i == warm:
             t_meas0 = time.perf_counter()
-        k = i % pool_size
+            st0 = srv.stats()
+        f, o, k = field(i)
         if k in busy_out:                      # output buffer still in use: wait for it
             tk_prev = busy_out[k]
             r = srv.wait(tk_prev)
-            j, nv = pending.pop(tk_prev)
+            j, nv, _ = pending.pop(tk_prev)
             busy_out.pop(k, None)
             if j >= warm:
                 lat.append(r[1])
                 vox_done += nv
                 t_last = time.perf_counter()
-        f, o = pool[k]
         tk = srv.submit(f, o)
-        pending[tk] = (i, f.numel() // 6)
+        pending[tk] = (i, f.numel() // 6, k)
         busy_out[k] = tk
+        offered.append(f.numel() // 6)
     drain(True)
+    st1 = srv.stats()
     srv.close()
     wall = (t_last or time.perf_counter()) - t_meas0
     lat_ms = sorted(1e3 * v for v in lat)
     q = lambda p: lat_ms[min(len(lat_ms) - 1, int(round(p * (len(lat_ms) - 1))))]
+    created = st1["plans_created"] - st0["plans_created"]
+    plan_s = st1["plan_create_seconds"] - st0["plan_create_seconds"]
+    what = ("every request a fresh grid (one 256^3 Voronoi field's leading values)" if fresh
+            else f"{pool_size} pre-generated Voronoi fields cycled")
     return {"workload": f"Poisson {rate:g} req/s, single FP32 fields, axes log-uniform 32..256, "
-                        f"{pool_size} pre-generated Voronoi fields cycled, 8 slots, 64 GiB budget",
+                        f"{what}, 8 slots, 64 GiB budget",
             "requests": len(lat_ms), "warmup_requests": warm, "p50_ms": q(0.5), "p99_ms": q(0.99),
             "max_ms": lat_ms[-1], "value": vox_done / wall, "unit": UNIT,
-            "offered_voxels_per_s": rate * float(np.mean([f.numel() // 6 for f, _ in pool]))}
+            "offered_voxels_per_s": rate * float(np.mean(offered)),
+            "plans_created": created, "plans_reused": st1["plans_reused"] - st0["plans_reused"],
+            "plans_evicted": st1["plans_evicted"] - st0["plans_evicted"],
+            "plan_create_ms_mean": 1e3 * plan_s / max(1, created),
+            "plan_thread_busy_frac": plan_s / wall, "inflight_peak": st1["inflight_peak"],
+            "hbm_in_use_peak_gib": st1["hbm_in_use_peak"] / 2 ** 30}
 
 
 def main():

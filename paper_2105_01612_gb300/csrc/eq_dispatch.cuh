@@ -199,6 +199,76 @@ template <typename T, int N, int MINB> struct XwInst {
   }
 };
 
+template <typename T, int N, int MINB, bool PF = false> struct XrInst {
+  static cudaError_t info(TmaInfo* out) {
+    using C = XrCfg<T, N>;
+    if constexpr (!C::OK) {
+      return cudaErrorInvalidValue;
+    } else {
+      out->threads = C::THREADS;
+      out->cols = 1;
+      out->box = 0;
+      out->smem = C::SMEM;
+      const void* f = reinterpret_cast<const void*>(&k_xproj_rows<T, N, MINB, false, PF>);
+      const void* fp = reinterpret_cast<const void*>(&k_xproj_rows<T, N, MINB, true, PF>);
+      cudaError_t e = cudaSuccess;
+      for (const void* g : {f, fp}) {
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(g, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared);
+      }
+      int bl = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, f, C::THREADS, C::SMEM);
+      out->blocks_per_sm = bl;
+      return e;
+    }
+  }
+  static cudaError_t launch(const XTmaArgs& a, dim3 grid, cudaStream_t s, bool pot = false) {
+    using C = XrCfg<T, N>;
+    if constexpr (!C::OK) {
+      return cudaErrorInvalidValue;
+    } else {
+      if (pot) k_xproj_rows<T, N, MINB, true, PF><<<grid, C::THREADS, C::SMEM, s>>>(a);
+      else k_xproj_rows<T, N, MINB, false, PF><<<grid, C::THREADS, C::SMEM, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
+};
+
+// the packed two-row x pass (k_xproj_pair): 512-point FP32 rows only
+template <typename T, int N, int MINB> struct XpInst {
+  static constexpr bool OK = sizeof(T) == 4 && N == 512;
+  static cudaError_t info(TmaInfo* out) {
+    if constexpr (!OK) {
+      return cudaErrorInvalidValue;
+    } else {
+      out->threads = XpCfg::THREADS;
+      out->cols = 1;
+      out->box = 0;
+      out->smem = XpCfg::SMEM;
+      const void* f = reinterpret_cast<const void*>(&k_xproj_pair<MINB>);
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XpCfg::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+      int bl = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, f, XpCfg::THREADS, XpCfg::SMEM);
+      out->blocks_per_sm = bl;
+      return e;
+    }
+  }
+  static cudaError_t launch(const XTmaArgs& a, dim3 grid, cudaStream_t s) {
+    if constexpr (!OK) {
+      return cudaErrorInvalidValue;
+    } else {
+      k_xproj_pair<MINB><<<grid, XpCfg::THREADS, XpCfg::SMEM, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
+};
+
 // blocks per SM asked of the register allocator for the warp-per-row x pass: FP32 variants 2 and
 // 3 target three and four blocks; FP64 rows take twice the shared memory, so one and two
 template <typename T> constexpr int XW_MINB(int fp32_blocks) {
@@ -279,7 +349,11 @@ template <typename T> cudaError_t xtma_info_t(int n, int v, TmaInfo* out) {
   switch (n) {
 #define EQ_CASE(N)                                              \
   case N:                                                         \
-    return v == 3   ? XwInst<T, N, XW_MINB<T>(4)>::info(out)                  \
+    return v == 7   ? XpInst<T, N, 5>::info(out)                              \
+           : v == 6 ? XrInst<T, N, XW_MINB<T>(3), true>::info(out)            \
+           : v == 5 ? XrInst<T, N, XW_MINB<T>(5)>::info(out)                  \
+           : v == 4 ? XrInst<T, N, XW_MINB<T>(4)>::info(out)                  \
+           : v == 3 ? XwInst<T, N, XW_MINB<T>(4)>::info(out)                  \
            : v == 2 ? XwInst<T, N, XW_MINB<T>(3)>::info(out)                  \
                     : (v ? XTmaInst<T, N, 1>::info(out) : XTmaInst<T, N, 0>::info(out));
     EQ_FOR_LENGTHS(EQ_CASE)
@@ -287,14 +361,17 @@ template <typename T> cudaError_t xtma_info_t(int n, int v, TmaInfo* out) {
     default: return cudaErrorInvalidValue;
   }
 }
-// potential x pass in the warp-per-row kernel (variants 2 and 3 only)
+// potential x pass in the warp-per-row kernels (variants 2 to 6 only)
 template <typename T> cudaError_t xpot_warp_t(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s) {
-  if (v != 2 && v != 3) return cudaErrorInvalidValue;
+  if (v < 2 || v > 6) return cudaErrorInvalidValue;
   switch (n) {
 #define EQ_CASE(N)                                                                     \
   case N:                                                                                \
-    return v == 3 ? XwInst<T, N, XW_MINB<T>(4)>::launch(a, grid, s, true)               \
-                  : XwInst<T, N, XW_MINB<T>(3)>::launch(a, grid, s, true);
+    return v == 6   ? XrInst<T, N, XW_MINB<T>(3), true>::launch(a, grid, s, true)       \
+           : v == 5 ? XrInst<T, N, XW_MINB<T>(5)>::launch(a, grid, s, true)             \
+           : v == 4 ? XrInst<T, N, XW_MINB<T>(4)>::launch(a, grid, s, true)             \
+           : v == 3 ? XwInst<T, N, XW_MINB<T>(4)>::launch(a, grid, s, true)             \
+                    : XwInst<T, N, XW_MINB<T>(3)>::launch(a, grid, s, true);
     EQ_FOR_LENGTHS(EQ_CASE)
 #undef EQ_CASE
     default: return cudaErrorInvalidValue;
@@ -304,7 +381,11 @@ template <typename T> cudaError_t xtma_launch_t(int n, int v, const XTmaArgs& a,
   switch (n) {
 #define EQ_CASE(N)                                                       \
   case N:                                                                  \
-    return v == 3   ? XwInst<T, N, XW_MINB<T>(4)>::launch(a, grid, s)                  \
+    return v == 7   ? XpInst<T, N, 5>::launch(a, grid, s)                              \
+           : v == 6 ? XrInst<T, N, XW_MINB<T>(3), true>::launch(a, grid, s)            \
+           : v == 5 ? XrInst<T, N, XW_MINB<T>(5)>::launch(a, grid, s)                  \
+           : v == 4 ? XrInst<T, N, XW_MINB<T>(4)>::launch(a, grid, s)                  \
+           : v == 3 ? XwInst<T, N, XW_MINB<T>(4)>::launch(a, grid, s)                  \
            : v == 2 ? XwInst<T, N, XW_MINB<T>(3)>::launch(a, grid, s)                  \
                     : (v ? XTmaInst<T, N, 1>::launch(a, grid, s) : XTmaInst<T, N, 0>::launch(a, grid, s));
     EQ_FOR_LENGTHS(EQ_CASE)

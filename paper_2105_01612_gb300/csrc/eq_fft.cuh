@@ -375,6 +375,12 @@ __device__ __forceinline__ void fft512_warp(T2 (&v)[16], int lane, T2* buf,
   }
 }
 
+// Plain running sum (a short per-thread partial, folded into a Kahan sum by the caller).
+template <typename T> struct PlainSum {
+  T s = T(0);
+  __device__ __forceinline__ void add(T v) { s += v; }
+};
+
 // Kahan-compensated FP32/FP64 running sum (per-thread partial of a global FP64 reduction).
 template <typename T> struct Kahan {
   T s = T(0), c = T(0);

@@ -411,9 +411,9 @@ __global__ void __launch_bounds__(512) k_gen_xproj(const GenArgs a) {
     const T* xix = xipool + fd.xi[0];
     const T* xiy = xipool + fd.xi[1];
     const T* xiz = xipool + fd.xi[2];
-    const double* mean = a.mean + f * 6;
+    T zmv[6];
+    eqk::zero_mode_values(a.mean + f * 6, double(fd.V), zmv);
     const T inv_v = T(1.0 / double(fd.V));
-    const double vol = double(fd.V);
     Kahan<T> r2, di2, do2, o2;
     const int ngroups = (fd.npairs + P - 1) / P;
     // row handled by this warp: column wrow = slot * 6 + side * 3 + comp
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(512) k_gen_xproj(const GenArgs a) {
           bv[c] = r[kxm * pitch + colB + c];
         }
         const bool selfmode = self2 && kx == kxm;
-        eqk::project_pair<T>(av, bv, xix[kx], xiy[ky], xiz[kz], rA == 0 && kx == 0, mean, vol,
+        eqk::project_pair<T>(av, bv, xix[kx], xiy[ky], xiz[kz], rA == 0 && kx == 0, zmv,
                              a.nyq_zero != 0, a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {

@@ -7,6 +7,7 @@
 #include "../../include/eq.h"
 #include "eq_kernels.cuh"
 #include "eq_tma.cuh"
+#include "eq_xrow.cuh"
 
 namespace eqk {
 
@@ -48,7 +49,10 @@ cudaError_t launch_tma_f32(int n, int v, bool inv, const CUtensorMap& map, const
                            const CUtensorMap& outmap, const TmaArgs& a, dim3 grid, cudaStream_t s);
 cudaError_t launch_tma_f64(int n, int v, bool inv, const CUtensorMap& map, const CUtensorMap& refmap,
                            const CUtensorMap& outmap, const TmaArgs& a, dim3 grid, cudaStream_t s);
-// bulk-copy fused x pass: info fails when no instance exists for n
+// fused x pass variants (0, 1: bulk-copy row groups; 2, 3: warp per row through a bulk-copy stage,
+// three / four blocks per SM; 4, 5: warp per row with direct loads and stores, four / five blocks
+// per SM in FP32; 6: as 4 with the next row pair's loads issued early, three blocks): info fails
+// when no instance exists for n
 cudaError_t xtma_info_f32(int n, int v, TmaInfo* out);
 cudaError_t xtma_info_f64(int n, int v, TmaInfo* out);
 cudaError_t launch_xtma_f32(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s);

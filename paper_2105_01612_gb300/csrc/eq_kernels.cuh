@@ -204,6 +204,16 @@ k_strided(const StridedArgs a) {
   }
 }
 
+// 2 c0_j V of field `mean` (FP64 means, V voxels) in the working precision, computed once per
+// field outside the mode loops; false (and nothing written) when there is no mean.
+template <typename T>
+__device__ __forceinline__ bool zero_mode_values(const double* mean, double vol, T (&zm)[6]) {
+  if (!mean) return false;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) zm[j] = T(2.0 * mean[j] * vol);
+  return true;
+}
+
 // rsqrt in the kernel's precision (library calls)
 __device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
@@ -212,7 +222,8 @@ __device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
 //   in:  a[c] = Z_c(k), bb[c] = Z_c(-k)  (c = 0..2)
 //   out: a[c] <- Zout_c(k) / V,  bb[c] <- Zout_c(-k) / V
 // Zout is the projected field Q S Q, or with `compat` its complement S - Q S Q (the mean, at
-// k = 0, is kept either way).
+// k = 0, is kept either way).  zm (nullable): the k = 0 values of the doubled Voigt components,
+// 2 c0_j V, set in place of the transformed mean at the zero mode (zero_mode_values below).
 // Works on twice the Voigt components (the unpack's 1/2 is folded into the repack and into the
 // norm weights).  With n = xi / |xi|, v = S n and s = n . v, the projector removes
 // D = n (x) v + v (x) n - s n (x) n, whose squared Frobenius norm is 2 |v|^2 - s^2 (no
@@ -222,12 +233,14 @@ __device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
 // FP32 form of project_pair below, the same arithmetic with the real and imaginary parts of each
 // doubled Voigt component held as one pair P_j = {Re, Im} and worked by packed two-lane
 // instructions (one instruction for both parts wherever they meet the same real factor).
+// ACC: the running sums of the four norm terms (anything with add(float): a Kahan sum, or a plain
+// sum that the caller folds into a compensated one).
+template <typename ACC>
 __device__ __forceinline__ void project_pair_f32x2(float2 (&a)[3], float2 (&bb)[3], float xi0,
                                                    float xi1, float xi2, bool zero_mode,
-                                                   const double* mean, double vol, bool nyq_zero,
+                                                   const float* zm, bool nyq_zero,
                                                    bool compat, float inv_v, float mult,
-                                                   Kahan<float>& r2, Kahan<float>& di2,
-                                                   Kahan<float>& do2, Kahan<float>& o2) {
+                                                   ACC& r2, ACC& di2, ACC& do2, ACC& o2) {
   // 2 S_2c = A + conj B, 2 S_2c+1 = -i (A - conj B)
   float2 P[6];
   const float2 pm = make_float2(1.f, -1.f);
@@ -236,9 +249,9 @@ __device__ __forceinline__ void project_pair_f32x2(float2 (&a)[3], float2 (&bb)[
     P[2 * c] = __ffma2_rn(bb[c], pm, a[c]);
     P[2 * c + 1] = make_float2(a[c].y + bb[c].y, bb[c].x - a[c].x);
   }
-  if (zero_mode && mean) {
+  if (zero_mode && zm) {
 #pragma unroll
-    for (int j = 0; j < 6; ++j) P[j] = make_float2(float(2.0 * mean[j] * vol), 0.f);
+    for (int j = 0; j < 6; ++j) P[j] = make_float2(zm[j], 0.f);
   }
   const float k2 = xi0 * xi0 + xi1 * xi1 + xi2 * xi2;
   float2 O[6];
@@ -311,14 +324,13 @@ __device__ __forceinline__ void project_pair_f32x2(float2 (&a)[3], float2 (&bb)[
   }
 }
 
-template <typename T, typename T2>
+template <typename T, typename T2, typename ACC>
 __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T xi1, T xi2,
-                                             bool zero_mode, const double* mean, double vol,
+                                             bool zero_mode, const T* zm,
                                              bool nyq_zero, bool compat, T inv_v, T mult,
-                                             Kahan<T>& r2, Kahan<T>& di2, Kahan<T>& do2,
-                                             Kahan<T>& o2) {
+                                             ACC& r2, ACC& di2, ACC& do2, ACC& o2) {
   if constexpr (sizeof(T) == 4) {
-    project_pair_f32x2(a, bb, xi0, xi1, xi2, zero_mode, mean, vol, nyq_zero, compat, inv_v, mult,
+    project_pair_f32x2(a, bb, xi0, xi1, xi2, zero_mode, zm, nyq_zero, compat, inv_v, mult,
                        r2, di2, do2, o2);
   } else {
     // 2 S_2c = A + conj B, 2 S_2c+1 = -i (A - conj B)
@@ -330,10 +342,10 @@ __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T x
       sr[2 * c + 1] = a[c].y + bb[c].y;
       si[2 * c + 1] = bb[c].x - a[c].x;
     }
-    if (zero_mode && mean) {
+    if (zero_mode && zm) {
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
-        sr[j] = T(2.0 * mean[j] * vol);
+        sr[j] = zm[j];
         si[j] = T(0);
       }
     }
@@ -498,10 +510,11 @@ k_xproj(const XArgs a) {
   T* fdata = reinterpret_cast<T*>(a.data) + field * a.field_stride;
   T* pre = fdata + (2LL * comp) * a.V;
   T* pim = pre + a.V;
-  const double* mean = a.mean ? a.mean + field * 6 : nullptr;
+  T zmv[6];
+  const T* zm = zero_mode_values(a.mean ? a.mean + field * 6 : nullptr, 1.0 / a.inv_v, zmv)
+                    ? zmv : nullptr;
   const IdxRow idx{col * PITCH};
   const T inv_v = T(a.inv_v);
-  const double vol = 1.0 / a.inv_v;
 
   Kahan<T> r2, di2, do2, o2;
 
@@ -548,7 +561,7 @@ k_xproj(const XArgs a) {
       }
       const bool selfmode = self2 && kx == kxm;
       const bool zero_mode = (rA == 0) && kx == 0;
-      project_pair<T>(av, bv, xix[kx], xiy[ky], xiz[kz], zero_mode, mean, vol, a.nyq_zero != 0,
+      project_pair<T>(av, bv, xix[kx], xiy[ky], xiz[kz], zero_mode, zm, a.nyq_zero != 0,
                       a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {

@@ -714,10 +714,11 @@ k_xproj_tma(const XTmaArgs a) {
   const int slot = col / 6, side = (col % 6) / 3;
   const int field = blockIdx.y;
   T* fdata = reinterpret_cast<T*>(a.data) + field * a.field_stride;
-  const double* mean = a.mean ? a.mean + field * 6 : nullptr;
+  T zmv[6];
+  const T* zm = zero_mode_values(a.mean ? a.mean + field * 6 : nullptr, 1.0 / a.inv_v, zmv)
+                    ? zmv : nullptr;
   const SoaAcc<T> acc{xre + col * PF, xim + col * PF};
   const T inv_v = T(a.inv_v);
-  const double vol = 1.0 / a.inv_v;
 
   auto mirror = [&](int r) {
     const int kz = r / a.ny, ky = r - kz * a.ny;
@@ -822,7 +823,7 @@ k_xproj_tma(const XTmaArgs a) {
         bv[c] = T2{xre[(colB + c) * PF + jb], xim[(colB + c) * PF + jb]};
       }
       const bool selfmode = self2 && kx == kxm;
-      project_pair<T>(av, bv, xix[kx], rxi[s][s2][0], rxi[s][s2][1], rA == 0 && kx == 0, mean, vol,
+      project_pair<T>(av, bv, xix[kx], rxi[s][s2][0], rxi[s][s2][1], rA == 0 && kx == 0, zm,
                       a.nyq_zero != 0, a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -960,12 +961,13 @@ k_xproj_warp(const XTmaArgs a) {
   const T* xiz = reinterpret_cast<const T*>(a.xi_z);
   const int field = blockIdx.y;
   T* fdata = reinterpret_cast<T*>(a.data) + field * a.field_stride;
-  const double* mean = a.mean ? a.mean + field * 6 : nullptr;
+  T zmv[6];
+  const T* zm = zero_mode_values(a.mean ? a.mean + field * 6 : nullptr, 1.0 / a.inv_v, zmv)
+                    ? zmv : nullptr;
   T* wre = rows + (2 * w) * N;
   T* wim = wre + N;
   const SoaAcc<T> acc{wre, wim};
   const T inv_v = T(a.inv_v);
-  const double vol = 1.0 / a.inv_v;
 
   // thread 0: rows of row pair g into info slot s, then stream them into the stage
   int issued = 0;
@@ -1058,7 +1060,7 @@ k_xproj_warp(const XTmaArgs a) {
           bv[c] = ym[c];
         }
       } else {
-        project_pair<T>(av, bv, xix[kx], rxi[s][0], rxi[s][1], rA == 0 && kx == 0, mean, vol,
+        project_pair<T>(av, bv, xix[kx], rxi[s][0], rxi[s][1], rA == 0 && kx == 0, zm,
                         a.nyq_zero != 0, a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2, di2,
                         do2, o2);
       }
