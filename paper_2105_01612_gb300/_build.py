@@ -12,6 +12,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeq.so")
+# the same library with device-side bounds checks (EQ_BOUNDS_CHECK): an out-of-range index raises
+# the plan's error word (reported by eq_norms) and the access is skipped; loaded instead of
+# libeq.so when the environment sets EQ_BOUNDS_CHECK=1
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libeq_check.so")
 # measurement kernels of the benchmark (throughput probes, the cuFFT baseline's projector): a
 # library of their own, not on the projection path
 MEASURE_SRC = os.path.join(CSRC, "measure", "eqm.cu")
@@ -37,40 +42,51 @@ def _stale(obj: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    """Compile every CUDA translation unit and link libeq.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, checked: bool = True) -> str:
+    """Compile every CUDA translation unit and link libeq.so (and, with `checked`, the
+    bounds-checked libeq_check.so, compiled alongside) and the measurement library libeqm.so;
+    returns the path of libeq.so."""
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(INCLUDE, "eq.h"))
-    procs, objs = [], []
+    procs = []
     mp = None
     if force or _stale(MEASURE_LIB, [MEASURE_SRC]):
         cmd = [nvcc(), *ARCH, *FLAGS, "-shared", MEASURE_SRC, "-o", MEASURE_LIB]
         mp = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
-    for src in SOURCES:
-        s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
-        objs.append(o)
-        if force or _stale(o, [s] + headers):
-            cmd = [nvcc(), *ARCH, *FLAGS, "-c", s, "-o", o]
-            if verbose:
-                print(" ".join(cmd), file=sys.stderr)
-            procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE,
-                                                stderr=subprocess.STDOUT, text=True)))
-    errors = []
-    for src, p in procs:
+    variants = [(BUILD, LIB, [])]
+    if checked:
+        variants.append((BUILD_CHECK, LIB_CHECK, ["-DEQ_BOUNDS_CHECK=1"]))
+    objs_of = {}
+    for bdir, lib, extra in variants:
+        os.makedirs(bdir, exist_ok=True)
+        objs = objs_of.setdefault(lib, [])
+        for src in SOURCES:
+            s = os.path.join(CSRC, src)
+            o = os.path.join(bdir, src.replace(".cu", ".o"))
+            objs.append(o)
+            if force or _stale(o, [s] + headers):
+                cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", s, "-o", o]
+                if verbose:
+                    print(" ".join(cmd), file=sys.stderr)
+                procs.append((lib, src, subprocess.Popen(cmd, stdout=subprocess.PIPE,
+                                                         stderr=subprocess.STDOUT, text=True)))
+    errors, rebuilt = [], set()
+    for lib, src, p in procs:
         out, _ = p.communicate()
+        rebuilt.add(lib)
         if p.returncode != 0:
             errors.append(f"{src}:\n{out}")
         elif verbose and out.strip():
             print(out, file=sys.stderr)
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    if force or procs or _stale(LIB, objs):
-        cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs]
-        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
-        if r.returncode != 0:
-            raise RuntimeError("link failed:\n" + r.stdout)
+    for _, lib, _ in variants:
+        objs = objs_of[lib]
+        if force or lib in rebuilt or _stale(lib, objs):
+            cmd = [nvcc(), *ARCH, "-shared", "-o", lib, *objs]
+            r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+            if r.returncode != 0:
+                raise RuntimeError("link failed:\n" + r.stdout)
     if mp is not None:
         out, _ = mp.communicate()
         if mp.returncode != 0:

@@ -102,7 +102,9 @@ class EqError(RuntimeError):
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """libeq.so, or the bounds-checked libeq_check.so when the environment sets
+    EQ_BOUNDS_CHECK=1 (read when the library is first loaded)."""
+    return _build.LIB_CHECK if os.environ.get("EQ_BOUNDS_CHECK") == "1" else _build.LIB
 
 
 def load() -> ctypes.CDLL:

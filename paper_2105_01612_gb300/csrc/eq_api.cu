@@ -8,6 +8,11 @@
 #include <string>
 #include <vector>
 
+#include <cstdarg>
+#include <cstdio>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/eq.h"
 #include "eq_gen_host.h"
 #include "eq_internal.h"
@@ -15,6 +20,15 @@
 namespace {
 
 thread_local std::string g_last_error;
+
+// Host-side trace ranges (NVTX: no-ops unless a profiler is attached): one per call and one per
+// pass launch, so that a timeline shows which call and pass each kernel belongs to.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 eq_status fail(eq_status st, const std::string& msg) {
   g_last_error = msg;
@@ -31,6 +45,26 @@ bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 namespace eqk {
 bool length_supported(int n) { return is_pow2(n) && n <= 1024; }
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+// Diagnostics on stderr, by the level in the environment variable EQ_LOG (read once): 0 or unset
+// silent, 1 plan decisions (kernel variants, grids, workspace), 2 also every call and every
+// serving admission, completion and plan release.
+int log_level() {
+  static const int lv = [] {
+    const char* e = getenv("EQ_LOG");
+    return e && e[0] >= '0' && e[0] <= '9' ? e[0] - '0' : 0;
+  }();
+  return lv;
+}
+void log(int level, const char* fmt, ...) {
+  if (log_level() < level) return;
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  fprintf(stderr, "[eq] %s\n", buf);
+}
 }  // namespace eqk
 
 // ---------------------------------------------------------------- finalisation kernels
@@ -507,7 +541,20 @@ eq_status enqueue_passes(eq_plan* p, const void* d_in, void* d_final, cudaStream
     if (st != EQ_OK) return fail(st, "eq_project: " + err);
     return EQ_OK;
   }
-  auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
+  static const char* kPassNames[EQ_NUM_PASSES] = {"eq z forward", "eq mean", "eq y forward",
+                                                   "eq x project", "eq y inverse", "eq z inverse",
+                                                   "eq norms"};
+  int open_range = -1;
+  auto mark = [&](int i) {
+    if (ev) cudaEventRecord(ev[i], s);
+    if (open_range >= 0) nvtxRangePop();
+    open_range = i < EQ_NUM_PASSES ? i : -1;
+    if (open_range >= 0) nvtxRangePushA(kPassNames[i]);
+  };
+  struct CloseRange {
+    int* r;
+    ~CloseRange() { if (*r >= 0) nvtxRangePop(); }
+  } close_range{&open_range};
   mark(0);
   // the TMA passes need 16-byte aligned buffers; decide once per call so the reductions and
   // their finalisation agree on the grid
@@ -522,6 +569,7 @@ eq_status enqueue_passes(eq_plan* p, const void* d_in, void* d_final, cudaStream
   eqk::StridedArgs a{};
   a.field_stride = fstride;
   a.V = V;
+  a.err = p->err;
   {
     a.in = d_in; a.out = d_out; a.ref = nullptr; a.tw = p->tw[2];
     a.nstride = (long long)p->ny * p->nx; a.inner = a.nstride; a.outer_stride = 0;
@@ -546,7 +594,7 @@ eq_status enqueue_passes(eq_plan* p, const void* d_in, void* d_final, cudaStream
   mark(2);
   // pass 2: y forward
   eqk::StridedArgs ay{};
-  ay.field_stride = fstride; ay.V = V;
+  ay.field_stride = fstride; ay.V = V; ay.err = p->err;
   ay.in = d_out; ay.out = d_out; ay.ref = nullptr; ay.tw = p->tw[1];
   ay.nstride = p->nx; ay.inner = p->nx; ay.outer_stride = (long long)p->ny * p->nx;
   ay.ncols = (long long)p->nz * p->nx;
@@ -587,7 +635,7 @@ eq_status enqueue_passes(eq_plan* p, const void* d_in, void* d_final, cudaStream
     if (e != cudaSuccess) return fail_cuda(e, "potential x pass");
   } else if (d_y) {
     eqk::XArgs x{};
-    x.data = d_out; x.tw = p->tw[0];
+    x.data = d_out; x.tw = p->tw[0]; x.err = p->err;
     x.xi_x = p->xi[0]; x.xi_y = p->xi[1]; x.xi_z = p->xi[2];
     x.pairs = p->pairs;
     x.field_stride = fstride; x.V = V;
@@ -622,7 +670,7 @@ eq_status enqueue_passes(eq_plan* p, const void* d_in, void* d_final, cudaStream
     if (e != cudaSuccess) return fail_cuda(e, "x projection pass");
   } else {
     eqk::XArgs x{};
-    x.data = d_out; x.tw = p->tw[0];
+    x.data = d_out; x.tw = p->tw[0]; x.err = p->err;
     x.xi_x = p->xi[0]; x.xi_y = p->xi[1]; x.xi_z = p->xi[2];
     x.pairs = p->pairs; x.mean = p->mean; x.partials = p->partx;
     x.field_stride = fstride; x.V = V;
@@ -825,6 +873,7 @@ static eq_status create_generic(const int* dims, int count, eq_dtype dtype, cons
   if (st != EQ_OK) { release(p); return fail(st, "eq_plan_create: " + err); }
   p->total_elems = eqg::gen_total_elems(p->gen);
   p->dbytes = eqg::gen_device_bytes(p->gen);
+  p->err = eqg::gen_err_device(p->gen);
   if (alloc_mirror(p) != EQ_OK) {
     release(p);
     return EQ_ERR_CUDA;
@@ -1008,6 +1057,11 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
     release(p);
     return fail_cuda(e, "cudaEventCreate");
   }
+  eqk::log(1, "eq_plan_create %dx%dx%d %s batch %d: z %s variant %d grid %d, y %s variant %d grid %d, "
+              "x %s variant %d grid %d, %zu workspace bytes",
+           nx, ny, nz, dtype == EQ_F32 ? "f32" : "f64", batch, p->tma_z ? "tma" : "plain", p->vz,
+           p->tma_z ? p->gtz : p->g1, p->tma_y ? "tma" : "plain", p->vy, p->tma_y ? p->gty : p->gy,
+           p->tma_x ? "fused" : "plain", p->vx, p->tma_x ? p->gtx : p->gx, p->dbytes);
   *out = p;
   return EQ_OK;
 }
@@ -1039,6 +1093,8 @@ eq_status eq_project(eq_plan* p, const void* d_in, void* d_out, void* stream) {
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != p->device) return fail(EQ_ERR_INVALID, "eq_project: current device differs from the plan's");
+  TraceRange tr("eq_project");
+  eqk::log(2, "eq_project %dx%dx%d batch %d", p->nx, p->ny, p->nz, p->batch);
   return run(p, d_in, d_out, static_cast<cudaStream_t>(stream));
 }
 
@@ -1192,10 +1248,13 @@ eq_status eq_norms(eq_plan* p, eq_norms_t* host_out) {
   if ((e = cudaEventSynchronize(p->done)) != cudaSuccess) return fail_cuda(e, "eq_norms: wait");
   // the call's last kernel has written the host mirror
   volatile int* herr = p->herr;
-  if (*herr) {
+  if (const int flags = *herr) {
     *herr = 0;
     if (p->err && (e = cudaMemset(p->err, 0, sizeof(int))) != cudaSuccess)
       return fail_cuda(e, "eq_norms: error flag");
+    if (flags & EQ_ERRBIT_BOUNDS)
+      return fail(EQ_ERR_CUDA, "eq_norms: an index out of range was caught (bounds-checked build); "
+                               "results are invalid");
     return fail(EQ_ERR_TIMEOUT, "eq_norms: a bounded wait inside a kernel ran out; results are invalid");
   }
   std::memcpy(host_out, p->hnorms, sizeof(eq_norms_t) * p->batch);
@@ -1205,7 +1264,7 @@ eq_status eq_norms(eq_plan* p, eq_norms_t* host_out) {
 eq_status eq_selftest_wait_timeout(eq_plan* p, long long polls, void* stream) {
   if (!p || polls < 1 || polls > (1LL << 24))
     return fail(EQ_ERR_INVALID, "eq_selftest_wait_timeout: NULL plan or polls outside 1..2^24");
-  if (!p->err)
+  if (!p->err || p->gen)
     return fail(EQ_ERR_INVALID, "eq_selftest_wait_timeout: this plan's kernels have no bounded waits");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_wait_selftest<<<1, 32, 0, s>>>(p->err, polls);

@@ -37,6 +37,12 @@ struct AxisPlan {
   int bhat;           // Bluestein: m entries DFT_m(conj c, wrapped) / m
   int fast;           // 1: m is a power of two served by the fixed-size register FFT when the
                       //    pass shape gives it a compiled (m, points per thread) instance
+  // warp-per-row x pass (k_gen_xrows): transform length wm (256 or 512; 0 = not served), n itself
+  // for n = wm, else Bluestein with the tables below
+  int wm;
+  int wchirp;         // n entries c_j (complex pool), -1 when wm == n
+  int wbhat;          // wm entries DFT_wm(conj c, wrapped) / wm, -1 when wm == n
+  int wtw;            // staged twiddles of the length-wm radix-8 schedule as complex (cos, sin)
 };
 
 struct FieldDesc {
@@ -72,6 +78,7 @@ struct GenArgs {
   int mmax;                // largest transform length among the fields
   int nyq_zero;
   int compat;              // 1: return the compatible part c0 + (S - S_equil)
+  int* err;                // plan error word (bounds-checked builds)
 };
 
 // ---- small DFTs -------------------------------------------------------------------------
@@ -100,7 +107,8 @@ __device__ __forceinline__ void dft_small(T2 (&v)[R], const T2 (&wr)[R]) {
 // thread t works on column t % C and butterflies t / C, t / C + blockDim.x / C, ...
 template <int R, bool INV, typename T2>
 __device__ __forceinline__ void gen_stage(const T2* __restrict__ src, T2* __restrict__ dst, int m,
-                                          int ns, int C, int pitch, const T2* __restrict__ tw) {
+                                          int ns, int C, int pitch, const T2* __restrict__ tw,
+                                          int* err = nullptr) {
   const int nb = m / R;
   const int tstep = m / (ns * R);
   const int col = threadIdx.x % C, jstep = blockDim.x / C;
@@ -114,7 +122,10 @@ __device__ __forceinline__ void gen_stage(const T2* __restrict__ src, T2* __rest
   for (int j = threadIdx.x / C; j < nb; j += jstep) {
     T2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * pitch + col];
+    for (int r = 0; r < R; ++r) {
+      const int ix = (j + r * nb) * pitch + col;
+      v[r] = eqk::in_bounds(ix, (long long)m * pitch, err) ? src[ix] : T2{};
+    }
     const int k = j % ns;
     if (ns > 1) {
 #pragma unroll
@@ -127,25 +138,29 @@ __device__ __forceinline__ void gen_stage(const T2* __restrict__ src, T2* __rest
     dft_small<R, INV>(v, wr);
     const int base = (j / ns) * ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[(base + r * ns) * pitch + col] = v[r];
+    for (int r = 0; r < R; ++r) {
+      const int ix = (base + r * ns) * pitch + col;
+      if (eqk::in_bounds(ix, (long long)m * pitch, err)) dst[ix] = v[r];
+    }
   }
 }
 
 // Length-m transform of C columns; data starts in a, returns the buffer holding the result.
 template <bool INV, typename T2>
-__device__ T2* gen_fft(T2* a, T2* b, const AxisPlan& ap, int C, int pitch, const T2* tw) {
+__device__ T2* gen_fft(T2* a, T2* b, const AxisPlan& ap, int C, int pitch, const T2* tw,
+                       int* err = nullptr) {
   int ns = 1;
   for (int s = 0; s < ap.nst; ++s) {
     const int R = ap.radix[s];
     switch (R) {
-      case 2: gen_stage<2, INV>(a, b, ap.m, ns, C, pitch, tw); break;
-      case 3: gen_stage<3, INV>(a, b, ap.m, ns, C, pitch, tw); break;
-      case 4: gen_stage<4, INV>(a, b, ap.m, ns, C, pitch, tw); break;
-      case 5: gen_stage<5, INV>(a, b, ap.m, ns, C, pitch, tw); break;
-      case 7: gen_stage<7, INV>(a, b, ap.m, ns, C, pitch, tw); break;
-      case 8: gen_stage<8, INV>(a, b, ap.m, ns, C, pitch, tw); break;
-      case 11: gen_stage<11, INV>(a, b, ap.m, ns, C, pitch, tw); break;
-      case 13: gen_stage<13, INV>(a, b, ap.m, ns, C, pitch, tw); break;
+      case 2: gen_stage<2, INV>(a, b, ap.m, ns, C, pitch, tw, err); break;
+      case 3: gen_stage<3, INV>(a, b, ap.m, ns, C, pitch, tw, err); break;
+      case 4: gen_stage<4, INV>(a, b, ap.m, ns, C, pitch, tw, err); break;
+      case 5: gen_stage<5, INV>(a, b, ap.m, ns, C, pitch, tw, err); break;
+      case 7: gen_stage<7, INV>(a, b, ap.m, ns, C, pitch, tw, err); break;
+      case 8: gen_stage<8, INV>(a, b, ap.m, ns, C, pitch, tw, err); break;
+      case 11: gen_stage<11, INV>(a, b, ap.m, ns, C, pitch, tw, err); break;
+      case 13: gen_stage<13, INV>(a, b, ap.m, ns, C, pitch, tw, err); break;
       default: break;
     }
     __syncthreads();
@@ -222,18 +237,19 @@ __device__ __forceinline__ T2* fast_dispatch(T2* a, T2* b, const AxisPlan& ap, i
 // the outputs (before the Bluestein post-chirp, see post()).
 template <typename T2>
 __device__ T2* axis_transform(T2* a, T2* b, const AxisPlan& ap, int C, int pitch, const T2* tws,
-                              const T2* bhs, bool inv) {
+                              const T2* bhs, bool inv, int* err = nullptr) {
   if (ap.fast) {
     T2* r = fast_dispatch(a, b, ap, C, pitch, tws, bhs, inv);
     if (r) return r;
   }
-  if (!ap.blue) return inv ? gen_fft<true>(a, b, ap, C, pitch, tws) : gen_fft<false>(a, b, ap, C, pitch, tws);
-  T2* r = gen_fft<false>(a, b, ap, C, pitch, tws);
+  if (!ap.blue)
+    return inv ? gen_fft<true>(a, b, ap, C, pitch, tws, err) : gen_fft<false>(a, b, ap, C, pitch, tws, err);
+  T2* r = gen_fft<false>(a, b, ap, C, pitch, tws, err);
   T2* o = (r == a) ? b : a;
   const int col = threadIdx.x % C, jstep = blockDim.x / C;
   for (int k = threadIdx.x / C; k < ap.m; k += jstep) r[k * pitch + col] = cmul(r[k * pitch + col], bhs[k]);
   __syncthreads();
-  return gen_fft<true>(r, o, ap, C, pitch, tws);
+  return gen_fft<true>(r, o, ap, C, pitch, tws, err);
 }
 
 // value to place in the work buffer for input element j of a transform (pre-chirp, conj trick)
@@ -333,32 +349,63 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
       const bool valid = c < ncols;
       const long long o = valid ? c / inner : 0;
       const long long base = o * outer_stride + (valid ? c - o * inner : 0);
-      for (int j = j0; j < m; j += jstep) {
-        T2 x = {T(0), T(0)};
-        if (j < n && valid) {
+      // loads in batches of LB independent loads per thread (several in flight), then the
+      // statistics, the pre-chirp and the stores into the work buffer
+      constexpr int LB = 8;
+      for (int jb = j0; jb < m; jb += LB * jstep) {
+        T2 xb[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int j = jb + u * jstep;
           const long long off = base + (long long)j * nstride;
-          x = T2{in_re[off], in_im[off]};
-          if (a.mode == 1) {
-            if (!isfinite(x.x) || !isfinite(x.y)) nonfinite += T(1);
-            sa.add(x.x);
-            sb.add(x.y);
-            sq.add(wa * x.x * x.x + wb * x.y * x.y);
-          }
-          x = pre(x, j, ap, sm.ch, inv);
+          xb[u] = (j < n && valid && eqk::in_bounds(off, fd.V, a.err)) ? T2{in_re[off], in_im[off]}
+                                                                       : T2{T(0), T(0)};
         }
-        sm.a[j * pitch + col] = x;
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int j = jb + u * jstep;
+          if (j >= m) break;
+          T2 x = xb[u];
+          if (j < n && valid) {
+            if (a.mode == 1) {
+              if (!isfinite(x.x) || !isfinite(x.y)) nonfinite += T(1);
+              sa.add(x.x);
+              sb.add(x.y);
+              sq.add(wa * x.x * x.x + wb * x.y * x.y);
+            }
+            x = pre(x, j, ap, sm.ch, inv);
+          }
+          sm.a[j * pitch + col] = x;
+        }
       }
       __syncthreads();
-      T2* r = axis_transform(sm.a, sm.b, ap, C, pitch, sm.tw, sm.bh, inv);
+      T2* r = axis_transform(sm.a, sm.b, ap, C, pitch, sm.tw, sm.bh, inv, a.err);
       if (valid) {
-        for (int k = j0; k < n; k += jstep) {
-          const long long off = base + (long long)k * nstride;
-          const T2 y = post(r[k * pitch + col], k, ap, sm.ch, inv);
-          out_re[off] = y.x;
-          out_im[off] = y.y;
+        constexpr int SB = 8;
+        for (int kb = j0; kb < n; kb += SB * jstep) {
+          T2 rb[SB];                                   // residual reference, loaded ahead
           if (ref_re) {
-            linf = fmax(linf, fabs(ref_re[off] - y.x));
-            linf = fmax(linf, fabs(ref_re[off + fd.V] - y.y));
+#pragma unroll
+            for (int u = 0; u < SB; ++u) {
+              const int k = kb + u * jstep;
+              const long long off = base + (long long)k * nstride;
+              rb[u] = (k < n && eqk::in_bounds(off, fd.V, a.err))
+                          ? T2{ref_re[off], ref_re[off + fd.V]} : T2{T(0), T(0)};
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < SB; ++u) {
+            const int k = kb + u * jstep;
+            if (k >= n) break;
+            const long long off = base + (long long)k * nstride;
+            if (!eqk::in_bounds(off, fd.V, a.err)) continue;
+            const T2 y = post(r[k * pitch + col], k, ap, sm.ch, inv);
+            out_re[off] = y.x;
+            out_im[off] = y.y;
+            if (ref_re) {
+              linf = fmax(linf, fabs(rb[u].x - y.x));
+              linf = fmax(linf, fabs(rb[u].y - y.y));
+            }
           }
         }
       }
@@ -430,11 +477,12 @@ __global__ void __launch_bounds__(512) k_gen_xproj(const GenArgs a) {
       }
       for (int j = lane; j < m; j += 32) {
         T2 x = {T(0), T(0)};
-        if (j < nx && roff >= 0) x = pre(T2{base[roff + j], base[roff + j + fd.V]}, j, ap, sm.ch, false);
+        if (j < nx && roff >= 0 && eqk::in_bounds(roff + j + fd.V, 6 * fd.V, a.err))
+          x = pre(T2{base[roff + j], base[roff + j + fd.V]}, j, ap, sm.ch, false);
         sm.a[j * pitch + wrow] = x;
       }
       __syncthreads();
-      T2* r = axis_transform(sm.a, sm.b, ap, C, pitch, sm.tw, sm.bh, false);
+      T2* r = axis_transform(sm.a, sm.b, ap, C, pitch, sm.tw, sm.bh, false, a.err);
       if (ap.blue) {
         const int col = threadIdx.x % C, jstep = blockDim.x / C;
         for (int k = threadIdx.x / C; k < nx; k += jstep)
@@ -475,14 +523,218 @@ __global__ void __launch_bounds__(512) k_gen_xproj(const GenArgs a) {
           other[j * pitch + col] = j < nx ? pre(r[j * pitch + col], j, ap, sm.ch, true) : T2{T(0), T(0)};
       }
       __syncthreads();
-      T2* q = axis_transform(other, r, ap, C, pitch, sm.tw, sm.bh, true);
+      T2* q = axis_transform(other, r, ap, C, pitch, sm.tw, sm.bh, true, a.err);
       if (roff >= 0)
         for (int j = lane; j < nx; j += 32) {
+          if (!eqk::in_bounds(roff + j + fd.V, 6 * fd.V, a.err)) continue;
           const T2 y = post(q[j * pitch + wrow], j, ap, sm.ch, true);
           base[roff + j] = y.x;
           base[roff + j + fd.V] = y.y;
         }
       __syncthreads();
+    }
+    double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
+    warp_partials<4>(v, a.partials + item * WARPS_MAX * 4);
+    for (int k = nw * 4 + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
+      a.partials[item * WARPS_MAX * 4 + k] = 0.0;
+  }
+}
+
+// ---- x pass, one warp per row (lengths served by a 256- or 512-point register transform) --------
+//
+// As eqk::k_xproj_rows for one row pair at a time, with the row length n of the item's field: a
+// block of six warps, warp (side, component) loads its row of n points straight into registers
+// (lane l holds points l + 32 e, zero beyond n), takes the length-wm transform through its own
+// shared row (radix-8 stages, warp barriers only) - directly when wm = n, else as Bluestein's
+// chirp-z convolution (pre-chirp, transform, chirp transform, inverse transform, post-chirp) -
+// and leaves the n spectrum values in that row; the block meets; the mode pairs are projected
+// across the six rows; the block meets again; every warp takes the inverse transform and stores
+// its row.  All fields of an item share wm (one item = one field).
+constexpr int XR_MAXN = 256;         // longest Bluestein row (wm = 512 >= 2 n - 1)
+constexpr int XR_MAXM = 512;
+constexpr int XR_THREADS = 192;
+template <typename T> constexpr size_t xrows_smem() {
+  return sizeof(T) * (12 * XR_MAXM + 2 * eqk::staged_size(XR_MAXM) + XR_MAXN) +
+         2 * sizeof(T) * (XR_MAXN + XR_MAXM);
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void xrows_pair(const GenArgs& a, const FieldDesc& fd, int g, T* rows,
+                                           const eqk::TwStaged<T>& tw,
+                                           const typename eqk::V2<T>::t* chs,
+                                           const typename eqk::V2<T>::t* bhs, const T* xix,
+                                           const T* xiy, const T* xiz, const T* zm, T inv_v,
+                                           T* base, eqk::PlainSum<T> (&ps)[4]) {
+  using T2 = typename eqk::V2<T>::t;
+  constexpr int E = M / 32;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, side = w / 3, comp = w % 3;
+  const int n = fd.nx, ny = fd.ny, nz = fd.nz;
+  const bool blue = M != n;
+  const int rA = a.pairpool[fd.pairs + g];
+  const int kz = rA / ny, ky = rA - kz * ny;
+  const int rB = (kz == 0 ? 0 : nz - kz) * ny + (ky == 0 ? 0 : ny - ky);
+  const bool self = rA == rB;
+  const bool active = !(side == 1 && self);                 // warp-uniform
+  const long long roff = (long long)(side == 0 ? rA : rB) * n + 2LL * comp * fd.V;
+  T* wre = rows + (2 * w) * XR_MAXM;
+  T* wim = wre + XR_MAXM;
+  const eqk::SoaAcc<T> acc{wre, wim};
+  // Bluestein convolution of the pre-chirped row in x (length-M transforms): X_k = conv * c_k
+  auto chirpz = [&](T2 (&x)[E]) {
+    eqk::fft_column_acc<M, E, false, 0, true>(x, lane, acc, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = cmul(x[e], bhs[lane + 32 * e]);
+    __syncwarp();
+    eqk::fft_column_acc<M, E, true, 0, true>(x, lane, acc, tw);
+  };
+  if (active) {
+    T2 x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = lane + 32 * e;
+      x[e] = T2{T(0), T(0)};
+      if (j < n && eqk::in_bounds(roff + j + fd.V, 6 * fd.V, a.err)) {
+        x[e] = T2{base[roff + j], base[roff + j + fd.V]};
+        if (blue) x[e] = cmul(x[e], chs[j]);
+      }
+    }
+    __syncwarp();                                           // the row is free (last pair read)
+    if (blue) {
+      chirpz(x);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = lane + 32 * e;
+        if (k < n) x[e] = cmul(x[e], chs[k]);
+      }
+    } else {
+      eqk::fft_column_acc<M, E, false, 0, true>(x, lane, acc, tw);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (lane + 32 * e < n) acc.put(lane + 32 * e, x[e]);
+  }
+  __syncthreads();
+  const T xi_y = xiy[ky], xi_z = xiz[kz];
+  for (int kx = tid; kx < n; kx += blockDim.x) {
+    const int kxm = kx == 0 ? 0 : n - kx;
+    if (self && kx > kxm) continue;
+    const int ja = eqk::swz(kx), jb = eqk::swz(kxm);
+    T2 av[3], bv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T* ra = rows + (2 * c) * XR_MAXM;
+      const T* rb = rows + (2 * (self ? c : 3 + c)) * XR_MAXM;
+      av[c] = T2{ra[ja], ra[XR_MAXM + ja]};
+      bv[c] = T2{rb[jb], rb[XR_MAXM + jb]};
+    }
+    const bool selfmode = self && kx == kxm;
+    eqk::project_pair<T>(av, bv, xix[kx], xi_y, xi_z, rA == 0 && kx == 0, zm, a.nyq_zero != 0,
+                         a.compat != 0, inv_v, selfmode ? T(1) : T(2), ps[0], ps[1], ps[2], ps[3]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T* ra = rows + (2 * c) * XR_MAXM;
+      T* rb = rows + (2 * (self ? c : 3 + c)) * XR_MAXM;
+      ra[ja] = av[c].x;
+      ra[XR_MAXM + ja] = av[c].y;
+      if (!selfmode) {
+        rb[jb] = bv[c].x;
+        rb[XR_MAXM + jb] = bv[c].y;
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+    T2 x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = lane + 32 * e;
+      x[e] = T2{T(0), T(0)};
+      if (k < n) {
+        x[e] = acc.get(k);
+        if (blue) x[e] = cmul(T2{x[e].x, -x[e].y}, chs[k]);   // inverse by conjugation
+      }
+    }
+    __syncwarp();
+    if (blue) {
+      chirpz(x);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const T2 r = cmul(x[e], chs[(lane + 32 * e) < n ? lane + 32 * e : 0]);
+        x[e] = T2{r.x, -r.y};
+      }
+    } else {
+      eqk::fft_column_acc<M, E, true, 0, true>(x, lane, acc, tw);
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = lane + 32 * e;
+      if (j < n && eqk::in_bounds(roff + j + fd.V, 6 * fd.V, a.err)) {
+        base[roff + j] = x[e].x;
+        base[roff + j + fd.V] = x[e].y;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Item = (field, tiles_per_item row pairs); every field's x length has wm in {256, 512}.
+template <typename T>
+__global__ void __launch_bounds__(XR_THREADS, 2) k_gen_xrows(const GenArgs a) {
+  using T2 = typename eqk::V2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int TWS = eqk::staged_size(XR_MAXM);
+  T* rows = reinterpret_cast<T*>(smem_raw);                 // [warp][re M | im M]
+  T* twc = rows + 12 * XR_MAXM;
+  T* tws = twc + TWS;
+  T* xix = tws + TWS;
+  T2* chs = reinterpret_cast<T2*>(xix + XR_MAXN);
+  T2* bhs = chs + XR_MAXN;
+  const T2* cpool = reinterpret_cast<const T2*>(a.cpool);
+  const T* xipool = reinterpret_cast<const T*>(a.xipool);
+  const int nw = blockDim.x >> 5;
+  int cur_f = -1;
+  for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    const int f = find_field(a.item0, a.nfields, item);
+    const FieldDesc fd = a.fields[f];
+    const AxisPlan& ap = a.axes[fd.ax[0]];
+    const int wm = ap.wm;
+    if (f != cur_f) {                       // tables of this field's x length into shared memory
+      __syncthreads();
+      const int ts = eqk::staged_size(wm);
+      for (int i = threadIdx.x; i < ts; i += blockDim.x) {
+        const T2 t = cpool[ap.wtw + i];
+        twc[i] = t.x;
+        tws[i] = t.y;
+      }
+      for (int i = threadIdx.x; i < fd.nx; i += blockDim.x) xix[i] = xipool[fd.xi[0] + i];
+      if (wm != fd.nx) {
+        for (int i = threadIdx.x; i < fd.nx; i += blockDim.x) chs[i] = cpool[ap.wchirp + i];
+        for (int i = threadIdx.x; i < wm; i += blockDim.x) bhs[i] = cpool[ap.wbhat + i];
+      }
+      __syncthreads();
+      cur_f = f;
+    }
+    const eqk::TwStaged<T> tw{twc, tws};
+    T* base = reinterpret_cast<T*>(a.out) + fd.out_off;
+    const T* xiy = xipool + fd.xi[1];
+    const T* xiz = xipool + fd.xi[2];
+    T zmv[6];
+    eqk::zero_mode_values(a.mean + f * 6, double(fd.V), zmv);
+    const T inv_v = T(1.0 / double(fd.V));
+    Kahan<T> r2, di2, do2, o2;
+    const long long local = item - a.item0[f];
+    for (int g = (int)(local * a.tiles_per_item);
+         g < fd.npairs && g < (local + 1) * a.tiles_per_item; ++g) {
+      eqk::PlainSum<T> ps[4];
+      if (wm == 512)
+        xrows_pair<T, 512>(a, fd, g, rows, tw, chs, bhs, xix, xiy, xiz, zmv, inv_v, base, ps);
+      else
+        xrows_pair<T, 256>(a, fd, g, rows, tw, chs, bhs, xix, xiy, xiz, zmv, inv_v, base, ps);
+      r2.add(ps[0].s);
+      di2.add(ps[1].s);
+      do2.add(ps[2].s);
+      o2.add(ps[3].s);
     }
     double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
     warp_partials<4>(v, a.partials + item * WARPS_MAX * 4);

@@ -166,6 +166,7 @@ struct GenPlan {
   double* mean = nullptr;
   double* instats = nullptr;
   eq_norms_t* norms = nullptr;
+  int* err = nullptr;          // error word (bounds-checked builds raise it)
   PassShape z, y, x;
   std::vector<FieldDesc> fh;
   std::vector<AxisPlan> ah;
@@ -227,6 +228,26 @@ void build_tables(GenPlan* g, const std::vector<int>& lens, std::vector<unsigned
     tw_of_m[m] = off;
     return off;
   };
+  // staged twiddles W_{Ns R}^{r k} of the radix-8 schedule of a power-of-two length M (stages with
+  // Ns > 1 in order, k < Ns, r = 1..R-1), as complex (cos, sin) entries
+  std::map<int, int> staged_of_m;
+  auto staged = [&](int M) {
+    auto it = staged_of_m.find(M);
+    if (it != staged_of_m.end()) return it->second;
+    const int off = int(cpool.size() / (2 * sizeof(T)));
+    int ns = 1, st = 0;
+    while (ns < M) {
+      const int R = eqk::stage_radix(M, st);
+      if (ns > 1)
+        for (int k = 0; k < ns; ++k)
+          for (int r = 1; r < R; ++r)
+            push_complex<T>(cpool, std::polar(1.0, -two_pi * double(r * k) / double(ns * R)));
+      ns *= R;
+      ++st;
+    }
+    staged_of_m[M] = off;
+    return off;
+  };
   for (int n : lens) {
     if (axis_of_len.count(n)) continue;
     AxisPlan ap{};
@@ -273,6 +294,40 @@ void build_tables(GenPlan* g, const std::vector<int>& lens, std::vector<unsigned
       for (int j = 0; j < n; ++j) push_complex<T>(cpool, c[j]);
       ap.bhat = int(cpool.size() / (2 * sizeof(T)));
       for (const std::complex<double>& v : chirp_transform(n, ap.m, b)) push_complex<T>(cpool, v);
+    }
+    // warp-per-row x pass: a power-of-two transform of 256 or 512 points in registers, directly
+    // for n = 256, 512, else Bluestein with the power of two >= max(256, 2 n - 1)
+    ap.wm = 0;
+    ap.wchirp = ap.wbhat = ap.wtw = -1;
+    if (n == 256 || n == 512) {
+      ap.wm = n;
+    } else {
+      int p2 = 256;
+      while (p2 < 2 * n - 1) p2 <<= 1;
+      if (p2 <= 512) ap.wm = p2;
+    }
+    if (ap.wm) {
+      ap.wtw = staged(ap.wm);
+      if (ap.wm != n) {
+        if (ap.blue && ap.m == ap.wm) {
+          ap.wchirp = ap.chirp;
+          ap.wbhat = ap.bhat;
+        } else {
+          std::vector<std::complex<double>> c(n), b(ap.wm, 0.0);
+          for (int j = 0; j < n; ++j) {
+            const long long q = (long long)j * j % (2LL * n);
+            c[j] = std::polar(1.0, -pi * double(q) / n);
+          }
+          for (int d = 0; d < n; ++d) {
+            b[d] = std::conj(c[d]);
+            if (d > 0) b[ap.wm - d] = std::conj(c[d]);
+          }
+          ap.wchirp = int(cpool.size() / (2 * sizeof(T)));
+          for (int j = 0; j < n; ++j) push_complex<T>(cpool, c[j]);
+          ap.wbhat = int(cpool.size() / (2 * sizeof(T)));
+          for (const std::complex<double>& v : chirp_transform(n, ap.wm, b)) push_complex<T>(cpool, v);
+        }
+      }
     }
     axis_of_len[n] = (int)g->ah.size();
     g->ah.push_back(ap);
@@ -392,6 +447,7 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
   const size_t o_m = take(sizeof(double) * 6 * count);
   const size_t o_is = take(sizeof(double) * 2 * count);
   const size_t o_n = take(sizeof(eq_norms_t) * count);
+  const size_t o_err = take(sizeof(int));
   g->dbytes = cur;
   cudaError_t e = cudaMalloc(&g->dmem, cur);
   if (e != cudaSuccess) {
@@ -409,6 +465,12 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
   g->mean = reinterpret_cast<double*>(b + o_m);
   g->instats = reinterpret_cast<double*>(b + o_is);
   g->norms = reinterpret_cast<eq_norms_t*>(b + o_n);
+  g->err = reinterpret_cast<int*>(b + o_err);
+  if ((e = cudaMemset(g->err, 0, sizeof(int))) != cudaSuccess) {
+    *err = std::string("error word: ") + cudaGetErrorString(e);
+    gen_destroy(g);
+    return EQ_ERR_CUDA;
+  }
   struct Up { void* d; const void* h; size_t n; } ups[] = {
       {g->fields, g->fh.data(), sizeof(FieldDesc) * count},
       {g->axes, g->ah.data(), sizeof(AxisPlan) * g->ah.size()},
@@ -435,13 +497,20 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
   return EQ_OK;
 }
 
+// Every field's x length is served by the warp-per-row x pass (a 256- or 512-point transform).
+bool xrows_supported(const GenPlan* g) {
+  for (const FieldDesc& fd : g->fh)
+    if (g->ah[fd.ax[0]].wm == 0) return false;
+  return true;
+}
+
 GenTune gen_default_tune(const GenPlan* g) {
   const size_t es = g->dtype == EQ_F32 ? 4 : 8;
   GenTune t;
   t.zc = es == 4 ? (g->mx[2] > 256 ? 8 : 16) : (g->mx[2] > 256 ? 4 : 8);
   t.yc = es == 4 ? (g->mx[1] > 256 ? 8 : 16) : (g->mx[1] > 256 ? 4 : 8);
   t.zt = t.yt = 256;
-  t.xp = g->mx[0] > 256 ? 1 : 2;
+  t.xp = xrows_supported(g) ? 0 : (g->mx[0] > 256 ? 1 : 2);
   return t;
 }
 
@@ -453,10 +522,19 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
   PassShape z = g->z, y = g->y, x = g->x;
   z.kind = 0; z.mmax = g->mx[2]; z.cols = t.zc; z.pitch = t.zc; z.threads = t.zt;
   y.kind = 0; y.mmax = g->mx[1]; y.cols = t.yc; y.pitch = t.yc; y.threads = t.yt;
-  x.kind = 2; x.mmax = g->mx[0]; x.cols = 6 * t.xp; x.pitch = 6 * t.xp + 1; x.threads = 32 * x.cols;
+  if (t.xp == 0 && !xrows_supported(g)) {
+    *err = "x pass: the warp-per-row kernel serves x lengths up to 256 and 512 only";
+    return EQ_ERR_INVALID;
+  }
+  if (t.xp == 0) {
+    x.kind = 3; x.mmax = g->mx[0]; x.cols = 6; x.pitch = 0; x.threads = XR_THREADS;
+  } else {
+    x.kind = 2; x.mmax = g->mx[0]; x.cols = 6 * t.xp; x.pitch = 6 * t.xp + 1; x.threads = 32 * x.cols;
+  }
   PassShape* ps[3] = {&z, &y, &x};
   for (PassShape* p : ps) {
-    p->smem = (2 * (size_t)p->mmax * p->pitch + 3 * (size_t)p->mmax) * cs;
+    p->smem = p->kind == 3 ? (g->dtype == EQ_F32 ? xrows_smem<float>() : xrows_smem<double>())
+                           : (2 * (size_t)p->mmax * p->pitch + 3 * (size_t)p->mmax) * cs;
     if (p->smem > limit || p->threads > 512 || p->threads % p->cols != 0 || p->cols < 1) {
       *err = "pass shape does not fit (tile columns, threads or shared memory)";
       return EQ_ERR_INVALID;
@@ -467,8 +545,8 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
   for (int pi = 0; pi < 3; ++pi) {
     PassShape* p = ps[pi];
     int blocks = 0;
-    cudaError_t e = occupancy(g->dtype, pi == 2 ? 2 : 0, p->threads, p->smem, &blocks);
-    if (e == cudaSuccess) e = occupancy(g->dtype, pi == 2 ? 2 : 1, p->threads, p->smem, &blocks);
+    cudaError_t e = occupancy(g->dtype, pi == 2 ? p->kind : 0, p->threads, p->smem, &blocks);
+    if (e == cudaSuccess) e = occupancy(g->dtype, pi == 2 ? p->kind : 1, p->threads, p->smem, &blocks);
     if (e != cudaSuccess || blocks < 1) {
       cudaGetLastError();
       *err = std::string("occupancy: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "0 blocks");
@@ -553,6 +631,7 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   a.fields = g->fields; a.axes = g->axes; a.cpool = g->cpool; a.xipool = g->xipool;
   a.pairpool = g->pairpool; a.mean = g->mean; a.nfields = g->F;
   a.nyq_zero = g->opts.nyq == EQ_NYQ_ZERO;
+  a.err = g->err;
   a.compat = g->opts.target == EQ_TARGET_COMPATIBILITY;
   auto shape = [&](const PassShape& p) {
     a.item0 = p.item0; a.nitems = p.nitems; a.tiles_per_item = p.tpi; a.cols = p.cols;
@@ -575,7 +654,7 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   mark(3);
   shape(g->x);
   a.partials = g->part_x; a.mode = 0;
-  if ((e = launch(2, a, g->x)) != cudaSuccess) { *err = std::string("x pass: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
+  if ((e = launch(g->x.kind, a, g->x)) != cudaSuccess) { *err = std::string("x pass: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
   mark(4);
   shape(g->y);
   a.partials = nullptr; a.axis = 1; a.mode = 0;
@@ -595,6 +674,7 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
 }
 
 const eq_norms_t* gen_norms_device(const GenPlan* g) { return g->norms; }
+int* gen_err_device(const GenPlan* g) { return g->err; }
 GenTune gen_current_tune(const GenPlan* g) { return g->tune; }
 
 // ---- tuning cache: a JSON object {"key": [zc, zt, yc, yt, xp], ...} in the file $EQ_TUNE_CACHE
@@ -677,6 +757,7 @@ static float time_pass(GenPlan* g, int which, const void* d_in, void* d_out, cud
   a.fields = g->fields; a.axes = g->axes; a.cpool = g->cpool; a.xipool = g->xipool;
   a.pairpool = g->pairpool; a.mean = g->mean; a.nfields = g->F;
   a.nyq_zero = g->opts.nyq == EQ_NYQ_ZERO;
+  a.err = g->err;
   a.compat = g->opts.target == EQ_TARGET_COMPATIBILITY;
   const PassShape& p = which == 0 ? g->z : (which == 1 ? g->y : g->x);
   a.item0 = p.item0; a.nitems = p.nitems; a.tiles_per_item = p.tpi; a.cols = p.cols;
@@ -686,7 +767,7 @@ static float time_pass(GenPlan* g, int which, const void* d_in, void* d_out, cud
   a.axis = which == 0 ? 2 : 1;
   a.mode = which == 0 ? 1 : 0;
   a.partials = which == 0 ? g->part_first : (which == 2 ? g->part_x : nullptr);
-  const int kind = which == 2 ? 2 : 0;
+  const int kind = which == 2 ? g->x.kind : 0;
   float best[3];
   for (int r = 0; r < 4; ++r) {
     cudaEventRecord(e0, s);
@@ -721,7 +802,7 @@ eq_status gen_autotune(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s
           cands.push_back(u);
         }
     } else {
-      for (int xp : {1, 2, 3}) {
+      for (int xp : {0, 1, 2, 3}) {
         GenTune u = best;
         u.xp = xp;
         cands.push_back(u);

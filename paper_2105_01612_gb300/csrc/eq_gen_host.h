@@ -20,7 +20,8 @@ struct GenPlan;
 struct GenTune {
   int zc = 16, zt = 256;   // z pass: tile columns, threads per block
   int yc = 16, yt = 256;   // y pass
-  int xp = 2;              // x pass: row pairs per block (6 xp transforms, 32 threads each)
+  int xp = 2;              // x pass: row pairs per block (6 xp transforms, 32 threads each) of
+                           // the shared-memory kernel; 0 = the warp-per-row kernel (k_gen_xrows)
 };
 
 // Largest supported axis length and the rule for it (for error messages).
@@ -33,6 +34,7 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
 eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s, cudaEvent_t* ev,
                       std::string* err);
 const eq_norms_t* gen_norms_device(const GenPlan* g);
+int* gen_err_device(const GenPlan* g);     // the plan's device error word
 GenTune gen_default_tune(const GenPlan* g);
 eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err);
 // Time candidate shapes of each pass on these buffers and keep the fastest (stored in the

@@ -8,6 +8,7 @@ template <typename T> struct GenInst {
   static const void* fn(int kind) {
     if (kind == 0) return reinterpret_cast<const void*>(&k_gen_strided<T, false>);
     if (kind == 1) return reinterpret_cast<const void*>(&k_gen_strided<T, true>);
+    if (kind == 3) return reinterpret_cast<const void*>(&k_gen_xrows<T>);
     return reinterpret_cast<const void*>(&k_gen_xproj<T>);
   }
   static cudaError_t occupancy(int kind, int threads, size_t smem, int* blocks) {
@@ -25,6 +26,7 @@ template <typename T> struct GenInst {
                             cudaStream_t s) {
     if (kind == 0) k_gen_strided<T, false><<<grid, threads, smem, s>>>(a);
     else if (kind == 1) k_gen_strided<T, true><<<grid, threads, smem, s>>>(a);
+    else if (kind == 3) k_gen_xrows<T><<<grid, threads, smem, s>>>(a);
     else k_gen_xproj<T><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
   }

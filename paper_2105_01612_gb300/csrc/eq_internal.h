@@ -65,5 +65,7 @@ void finalize_norms(const double* partx, int gridx, const double* partl, int gri
                     double vol, const double* mean, const double* instats, int linf_flag,
                     eq_norms_t* out, cudaStream_t s);
 void set_last_error(const std::string& msg);
+// diagnostics on stderr when the environment's EQ_LOG level is at least `level` (eq_api.cu)
+void log(int level, const char* fmt, ...);
 
 }  // namespace eqk

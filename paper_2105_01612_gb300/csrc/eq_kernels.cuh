@@ -18,6 +18,24 @@
 
 namespace eqk {
 
+// Bounds-checked builds (compiled with EQ_BOUNDS_CHECK defined; libeq_check.so): an index outside
+// [0, n) raises bit EQ_ERRBIT_BOUNDS of the plan's error word and the access is skipped, so a
+// wrong index shows up as an error status at eq_norms instead of a fault.  Other builds compile
+// the check away.  Checked: the global loads and stores of the plain strided and x passes, of the
+// warp-per-row x passes and of the runtime-length passes, and the shared-memory work-buffer
+// indices of the runtime-length transforms.
+#define EQ_ERRBIT_BOUNDS 2
+__device__ __forceinline__ bool in_bounds(long long i, long long n, int* err) {
+#ifdef EQ_BOUNDS_CHECK
+  if (i >= 0 && i < n) return true;
+  if (err) atomicOr(err, EQ_ERRBIT_BOUNDS);
+  return false;
+#else
+  (void)i; (void)n; (void)err;
+  return true;
+#endif
+}
+
 template <typename T, int N> struct Cfg {
   static constexpr int E = N >= 8 ? 8 : N;
   static constexpr int TPC = N / E;
@@ -54,6 +72,7 @@ struct StridedArgs {
   double* partials;        // first: [batch][3][grid][4]; last: [batch][3][grid] (linf)
   int mode;                // 0 = middle pass, 1 = first (reductions), 2 = last
   int ncomp;               // complex fields (pairs of planes) per field: 3 (stress), 2 (potential)
+  int* err;                // plan error word (bounds-checked builds; nullable)
 };
 
 struct XArgs {
@@ -75,6 +94,7 @@ struct XArgs {
   double inv_v;            // 1 / (nx ny nz)
   void* ydata;             // potential pass: field 0, plane 0 of the 4-plane y buffer
   long long yfield_stride; // elements between fields of the y buffer (4 V)
+  int* err;                // plan error word (bounds-checked builds; nullable)
 };
 
 // deterministic block sum of K doubles per thread; result valid in thread 0
@@ -166,7 +186,7 @@ k_strided(const StridedArgs a) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const long long off = base + (long long)(t + TPC * e) * a.nstride;
-      x[e] = valid ? T2{in_re[off], in_im[off]} : T2{T(0), T(0)};
+      x[e] = valid && in_bounds(off, a.V, a.err) ? T2{in_re[off], in_im[off]} : T2{T(0), T(0)};
     }
     if (a.mode == 1 && valid) {
 #pragma unroll
@@ -182,6 +202,7 @@ k_strided(const StridedArgs a) {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const long long off = base + (long long)(t + TPC * e) * a.nstride;
+        if (!in_bounds(off, a.V, a.err)) continue;
         out_re[off] = x[e].x;
         out_im[off] = x[e].y;
         if (a.mode == 2 && ref_re) {
@@ -535,7 +556,7 @@ k_xproj(const XArgs a) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const long long off = roff + t + TPC * e;
-      x[e] = active ? T2{pre[off], pim[off]} : T2{T(0), T(0)};
+      x[e] = active && in_bounds(off, a.V, a.err) ? T2{pre[off], pim[off]} : T2{T(0), T(0)};
     }
     fft_column<N, E, false>(x, t, buf, idx, tw);
 #pragma unroll
@@ -578,6 +599,7 @@ k_xproj(const XArgs a) {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const long long off = roff + t + TPC * e;
+        if (!in_bounds(off, a.V, a.err)) continue;
         pre[off] = x[e].x;
         pim[off] = x[e].y;
       }
@@ -644,7 +666,7 @@ k_xpot(const XArgs a) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const long long off = roff + t + TPC * e;
-      x[e] = active ? T2{pre[off], pim[off]} : T2{T(0), T(0)};
+      x[e] = active && in_bounds(off, a.V, a.err) ? T2{pre[off], pim[off]} : T2{T(0), T(0)};
     }
     fft_column<N, E, false>(x, t, buf, idx, tw);
 #pragma unroll
@@ -687,6 +709,7 @@ k_xpot(const XArgs a) {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const long long off = roff + t + TPC * e;
+        if (!in_bounds(off, a.V, a.err)) continue;
         yre[off] = x[e].x;
         yim[off] = x[e].y;
       }

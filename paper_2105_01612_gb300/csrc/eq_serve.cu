@@ -20,6 +20,7 @@
 // plan frees device memory, which waits for the device, so that too happens on the plan thread.
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <list>
@@ -34,8 +35,11 @@
 
 #include "../../include/eq.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace eqk {
 void set_last_error(const std::string& msg);   // eq_api.cu
+void log(int level, const char* fmt, ...);     // eq_api.cu
 }
 
 namespace {
@@ -57,6 +61,7 @@ struct Request {
   size_t bytes = 0;
   Clock::time_point t_submit;
   double latency = 0.0;
+  nvtxRangeId_t trace = 0;        // trace range from admission to completion
   ReqState state = QUEUED;
   eq_status status = EQ_OK;
   std::string error;
@@ -171,6 +176,7 @@ void planner_loop(eq_server* s) {
       s->release_bytes = 0;
       lk.unlock();
       for (eq_plan* p : rel) eq_plan_destroy(p);
+      eqk::log(2, "serve: released %zu idle plans (%zu bytes)", rel.size(), rb);
       lk.lock();
       s->in_use -= rb;
       s->cv_work.notify_one();
@@ -263,6 +269,9 @@ void finish(eq_server* s, Slot& sl, bool ok, const std::string& err) {
   }
   if (ok) s->st.completed++;
   else s->st.failed++;
+  if (r->trace) nvtxRangeEnd(r->trace);
+  eqk::log(2, "serve: request %llu %dx%dx%d %s after %.3f ms", r->id, r->nx, r->ny, r->nz,
+           ok ? "done" : "failed", 1e3 * r->latency);
   if (sl.d_in) cudaFreeAsync(sl.d_in, sl.stream);
   if (sl.d_out) cudaFreeAsync(sl.d_out, sl.stream);
   sl.d_in = sl.d_out = nullptr;
@@ -287,6 +296,13 @@ bool start(eq_server* s, Slot& sl, Request* r) {
   update_peaks(s);
   sl.plan = r->plan;
   if (!sl.plan) err = "serve: no plan";
+  {
+    char name[64];
+    snprintf(name, sizeof(name), "eq request %llu", r->id);
+    r->trace = nvtxRangeStartA(name);
+  }
+  eqk::log(2, "serve: admit request %llu %dx%dx%d (%zu bytes in use)", r->id, r->nx, r->ny, r->nz,
+           s->in_use);
   cudaError_t e = cudaSuccess;
   if (sl.plan) {
     e = cudaMallocAsync(&sl.d_in, r->bytes, sl.stream);

@@ -117,8 +117,10 @@ k_xproj_rows(const XTmaArgs a) {
         for (int e = 0; e < E; ++e) x[e] = xn[PF ? e : 0];
       } else {
 #pragma unroll
-        for (int e = 0; e < E; ++e)
-          x[e] = T2{src_re[rowoff + lane + 32 * e], src_im[rowoff + lane + 32 * e]};
+        for (int e = 0; e < E; ++e) {
+          const long long off = rowoff + lane + 32 * e;
+          x[e] = in_bounds(off, a.V, a.err) ? T2{src_re[off], src_im[off]} : T2{T(0), T(0)};
+        }
       }
       if constexpr (F16) {
         fft512_warp<false>(x, lane, wrow, tw16);
@@ -137,8 +139,10 @@ k_xproj_rows(const XTmaArgs a) {
         const RowOf nx = row_of(g + gridDim.x);
         if (nx.active) {
 #pragma unroll
-          for (int e = 0; e < E; ++e)
-            xn[e] = T2{src_re[nx.off + lane + 32 * e], src_im[nx.off + lane + 32 * e]};
+          for (int e = 0; e < E; ++e) {
+            const long long off = nx.off + lane + 32 * e;
+            xn[e] = in_bounds(off, a.V, a.err) ? T2{src_re[off], src_im[off]} : T2{T(0), T(0)};
+          }
           have_next = true;
         }
       }
@@ -212,6 +216,7 @@ k_xproj_rows(const XTmaArgs a) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int pos = kap + 16 * q + 256 * hh;
+          if (!in_bounds(rowoff + pos, a.V, a.err)) continue;
           dre[pos] = x[q].x;
           dim[pos] = x[q].y;
         }
@@ -222,6 +227,7 @@ k_xproj_rows(const XTmaArgs a) {
         fft_column_acc<N, E, true, 0, true>(x, lane, acc, tw);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
+          if (!in_bounds(rowoff + lane + 32 * e, a.V, a.err)) continue;
           dre[lane + 32 * e] = x[e].x;
           dim[lane + 32 * e] = x[e].y;
         }
@@ -303,8 +309,9 @@ k_xproj_pair(const XTmaArgs a) {
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
         const int p = lane + 32 * e;
-        const float ra = pre[oA + p], ia = pim[oA + p];
-        const float rb = self ? ra : pre[oB + p], ib = self ? ia : pim[oB + p];
+        const bool okA = in_bounds(oA + p, a.V, a.err), okB = in_bounds(oB + p, a.V, a.err);
+        const float ra = okA ? pre[oA + p] : 0.f, ia = okA ? pim[oA + p] : 0.f;
+        const float rb = self || !okB ? ra : pre[oB + p], ib = self || !okB ? ia : pim[oB + p];
         v[e] = CPair{make_float2(ra, rb), make_float2(ia, ib)};
       }
       fft512_pair<false>(v, lane, wrow, tw4);
@@ -382,6 +389,7 @@ k_xproj_pair(const XTmaArgs a) {
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int p = kap + 16 * q + 256 * hh;
+        if (!in_bounds(oA + p, a.V, a.err) || !in_bounds(oB + p, a.V, a.err)) continue;
         pre[oA + p] = v[q].r.x;
         pim[oA + p] = v[q].i.x;
         if (!self) {
