@@ -217,8 +217,8 @@ def link_leg(hin, hout, dev, reps: int = 3):
     da, db = torch.empty(hin.shape, dtype=hin.dtype, device=dev), torch.empty(hin.shape, dtype=hin.dtype, device=dev)
     s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
 
-    def timed(fn):
-        best = float("inf")
+    def timed_all(fn):
+        ts = []
         for _ in range(reps):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -226,8 +226,11 @@ def link_leg(hin, hout, dev, reps: int = 3):
             fn()
             e1.record(s1)
             torch.cuda.synchronize()
-            best = min(best, e0.elapsed_time(e1))
-        return best
+            ts.append(e0.elapsed_time(e1))
+        return ts
+
+    def timed(fn):
+        return min(timed_all(fn))
 
     def h2d():
         with torch.cuda.stream(s1):
@@ -250,14 +253,16 @@ def link_leg(hin, hout, dev, reps: int = 3):
         s1.wait_event(ev2)
 
     t_in, t_out, t_both = timed(h2d), timed(d2h), timed(both)
+    t_both_med = statistics.median(timed_all(both))
     bdf, node = gpu_numa_node(dev)
     del da, db
     return {"bytes_per_direction": nbytes, "h2d_gbs": nbytes / (t_in / 1e3) / 1e9,
             "d2h_gbs": nbytes / (t_out / 1e3) / 1e9,
             "both_gbs_total": 2 * nbytes / (t_both / 1e3) / 1e9,
-            "both_ms_per_field": t_both, "gpu_pci": bdf, "gpu_numa_node": node,
+            "both_ms_per_field": t_both, "both_ms_per_field_median": t_both_med,
+            "gpu_pci": bdf, "gpu_numa_node": node,
             "method": "torch copies between the e2e leg's pinned host buffers and device "
-                      "tensors, best of 3, CUDA events"}
+                      "tensors, best (and median) of 3, CUDA events"}
 
 
 def fp64_leg(x, out, n, dev, stream):
@@ -516,16 +521,21 @@ def run_ours(args):
             plans[j].project_host(hin, houts[j], stream=streams[j], wait=False)
         for j in range(depth):
             plans[j].norms()
-        ke = max(2 * depth, min(args.steps, 20))
-        t0 = time.perf_counter()
-        for k in range(ke):
-            j = k % depth
-            if k >= depth:
-                plans[j].norms()                  # step k - depth done: output and norms read
-            plans[j].project_host(hin, houts[j], stream=streams[j], wait=False)
-        for j in range(depth):
-            plans[j].norms()
-        te = (time.perf_counter() - t0) / ke
+        # the host link is shared with the machine's other GPUs, so one window can catch
+        # another tenant's traffic: time three windows and report the median (all are listed)
+        ke = max(2 * depth, min(args.steps, 10))
+        windows = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            for k in range(ke):
+                j = k % depth
+                if k >= depth:
+                    plans[j].norms()              # step k - depth done: output and norms read
+                plans[j].project_host(hin, houts[j], stream=streams[j], wait=False)
+            for j in range(depth):
+                plans[j].norms()
+            windows.append((time.perf_counter() - t0) / ke)
+        te = statistics.median(windows)
         plans[0].project_host(hin, houts[0])
         t0 = time.perf_counter()
         ks = max(1, min(args.steps, 5))
@@ -535,9 +545,11 @@ def run_ours(args):
         ts = (time.perf_counter() - t0) / ks
         line["e2e"] = {"value": vox / te, "unit": UNIT, "h2d_bytes_per_step": hin.numel() * 4,
                        "d2h_bytes_per_step": hin.numel() * 4 + 112,
-                       "ms_per_step": te * 1e3, "steps": ke,
+                       "ms_per_step": te * 1e3, "steps": 3 * ke,
+                       "windows_ms": [w * 1e3 for w in windows],
                        "method": "eq_project_host_async, three plans on three streams (three "
-                                 "fields in flight), pinned host buffers, norms read every step",
+                                 "fields in flight), pinned host buffers, norms read every step; "
+                                 f"median of three windows of {ke} steps",
                        "blocking_call": {"value": vox / ts, "ms_per_step": ts * 1e3,
                                          "method": "eq_project_host (waits for each field)"}}
         for q in plans:
