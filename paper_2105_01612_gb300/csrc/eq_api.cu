@@ -614,7 +614,7 @@ eq_status enqueue_passes(eq_plan* p, const void* d_in, void* d_final, cudaStream
   // potential x pass (reads the spectrum before the projector rewrites it): the warp-per-row
   // kernel when the x pass runs it and the buffers allow bulk copies, else the plain-load kernel
   // (the packed two-row x pass, variant 7, has no potential form: the row kernel 4 runs it)
-  const int pot_vx = p->vx == 7 ? 4 : p->vx;
+  const int pot_vx = p->vx >= 7 ? 4 : p->vx;
   const bool pot_warp = d_y && p->tma_x && pot_vx >= 2 && pot_vx <= 6 &&
                         !(reinterpret_cast<uintptr_t>(d_out) & 15) &&
                         !(reinterpret_cast<uintptr_t>(d_y) & 15);
@@ -966,7 +966,7 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
     p->tma_allow = !(no_tma && no_tma[0] == '1') && encode_fn() != nullptr &&
                    ((size_t)nx * p->esize) % 16 == 0;
     int gmax_z = 1, gmax_x = 1;
-    for (int v = 7; v >= 0; --v) {
+    for (int v = 8; v >= 0; --v) {
       tma_setup(p, v <= 2 ? v : 0, v <= 2 ? v : 0, v);
       gmax_z = std::max(gmax_z, std::max(p->gtz, p->gty));
       gmax_x = std::max(gmax_x, p->gtx);
@@ -979,11 +979,12 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
     const char* vzs = getenv("EQ_TMA_VARIANT_Z");
     const int v0 = vs && vs[0] >= '0' && vs[0] <= '2' ? vs[0] - '0' : 2;
     const int vz0 = vzs && vzs[0] >= '0' && vzs[0] <= '2' ? vzs[0] - '0' : v0;
-    // x pass: the packed two-row kernel (7) where it exists (512-point FP32 rows), else the
-    // warp-per-row kernel with direct loads (4), measured faster than the staged forms (3, 2)
-    const int vx0 = vxs && vxs[0] >= '0' && vxs[0] <= '7' ? vxs[0] - '0' : 7;
+    // x pass: the packed two-row kernel with cp.async staging (8) where it exists (512-point
+    // FP32 rows), else the warp-per-row kernel with direct loads (4), measured faster than the
+    // bulk-copy staged forms (3, 2)
+    const int vx0 = vxs && vxs[0] >= '0' && vxs[0] <= '8' ? vxs[0] - '0' : 8;
     tma_setup(p, vz0, v0, vx0);
-    if (!p->tma_x && vx0 == 7) tma_setup(p, vz0, v0, 4);
+    if (!p->tma_x && vx0 >= 7) tma_setup(p, vz0, v0, 4);
     for (int v = vx0 - 1; !p->tma_x && v >= 0; --v) tma_setup(p, vz0, v0, v);   // fall back
     p->gtz_max = gmax_z;
     p->gtx_max = gmax_x;
@@ -1346,7 +1347,7 @@ eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stre
   cudaEvent_t ev[EQ_NUM_PASSES + 1];
   for (auto& x : ev)
     if ((e = cudaEventCreate(&x)) != cudaSuccess) return fail_cuda(e, "eq_plan_autotune: events");
-  constexpr int NCFG = 10;
+  constexpr int NCFG = 11;
   float ms[NCFG][EQ_NUM_PASSES] = {};
   bool ok[NCFG][3] = {};                                // [config][axis z, y, x] available
   const int saved_cap = p->tcap, saved_used = p->tused;
@@ -1355,7 +1356,7 @@ eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stre
   // strided kernel (where it exists; its config counts for an axis only if the axis really ran
   // it), 6 and 7 the warp-per-row x pass with direct loads and stores (four and five blocks),
   // 8 the same with the next row pair's loads issued early (three blocks), 9 the packed two-row
-  // x pass (512-point FP32 rows)
+  // x pass (512-point FP32 rows), 10 the same with the next rows staged by cp.async
   auto xvar = [](int cfg) {
     return cfg == 1 ? 1 : (cfg == 3 ? 2 : (cfg == 4 ? 3 : (cfg >= 6 ? cfg - 2 : 0)));
   };

@@ -238,23 +238,24 @@ template <typename T, int N, int MINB, bool PF = false> struct XrInst {
 };
 
 // the packed two-row x pass (k_xproj_pair): 512-point FP32 rows only
-template <typename T, int N, int MINB> struct XpInst {
+template <typename T, int N, int MINB, bool STAGED = false> struct XpInst {
   static constexpr bool OK = sizeof(T) == 4 && N == 512;
+  using C = XpCfg<STAGED>;
   static cudaError_t info(TmaInfo* out) {
     if constexpr (!OK) {
       return cudaErrorInvalidValue;
     } else {
-      out->threads = XpCfg::THREADS;
+      out->threads = C::THREADS;
       out->cols = 1;
       out->box = 0;
-      out->smem = XpCfg::SMEM;
-      const void* f = reinterpret_cast<const void*>(&k_xproj_pair<MINB>);
-      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XpCfg::SMEM);
+      out->smem = C::SMEM;
+      const void* f = reinterpret_cast<const void*>(&k_xproj_pair<MINB, STAGED>);
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
       int bl = 0;
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, f, XpCfg::THREADS, XpCfg::SMEM);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, f, C::THREADS, C::SMEM);
       out->blocks_per_sm = bl;
       return e;
     }
@@ -263,7 +264,7 @@ template <typename T, int N, int MINB> struct XpInst {
     if constexpr (!OK) {
       return cudaErrorInvalidValue;
     } else {
-      k_xproj_pair<MINB><<<grid, XpCfg::THREADS, XpCfg::SMEM, s>>>(a);
+      k_xproj_pair<MINB, STAGED><<<grid, C::THREADS, C::SMEM, s>>>(a);
       return cudaGetLastError();
     }
   }
@@ -349,7 +350,8 @@ template <typename T> cudaError_t xtma_info_t(int n, int v, TmaInfo* out) {
   switch (n) {
 #define EQ_CASE(N)                                              \
   case N:                                                         \
-    return v == 7   ? XpInst<T, N, 5>::info(out)                              \
+    return v == 8   ? XpInst<T, N, 4, true>::info(out)                        \
+           : v == 7 ? XpInst<T, N, 5>::info(out)                              \
            : v == 6 ? XrInst<T, N, XW_MINB<T>(3), true>::info(out)            \
            : v == 5 ? XrInst<T, N, XW_MINB<T>(5)>::info(out)                  \
            : v == 4 ? XrInst<T, N, XW_MINB<T>(4)>::info(out)                  \
@@ -381,7 +383,8 @@ template <typename T> cudaError_t xtma_launch_t(int n, int v, const XTmaArgs& a,
   switch (n) {
 #define EQ_CASE(N)                                                       \
   case N:                                                                  \
-    return v == 7   ? XpInst<T, N, 5>::launch(a, grid, s)                              \
+    return v == 8   ? XpInst<T, N, 4, true>::launch(a, grid, s)                        \
+           : v == 7 ? XpInst<T, N, 5>::launch(a, grid, s)                              \
            : v == 6 ? XrInst<T, N, XW_MINB<T>(3), true>::launch(a, grid, s)            \
            : v == 5 ? XrInst<T, N, XW_MINB<T>(5)>::launch(a, grid, s)                  \
            : v == 4 ? XrInst<T, N, XW_MINB<T>(4)>::launch(a, grid, s)                  \

@@ -145,16 +145,29 @@ template <bool INV> __device__ __forceinline__ void pdft16(CPair* v) {
 }
 
 // 512-point transform of the two rows held by one warp (see the file comment).  tw: W512^(l k1)
-// as [k1][l] entries {cos, cos, sin, sin} (forward factors; the inverse conjugates them).  buf:
+// as [k1][l] entries {cos, cos, sin, sin} or {cos, sin} (forward factors; the inverse conjugates
+// them).  buf:
 // the warp's 512 16-byte entries; no lane may still read it on entry, and it is free on return.
-template <bool INV>
+// twiddle pair registers {c, c} and {s, s} from a table of {c, c, s, s} or of {c, s} entries
+__device__ __forceinline__ void tw_pair(const float4* tw, int i, float2& C, float2& S) {
+  const float4 w = tw[i];
+  C = make_float2(w.x, w.y);
+  S = make_float2(w.z, w.w);
+}
+__device__ __forceinline__ void tw_pair(const float2* tw, int i, float2& C, float2& S) {
+  const float2 w = tw[i];
+  C = bcast(w.x);
+  S = bcast(w.y);
+}
+
+template <bool INV, typename TWE>
 __device__ __forceinline__ void fft512_pair(CPair (&v)[16], int lane, float4* buf,
-                                            const float4* __restrict__ tw) {
+                                            const TWE* __restrict__ tw) {
   pdft16<INV>(v);
 #pragma unroll
   for (int k1 = 1; k1 < 16; ++k1) {
-    const float4 w = tw[k1 * 32 + lane];
-    const float2 C = make_float2(w.x, w.y), S = make_float2(w.z, w.w);
+    float2 C, S;
+    tw_pair(tw, k1 * 32 + lane, C, S);
     const CPair x = v[k1];
     if (INV) {   // (r + i i)(c - i s) = (r c + i s) + i (i c - r s)
       v[k1] = CPair{__ffma2_rn(x.i, S, __fmul2_rn(x.r, C)), fsub2(__fmul2_rn(x.i, C), __fmul2_rn(x.r, S))};

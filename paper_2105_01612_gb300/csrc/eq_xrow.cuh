@@ -13,6 +13,8 @@
 // waits on a copy barrier.  Several blocks share an SM, so one block's loads and barriers overlap
 // the others' arithmetic.
 #pragma once
+#include <type_traits>
+
 #include "eq_fft_pair.cuh"
 #include "eq_tma.cuh"
 
@@ -256,21 +258,36 @@ k_xproj_rows(const XTmaArgs a) {
 // the two block barriers each thread takes modes kx and 512 - kx of all three fields: both mode
 // pairs (kx, -kx) and (512 - kx, kx - 512) of the row pair from six 16-byte loads.  A self-mirror
 // row pair (one row) is loaded into both halves and only its first half is stored.
-struct XpCfg {
+//
+// STAGED: each warp copies its two rows of the next row pair into a staging area of shared memory
+// with cp.async as soon as it has read the current ones, so the loads of the next pair are in
+// flight during this pair's transforms and projection (the twiddle table is then kept as {c, s}
+// to stay at four blocks per SM).
+template <bool STAGED = false> struct XpCfg {
   static constexpr int N = 512, THREADS = 96;
   static constexpr size_t SPEC_BYTES = 3 * sizeof(float4) * N;        // three warps' rows
-  static constexpr size_t SMEM = SPEC_BYTES + sizeof(float4) * 512 + sizeof(float) * N;
+  static constexpr size_t TW_BYTES = (STAGED ? sizeof(float2) : sizeof(float4)) * 512;
+  static constexpr size_t STAGE_BYTES = STAGED ? 3 * 4 * sizeof(float) * N : 0;  // 4 planes a warp
+  static constexpr size_t SMEM = SPEC_BYTES + TW_BYTES + sizeof(float) * N + STAGE_BYTES;
 };
 
-template <int MINB>
-__global__ void __launch_bounds__(XpCfg::THREADS, MINB)
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)),
+               "l"(reinterpret_cast<unsigned long long>(gsrc))
+               : "memory");
+}
+
+template <int MINB, bool STAGED = false>
+__global__ void __launch_bounds__(XpCfg<STAGED>::THREADS, MINB)
 k_xproj_pair(const XTmaArgs a) {
-  using C = XpCfg;
+  using C = XpCfg<STAGED>;
   constexpr int N = C::N;
+  using TWE = typename std::conditional<STAGED, float2, float4>::type;
   extern __shared__ __align__(16) unsigned char smem_xp[];
   float4* spec = reinterpret_cast<float4*>(smem_xp);     // [warp][512]
-  float4* tw4 = spec + 3 * N;                            // W512^(l k1) as {c, c, s, s}
+  TWE* tw4 = reinterpret_cast<TWE*>(spec + 3 * N);       // W512^(l k1): {c, c, s, s} or {c, s}
   float* xix = reinterpret_cast<float*>(tw4 + 512);
+  float* stage = xix + N;                                // STAGED: [warp][re A, im A, re B, im B][N]
   __shared__ double red[32 * 4];
 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -279,7 +296,8 @@ k_xproj_pair(const XTmaArgs a) {
     const float2* src = reinterpret_cast<const float2*>(reinterpret_cast<const float*>(a.tws) + 2 * TWS);
     for (int i = tid; i < 512; i += blockDim.x) {
       const float2 t = src[i];
-      tw4[i] = make_float4(t.x, t.x, t.y, t.y);
+      if constexpr (STAGED) tw4[i] = t;
+      else tw4[i] = make_float4(t.x, t.x, t.y, t.y);
     }
     for (int i = tid; i < N; i += blockDim.x) xix[i] = reinterpret_cast<const float*>(a.xi_x)[i];
   }
@@ -296,6 +314,23 @@ k_xproj_pair(const XTmaArgs a) {
   const int kap = lane >> 1, hh = lane & 1;
   float* pre = fdata + (2LL * w) * a.V;                  // this warp's field: planes 2 w, 2 w + 1
   float* pim = pre + a.V;
+  float* wst = stage + w * 4 * N;                        // STAGED: this warp's staging planes
+  // STAGED: this warp's rows of row pair g into the staging planes (16-byte copies)
+  auto stage_rows = [&](int g) {
+    const int rA = a.pairs[g];
+    const int kz = rA / a.ny, ky = rA - kz * a.ny;
+    const int rB = (kz == 0 ? 0 : a.nz - kz) * a.ny + (ky == 0 ? 0 : a.ny - ky);
+    const long long o[2] = {(long long)rA * N, (long long)rB * N};
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int chunk = lane + 32 * i;                   // 512 chunks of 4 floats: plane, offset
+      const int pl = chunk >> 7, off = (chunk & 127) * 4;
+      const float* src = (pl & 1 ? pim : pre) + o[pl >> 1] + off;
+      if (in_bounds(o[pl >> 1] + off + 3, a.V, a.err)) cp_async16(wst + pl * N + off, src);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (STAGED && (int)blockIdx.x < a.npairs) stage_rows(blockIdx.x);
 
   Kahan<float> r2, di2, do2, o2;
   for (int g = blockIdx.x; g < a.npairs; g += gridDim.x) {
@@ -306,13 +341,25 @@ k_xproj_pair(const XTmaArgs a) {
     const long long oA = (long long)rA * N, oB = (long long)rB * N;
     {
       CPair v[16];
+      if constexpr (STAGED) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int p = lane + 32 * e;
-        const bool okA = in_bounds(oA + p, a.V, a.err), okB = in_bounds(oB + p, a.V, a.err);
-        const float ra = okA ? pre[oA + p] : 0.f, ia = okA ? pim[oA + p] : 0.f;
-        const float rb = self || !okB ? ra : pre[oB + p], ib = self || !okB ? ia : pim[oB + p];
-        v[e] = CPair{make_float2(ra, rb), make_float2(ia, ib)};
+        for (int e = 0; e < 16; ++e) {
+          const int p = lane + 32 * e;
+          v[e] = CPair{make_float2(wst[p], wst[2 * N + p]), make_float2(wst[N + p], wst[3 * N + p])};
+        }
+        __syncwarp();                                    // staging read: refill with the next pair
+        if (g + (int)gridDim.x < a.npairs) stage_rows(g + gridDim.x);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int p = lane + 32 * e;
+          const bool okA = in_bounds(oA + p, a.V, a.err), okB = in_bounds(oB + p, a.V, a.err);
+          const float ra = okA ? pre[oA + p] : 0.f, ia = okA ? pim[oA + p] : 0.f;
+          const float rb = self || !okB ? ra : pre[oB + p], ib = self || !okB ? ia : pim[oB + p];
+          v[e] = CPair{make_float2(ra, rb), make_float2(ia, ib)};
+        }
       }
       fft512_pair<false>(v, lane, wrow, tw4);
 #pragma unroll
