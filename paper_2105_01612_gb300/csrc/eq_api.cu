@@ -613,9 +613,8 @@ eq_status enqueue_passes(eq_plan* p, const void* d_in, void* d_final, cudaStream
   mark(3);
   // potential x pass (reads the spectrum before the projector rewrites it): the warp-per-row
   // kernel when the x pass runs it and the buffers allow bulk copies, else the plain-load kernel
-  // (the packed two-row x pass, variant 7, has no potential form: the row kernel 4 runs it)
-  const int pot_vx = p->vx >= 7 ? 4 : p->vx;
-  const bool pot_warp = d_y && p->tma_x && pot_vx >= 2 && pot_vx <= 6 &&
+  const int pot_vx = p->vx;
+  const bool pot_warp = d_y && p->tma_x && pot_vx >= 2 && pot_vx <= 8 &&
                         !(reinterpret_cast<uintptr_t>(d_out) & 15) &&
                         !(reinterpret_cast<uintptr_t>(d_y) & 15);
   if (pot_warp) {

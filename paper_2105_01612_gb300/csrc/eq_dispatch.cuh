@@ -250,21 +250,27 @@ template <typename T, int N, int MINB, bool STAGED = false> struct XpInst {
       out->box = 0;
       out->smem = C::SMEM;
       const void* f = reinterpret_cast<const void*>(&k_xproj_pair<MINB, STAGED>);
-      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
+      const void* fp = reinterpret_cast<const void*>(&k_xproj_pair<MINB, STAGED, true>);
+      cudaError_t e = cudaSuccess;
+      for (const void* g : {f, fp}) {
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(g, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared);
+      }
       int bl = 0;
       if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, f, C::THREADS, C::SMEM);
       out->blocks_per_sm = bl;
       return e;
     }
   }
-  static cudaError_t launch(const XTmaArgs& a, dim3 grid, cudaStream_t s) {
+  static cudaError_t launch(const XTmaArgs& a, dim3 grid, cudaStream_t s, bool pot = false) {
     if constexpr (!OK) {
       return cudaErrorInvalidValue;
     } else {
-      k_xproj_pair<MINB, STAGED><<<grid, C::THREADS, C::SMEM, s>>>(a);
+      if (pot) k_xproj_pair<MINB, STAGED, true><<<grid, C::THREADS, C::SMEM, s>>>(a);
+      else k_xproj_pair<MINB, STAGED><<<grid, C::THREADS, C::SMEM, s>>>(a);
       return cudaGetLastError();
     }
   }
@@ -363,13 +369,15 @@ template <typename T> cudaError_t xtma_info_t(int n, int v, TmaInfo* out) {
     default: return cudaErrorInvalidValue;
   }
 }
-// potential x pass in the warp-per-row kernels (variants 2 to 6 only)
+// potential x pass in the warp-per-row and packed two-row kernels (variants 2 to 8)
 template <typename T> cudaError_t xpot_warp_t(int n, int v, const XTmaArgs& a, dim3 grid, cudaStream_t s) {
-  if (v < 2 || v > 6) return cudaErrorInvalidValue;
+  if (v < 2 || v > 8) return cudaErrorInvalidValue;
   switch (n) {
 #define EQ_CASE(N)                                                                     \
   case N:                                                                                \
-    return v == 6   ? XrInst<T, N, XW_MINB<T>(3), true>::launch(a, grid, s, true)       \
+    return v == 8   ? XpInst<T, N, 4, true>::launch(a, grid, s, true)                   \
+           : v == 7 ? XpInst<T, N, 5>::launch(a, grid, s, true)                         \
+           : v == 6 ? XrInst<T, N, XW_MINB<T>(3), true>::launch(a, grid, s, true)       \
            : v == 5 ? XrInst<T, N, XW_MINB<T>(5)>::launch(a, grid, s, true)             \
            : v == 4 ? XrInst<T, N, XW_MINB<T>(4)>::launch(a, grid, s, true)             \
            : v == 3 ? XwInst<T, N, XW_MINB<T>(4)>::launch(a, grid, s, true)             \

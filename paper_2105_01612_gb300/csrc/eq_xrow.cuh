@@ -277,7 +277,11 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
                : "memory");
 }
 
-template <int MINB, bool STAGED = false>
+// POT: the potential x pass of eq_project_hodge instead (reads the stress spectrum and does not
+// write it; forms y's spectra per mode pair with potential_pair in the rows of fields 0 and 1,
+// y0 + i y1 and y2 + i 0, rows A and B as pairs; warps 0 and 1 store their inverse transforms
+// into the 4-plane y buffer; no norm partials).
+template <int MINB, bool STAGED = false, bool POT = false>
 __global__ void __launch_bounds__(XpCfg<STAGED>::THREADS, MINB)
 k_xproj_pair(const XTmaArgs a) {
   using C = XpCfg<STAGED>;
@@ -386,8 +390,19 @@ k_xproj_pair(const XTmaArgs a) {
         bv[c] = make_float2(self ? e2[c].x : e2[c].y, self ? e2[c].z : e2[c].w);
       }
       const bool same = kx == kxm;                       // kx = 0 or N / 2
-      project_pair<float>(av, bv, xix[kx], xi_y, xi_z, rA == 0 && kx == 0, zm, a.nyq_zero != 0,
-                          a.compat != 0, inv_v, (self && same) ? 1.f : 2.f, pr2, pdi2, pdo2, po2);
+      if constexpr (POT) {
+        // y replaces the spectra of fields 0 and 1, laid out as the projection's outputs below
+        float2 yk[2], ym[2];
+        potential_pair<float>(av, bv, xix[kx], xi_y, xi_z, inv_v, yk, ym);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          av[c] = yk[c];
+          bv[c] = ym[c];
+        }
+      } else {
+        project_pair<float>(av, bv, xix[kx], xi_y, xi_z, rA == 0 && kx == 0, zm, a.nyq_zero != 0,
+                            a.compat != 0, inv_v, (self && same) ? 1.f : 2.f, pr2, pdi2, pdo2, po2);
+      }
       if (self) {
         // one row: the pair's outputs are that row at kx and at kxm (copied into both halves)
 #pragma unroll
@@ -406,8 +421,18 @@ k_xproj_pair(const XTmaArgs a) {
           av2[c] = make_float2(e2[c].x, e2[c].z);
           bv2[c] = make_float2(e1[c].y, e1[c].w);
         }
-        project_pair<float>(av2, bv2, xix[kxm], xi_y, xi_z, false, zm, a.nyq_zero != 0,
-                            a.compat != 0, inv_v, 2.f, pr2, pdi2, pdo2, po2);
+        if constexpr (POT) {
+          float2 yk[2], ym[2];
+          potential_pair<float>(av2, bv2, xix[kxm], xi_y, xi_z, inv_v, yk, ym);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            av2[c] = yk[c];
+            bv2[c] = ym[c];
+          }
+        } else {
+          project_pair<float>(av2, bv2, xix[kxm], xi_y, xi_z, false, zm, a.nyq_zero != 0,
+                              a.compat != 0, inv_v, 2.f, pr2, pdi2, pdo2, po2);
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           e1[c] = make_float4(av[c].x, bv2[c].x, av[c].y, bv2[c].y);
@@ -415,7 +440,7 @@ k_xproj_pair(const XTmaArgs a) {
         }
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+      for (int c = 0; c < (POT ? 2 : 3); ++c) {
         spec[c * N + j1] = e1[c];
         if (!same) spec[c * N + j2] = e2[c];
       }
@@ -425,7 +450,10 @@ k_xproj_pair(const XTmaArgs a) {
     do2.add(pdo2.s);
     o2.add(po2.s);
     __syncthreads();
-    {
+    if (!(POT && w == 2)) {                              // warp-uniform: no y row for warp 2
+      float* dre = POT ? reinterpret_cast<float*>(a.ydata) + field * a.yfield_stride + (2LL * w) * a.V
+                       : pre;
+      float* dim = dre + a.V;
       CPair v[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
@@ -437,21 +465,23 @@ k_xproj_pair(const XTmaArgs a) {
       for (int q = 0; q < 16; ++q) {
         const int p = kap + 16 * q + 256 * hh;
         if (!in_bounds(oA + p, a.V, a.err) || !in_bounds(oB + p, a.V, a.err)) continue;
-        pre[oA + p] = v[q].r.x;
-        pim[oA + p] = v[q].i.x;
+        dre[oA + p] = v[q].r.x;
+        dim[oA + p] = v[q].i.x;
         if (!self) {
-          pre[oB + p] = v[q].r.y;
-          pim[oB + p] = v[q].i.y;
+          dre[oB + p] = v[q].r.y;
+          dim[oB + p] = v[q].i.y;
         }
       }
       __syncwarp();                                      // the row buffer is free for the next pair
     }
   }
-  double v4[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
-  block_sum<4>(v4, red);
-  if (tid == 0) {
-    double* q = a.partials + ((long long)field * gridDim.x + blockIdx.x) * 4;
-    q[0] = v4[0]; q[1] = v4[1]; q[2] = v4[2]; q[3] = v4[3];
+  if constexpr (!POT) {
+    double v4[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
+    block_sum<4>(v4, red);
+    if (tid == 0) {
+      double* q = a.partials + ((long long)field * gridDim.x + blockIdx.x) * 4;
+      q[0] = v4[0]; q[1] = v4[1]; q[2] = v4[2]; q[3] = v4[3];
+    }
   }
 }
 
