@@ -140,7 +140,8 @@ k_gen_finalize_norms(const double* __restrict__ partx, const long long* __restri
 // ---- plan ------------------------------------------------------------------------------
 
 struct PassShape {
-  int kind = 0;            // 0 strided fwd, 1 strided inv, 2 x
+  int kind = 0;            // strided passes: 0 (k_gen_strided) or 4 (k_gen_scols), the inverse
+                           // launching kind + 1; x pass: 2 (k_gen_xproj) or 3 (k_gen_xrows)
   int cols = 16, pitch = 16, tpi = 1, threads = 256, mmax = 1, grid = 1;
   size_t smem = 0;
   long long nitems = 0;
@@ -487,8 +488,13 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
   }
   // pass shapes: the tuning cache if it knows this plan, else the defaults
   GenTune t = gen_default_tune(g);
-  gen_cache_lookup(g, &t);
-  eq_status st = gen_configure(g, t, err);
+  eq_status st = EQ_ERR_INVALID;
+  if (gen_cache_lookup(g, &t)) {
+    std::string stale;
+    st = gen_configure(g, t, &stale);                      // an entry that no longer fits is
+    if (st != EQ_OK) t = gen_default_tune(g);              // passed over for the defaults
+  }
+  if (st != EQ_OK) st = gen_configure(g, t, err);
   if (st != EQ_OK) {
     gen_destroy(g);
     return st;
@@ -504,11 +510,21 @@ bool xrows_supported(const GenPlan* g) {
   return true;
 }
 
+// Every field's length on this axis (1 = y, 2 = z) is served by the warp-per-column strided
+// kernel (the same 256- or 512-point register transforms).
+bool scols_supported(const GenPlan* g, int axis) {
+  for (const FieldDesc& fd : g->fh)
+    if (g->ah[fd.ax[axis]].wm == 0) return false;
+  return true;
+}
+
 GenTune gen_default_tune(const GenPlan* g) {
   const size_t es = g->dtype == EQ_F32 ? 4 : 8;
   GenTune t;
   t.zc = es == 4 ? (g->mx[2] > 256 ? 8 : 16) : (g->mx[2] > 256 ? 4 : 8);
   t.yc = es == 4 ? (g->mx[1] > 256 ? 8 : 16) : (g->mx[1] > 256 ? 4 : 8);
+  if (es == 4 && scols_supported(g, 2)) t.zc = 0;
+  if (es == 4 && scols_supported(g, 1)) t.yc = 0;
   t.zt = t.yt = 256;
   t.xp = xrows_supported(g) ? 0 : (g->mx[0] > 256 ? 1 : 2);
   return t;
@@ -522,6 +538,15 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
   PassShape z = g->z, y = g->y, x = g->x;
   z.kind = 0; z.mmax = g->mx[2]; z.cols = t.zc; z.pitch = t.zc; z.threads = t.zt;
   y.kind = 0; y.mmax = g->mx[1]; y.cols = t.yc; y.pitch = t.yc; y.threads = t.yt;
+  for (int axis = 1; axis <= 2; ++axis) {
+    PassShape& p = axis == 2 ? z : y;
+    if ((axis == 2 ? t.zc : t.yc) != 0) continue;
+    if (!scols_supported(g, axis)) {
+      *err = "strided pass: the warp-per-column kernel serves lengths up to 256 and 512 only";
+      return EQ_ERR_INVALID;
+    }
+    p.kind = 4; p.cols = SC_COLS; p.pitch = SC_PITCH; p.threads = SC_THREADS;
+  }
   if (t.xp == 0 && !xrows_supported(g)) {
     *err = "x pass: the warp-per-row kernel serves x lengths up to 256 and 512 only";
     return EQ_ERR_INVALID;
@@ -533,8 +558,9 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
   }
   PassShape* ps[3] = {&z, &y, &x};
   for (PassShape* p : ps) {
-    p->smem = p->kind == 3 ? (g->dtype == EQ_F32 ? xrows_smem<float>() : xrows_smem<double>())
-                           : (2 * (size_t)p->mmax * p->pitch + 3 * (size_t)p->mmax) * cs;
+    p->smem = p->kind == 3   ? (g->dtype == EQ_F32 ? xrows_smem<float>() : xrows_smem<double>())
+              : p->kind == 4 ? (g->dtype == EQ_F32 ? scols_smem<float>() : scols_smem<double>())
+                             : (2 * (size_t)p->mmax * p->pitch + 3 * (size_t)p->mmax) * cs;
     if (p->smem > limit || p->threads > 512 || p->threads % p->cols != 0 || p->cols < 1) {
       *err = "pass shape does not fit (tile columns, threads or shared memory)";
       return EQ_ERR_INVALID;
@@ -545,8 +571,8 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
   for (int pi = 0; pi < 3; ++pi) {
     PassShape* p = ps[pi];
     int blocks = 0;
-    cudaError_t e = occupancy(g->dtype, pi == 2 ? p->kind : 0, p->threads, p->smem, &blocks);
-    if (e == cudaSuccess) e = occupancy(g->dtype, pi == 2 ? p->kind : 1, p->threads, p->smem, &blocks);
+    cudaError_t e = occupancy(g->dtype, p->kind, p->threads, p->smem, &blocks);
+    if (e == cudaSuccess && pi < 2) e = occupancy(g->dtype, p->kind + 1, p->threads, p->smem, &blocks);
     if (e != cudaSuccess || blocks < 1) {
       cudaGetLastError();
       *err = std::string("occupancy: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "0 blocks");
@@ -642,7 +668,7 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   // z forward (d_in -> d_out) with input statistics
   shape(g->z);
   a.in = d_in; a.out = d_out; a.ref = nullptr; a.partials = g->part_first; a.axis = 2; a.mode = 1;
-  if ((e = launch(0, a, g->z)) != cudaSuccess) { *err = std::string("z forward: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
+  if ((e = launch(g->z.kind, a, g->z)) != cudaSuccess) { *err = std::string("z forward: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
   mark(1);
   k_gen_finalize_mean<<<g->F, FIN_THREADS, 0, s>>>(g->part_first, g->z.item0, g->fields, g->F,
                                                    g->mean, g->instats);
@@ -650,7 +676,7 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   mark(2);
   shape(g->y);
   a.in = d_out; a.partials = nullptr; a.axis = 1; a.mode = 0;
-  if ((e = launch(0, a, g->y)) != cudaSuccess) { *err = std::string("y forward: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
+  if ((e = launch(g->y.kind, a, g->y)) != cudaSuccess) { *err = std::string("y forward: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
   mark(3);
   shape(g->x);
   a.partials = g->part_x; a.mode = 0;
@@ -658,12 +684,12 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   mark(4);
   shape(g->y);
   a.partials = nullptr; a.axis = 1; a.mode = 0;
-  if ((e = launch(1, a, g->y)) != cudaSuccess) { *err = std::string("y inverse: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
+  if ((e = launch(g->y.kind + 1, a, g->y)) != cudaSuccess) { *err = std::string("y inverse: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
   mark(5);
   const bool linf = g->opts.want_linf && d_in != d_out;
   shape(g->z);
   a.ref = linf ? d_in : nullptr; a.partials = g->part_last; a.axis = 2; a.mode = linf ? 2 : 0;
-  if ((e = launch(1, a, g->z)) != cudaSuccess) { *err = std::string("z inverse: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
+  if ((e = launch(g->z.kind + 1, a, g->z)) != cudaSuccess) { *err = std::string("z inverse: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
   mark(6);
   k_gen_finalize_norms<<<g->F, FIN_THREADS, 0, s>>>(
       g->part_x, g->x.item0, linf ? g->part_last : nullptr, g->z.item0, g->fields, g->F, g->mean,
@@ -767,7 +793,7 @@ static float time_pass(GenPlan* g, int which, const void* d_in, void* d_out, cud
   a.axis = which == 0 ? 2 : 1;
   a.mode = which == 0 ? 1 : 0;
   a.partials = which == 0 ? g->part_first : (which == 2 ? g->part_x : nullptr);
-  const int kind = which == 2 ? g->x.kind : 0;
+  const int kind = p.kind;
   float best[3];
   for (int r = 0; r < 4; ++r) {
     cudaEventRecord(e0, s);
@@ -801,6 +827,11 @@ eq_status gen_autotune(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s
           if (which == 0) { u.zc = c; u.zt = t; } else { u.yc = c; u.yt = t; }
           cands.push_back(u);
         }
+      if (scols_supported(g, which == 0 ? 2 : 1)) {      // the warp-per-column kernel
+        GenTune u = best;
+        if (which == 0) { u.zc = 0; u.zt = SC_THREADS; } else { u.yc = 0; u.yt = SC_THREADS; }
+        cands.push_back(u);
+      }
     } else {
       for (int xp : {0, 1, 2, 3}) {
         GenTune u = best;

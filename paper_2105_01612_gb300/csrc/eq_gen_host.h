@@ -18,8 +18,9 @@ struct GenPlan;
 
 // Tunable pass shapes of the runtime-length path.
 struct GenTune {
-  int zc = 16, zt = 256;   // z pass: tile columns, threads per block
-  int yc = 16, yt = 256;   // y pass
+  int zc = 16, zt = 256;   // z pass: tile columns, threads per block; zc = 0 selects the
+                           // warp-per-column kernel (k_gen_scols, its own block shape)
+  int yc = 16, yt = 256;   // y pass, the same
   int xp = 2;              // x pass: row pairs per block (6 xp transforms, 32 threads each) of
                            // the shared-memory kernel; 0 = the warp-per-row kernel (k_gen_xrows)
 };

@@ -9,6 +9,8 @@ template <typename T> struct GenInst {
     if (kind == 0) return reinterpret_cast<const void*>(&k_gen_strided<T, false>);
     if (kind == 1) return reinterpret_cast<const void*>(&k_gen_strided<T, true>);
     if (kind == 3) return reinterpret_cast<const void*>(&k_gen_xrows<T>);
+    if (kind == 4) return reinterpret_cast<const void*>(&k_gen_scols<T, false>);
+    if (kind == 5) return reinterpret_cast<const void*>(&k_gen_scols<T, true>);
     return reinterpret_cast<const void*>(&k_gen_xproj<T>);
   }
   static cudaError_t occupancy(int kind, int threads, size_t smem, int* blocks) {
@@ -27,6 +29,8 @@ template <typename T> struct GenInst {
     if (kind == 0) k_gen_strided<T, false><<<grid, threads, smem, s>>>(a);
     else if (kind == 1) k_gen_strided<T, true><<<grid, threads, smem, s>>>(a);
     else if (kind == 3) k_gen_xrows<T><<<grid, threads, smem, s>>>(a);
+    else if (kind == 4) k_gen_scols<T, false><<<grid, threads, smem, s>>>(a);
+    else if (kind == 5) k_gen_scols<T, true><<<grid, threads, smem, s>>>(a);
     else k_gen_xproj<T><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
   }

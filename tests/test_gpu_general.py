@@ -1,5 +1,6 @@
 """Parity of the runtime-length path (mixed radix 2..13 and Bluestein) and of uneven batches
 (one launch per pass over all fields) with the FP64 CPU oracle."""
+import json
 import math
 
 import numpy as np
@@ -154,4 +155,43 @@ def test_pass_timing_covers_the_asked_calls_then_turns_off(dims):
     assert n2 == 0
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
+    plan.close()
+
+
+def test_every_pass_kernel_choice_matches_the_oracle(tmp_path, monkeypatch):
+    """The tuning cache picks each pass's kernel: the shared-memory strided kernel or the
+    warp-per-column one (z, y), the shared-memory x kernel or the warp-per-row one.  Every
+    combination gives the oracle's result on lengths served directly (256) and by Bluestein
+    (18..130 through 256- and 512-point transforms); an entry that does not fit is passed over."""
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("EQ_TUNE_CACHE", str(cache))
+    dims = [(24, 20, 18), (33, 16, 40), (64, 12, 10), (130, 5, 256), (7, 256, 129)]
+    fields = [voronoi_stress_field((nz, ny, nx), 6, 100.0, 5.0, 7100 + i, dtype=torch.float32)
+              for i, (nx, ny, nz) in enumerate(dims)]
+    refs = [oracle.project(f.double().numpy(), "ddo") for f in fields]
+    plan = eq.VarlenPlan(dims, torch.float32, "ddo")
+    flat = plan.pack([f.cuda() for f in fields])
+    out = torch.empty_like(flat)
+    plan.autotune(flat, out)
+    plan.close()
+    key = json.loads(cache.read_text())
+    assert len(key) == 1
+    key = next(iter(key))
+    for zc, yc, xp in [(0, 0, 0), (16, 16, 2), (0, 8, 2), (8, 0, 0), (0, 0, 1)]:
+        cache.write_text(json.dumps({key: [zc, 256, yc, 256, xp]}))
+        plan = eq.VarlenPlan(dims, torch.float32, "ddo")
+        out = torch.empty_like(flat)
+        plan.project(flat, out)
+        nrm = plan.norms()
+        for i, (o, r) in enumerate(zip(plan.unpack(out), refs)):
+            assert rel(o.double().cpu().numpy(), r) <= 2e-6, (zc, yc, xp, dims[i])
+            assert nrm[i]["div_out_l2"] <= 1e-5 * nrm[i]["div_in_l2"]
+        plan.close()
+    # a stale entry (a shape that does not fit) falls back to the default shapes
+    cache.write_text(json.dumps({key: [999, 256, 0, 256, 0]}))
+    plan = eq.VarlenPlan(dims, torch.float32, "ddo")
+    out = torch.empty_like(flat)
+    plan.project(flat, out)
+    for o, r in zip(plan.unpack(out), refs):
+        assert rel(o.double().cpu().numpy(), r) <= 2e-6
     plan.close()
