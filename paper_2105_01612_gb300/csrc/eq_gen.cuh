@@ -15,6 +15,7 @@
 
 #include "../../include/eq.h"
 #include "eq_kernels.cuh"
+#include "eq_fft_pair.cuh"
 
 namespace eqg {
 
@@ -79,6 +80,8 @@ struct GenArgs {
   int nyq_zero;
   int compat;              // 1: return the compatible part c0 + (S - S_equil)
   int* err;                // plan error word (bounds-checked builds)
+  int tw256;               // complex pool: staged twiddles of length 256 (k_gen_scols)
+  int w512;                // complex pool: W512^j, j < 256 (k_gen_scols)
 };
 
 // ---- small DFTs -------------------------------------------------------------------------
@@ -427,86 +430,177 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
   }
 }
 
-// ---- strided pass, a warp per column (lengths served by a 256- or 512-point register transform) --
+// ---- strided pass, a warp per column (lengths served by a 256- or 512-point transform) ------
 //
-// Same items, partial records and modes as k_gen_strided.  A tile of SC_COLS adjacent columns
-// (n points each) comes into shared memory by coalesced loads (SC_COLS consecutive elements of a
-// plane per point), eight loads in flight a thread; each warp then takes whole columns: lane l
-// holds points l + 32 e of a length-wm register transform (radix-8 stages through the warp's own
-// row), directly when n = wm, else Bluestein's convolution (pre-chirp, transform, product with
-// the chirp transform, inverse transform, post-chirp; the inverse direction by conjugation), and
-// writes the n outputs back into the tile, which leaves by coalesced stores (with the L-infinity
-// residual of the last pass).  All fields of a launch have their axis served (wm in {256, 512}).
-constexpr int SC_COLS = 16, SC_WARPS = 6, SC_THREADS = 32 * SC_WARPS, SC_PITCH = SC_COLS + 1;
+// FP32.  Same items, partial records and modes as k_gen_strided.  A tile of SC_COLS adjacent
+// columns (n points each) comes into shared memory by coalesced loads (SC_COLS consecutive
+// elements of a plane per point), eight loads in flight a thread; the warps then transform whole
+// columns with paired 256-point transforms (two sequences in one warp, packed two-lane
+// arithmetic, eq_fft_pair.cuh) and write the n outputs back into the tile, which leaves by
+// coalesced stores (with the L-infinity residual of the last pass).  Every field of a launch has
+// its axis served by a transform length wm in {256, 512}:
+//   wm = 256: a warp takes two adjacent columns as the pair, either transformed directly (n = 256)
+//     or by Bluestein's chirp-z convolution (n <= 128: pre-chirp, forward transform, product with
+//     the chirp transform, inverse transform, post-chirp);
+//   wm = 512: a warp takes one column at a time, its 512-point transform split into the 256-point
+//     transforms of the even and odd outputs (the decimation-in-frequency step
+//     a_j = u_j + u_{j+256}, b_j = (u_j - u_{j+256}) W512^j) as the pair.  Directly for n = 512;
+//     for Bluestein (n <= 256, so u_{j+256} = 0) the convolution's inverse transform needs only
+//     the outputs j < 256, y_j = P_j + W512^-j Q_j from the inverse transforms P, Q of the even
+//     and odd halves of the product.
+// The inverse direction of a Bluestein length goes by conjugation of input and output.
+constexpr int SC_COLS = 16, SC_WARPS = 8, SC_THREADS = 32 * SC_WARPS, SC_PITCH = SC_COLS + 1;
 constexpr int SC_MAXN = 512;          // longest column (n = wm = 512)
-template <typename T> constexpr size_t scols_smem() {
-  return 2 * sizeof(T) * (size_t(SC_MAXN) * SC_PITCH + 256 + 512) +   // tile, chirp, chirp transform
-         sizeof(T) * (size_t(SC_WARPS) * 2 * 512 + 2 * eqk::staged_size(512));
+constexpr size_t scols_smem() {
+  return sizeof(float4) * size_t(SC_WARPS) * 256 +                          // exchange rows
+         sizeof(float2) * (size_t(SC_MAXN) * SC_PITCH + 256 + 512 + 256) +   // tile, chirp, chirp
+                                                                             // transform, W512^j
+         2 * sizeof(float) * size_t(eqk::staged_size(256));                 // staged twiddles
 }
 
-template <typename T, int M, bool INV>
-__device__ __forceinline__ void scol_transform(typename eqk::V2<T>::t* tile, int col, int n,
-                                               const eqk::SoaAcc<T>& acc,
-                                               const eqk::TwStaged<T>& tw,
-                                               const typename eqk::V2<T>::t* chs,
-                                               const typename eqk::V2<T>::t* bhs, int* err) {
-  using T2 = typename eqk::V2<T>::t;
-  constexpr int E = M / 32;
-  const int lane = threadIdx.x & 31;
-  const bool blue = n != M;
-  T2 x[E];
+__device__ __forceinline__ eqk::CPair cpair(float2 a, float2 b) {
+  return eqk::CPair{make_float2(a.x, b.x), make_float2(a.y, b.y)};
+}
+__device__ __forceinline__ float2 pair_lo(const eqk::CPair& v) { return make_float2(v.r.x, v.i.x); }
+__device__ __forceinline__ float2 pair_hi(const eqk::CPair& v) { return make_float2(v.r.y, v.i.y); }
+// lane 0 times w0, lane 1 times w1 (complex)
+__device__ __forceinline__ eqk::CPair pmul_lanes(eqk::CPair v, float2 w0, float2 w1) {
+  const float2 C = make_float2(w0.x, w1.x), S = make_float2(w0.y, w1.y);
+  return eqk::CPair{eqk::fsub2(__fmul2_rn(v.r, C), __fmul2_rn(v.i, S)),
+                    __ffma2_rn(v.r, S, __fmul2_rn(v.i, C))};
+}
+
+// One column (wm = 512) through the even / odd split.  On entry no lane reads `acc`; on return the
+// column's n outputs are in the tile and `acc` is free.
+template <bool INV>
+__device__ __forceinline__ void scol512(float2* tile, int col, int n, const eqk::PairAcc& acc,
+                                        const eqk::TwStaged<float>& tw, const float2* w512,
+                                        const float2* chs, const float4* bhs2, int lane, int* err) {
+  const bool blue = n != 512;
+  eqk::CPair v[8];
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
+  for (int e = 0; e < 8; ++e) {
     const int j = lane + 32 * e;
-    x[e] = T2{T(0), T(0)};
-    if (j < n && eqk::in_bounds((long long)j * SC_PITCH + col, (long long)SC_MAXN * SC_PITCH, err)) {
-      x[e] = tile[j * SC_PITCH + col];
-      if (blue) {
-        if (INV) x[e].y = -x[e].y;
-        x[e] = cmul(x[e], chs[j]);
-      }
+    float2 u0 = make_float2(0.f, 0.f), u1 = make_float2(0.f, 0.f);
+    if (j < n && eqk::in_bounds((long long)j * SC_PITCH + col, (long long)SC_MAXN * SC_PITCH, err))
+      u0 = tile[j * SC_PITCH + col];
+    float2 w = w512[j];
+    if (blue) {
+      if (INV) u0.y = -u0.y;
+      u0 = cmul(u0, chs[j < n ? j : 0]);
+    } else {
+      u1 = tile[(j + 256) * SC_PITCH + col];
+      if (INV) w.y = -w.y;
     }
+    v[e] = cpair(cadd(u0, u1), cmul(csub(u0, u1), w));
   }
-  __syncwarp();                                             // the warp's row is free
   if (blue) {
-    eqk::fft_column_acc<M, E, false, 0, true>(x, lane, acc, tw);
+    eqk::pfft_column<256, 8, false>(v, lane, acc, tw);
 #pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = cmul(x[e], bhs[lane + 32 * e]);
-    __syncwarp();
-    eqk::fft_column_acc<M, E, true, 0, true>(x, lane, acc, tw);
-  } else {
-    eqk::fft_column_acc<M, E, INV, 0, true>(x, lane, acc, tw);
-  }
+    for (int e = 0; e < 8; ++e) {                 // U_{2k} (lane 0) and U_{2k+1} (lane 1) times b^
+      const float4 b = bhs2[lane + 32 * e];
+      v[e] = pmul_lanes(v[e], make_float2(b.x, b.y), make_float2(b.z, b.w));
+    }
+    eqk::pfft_column<256, 8, true>(v, lane, acc, tw);
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int k = lane + 32 * e;
-    if (k < n) {
-      T2 y = x[e];
-      if (blue) {
-        y = cmul(y, chs[k]);
+    for (int e = 0; e < 8; ++e) {
+      const int j = lane + 32 * e;
+      if (j < n) {
+        const float2 w = w512[j];
+        float2 y = cadd(pair_lo(v[e]), cmul(pair_hi(v[e]), make_float2(w.x, -w.y)));
+        y = cmul(y, chs[j]);
         if (INV) y.y = -y.y;
+        tile[j * SC_PITCH + col] = y;
       }
-      tile[k * SC_PITCH + col] = y;
+    }
+  } else {
+    eqk::pfft_column<256, 8, INV>(v, lane, acc, tw);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {                 // outputs 2k and 2k + 1, k = lane + 32 e
+      const int k = lane + 32 * e;
+      tile[(2 * k) * SC_PITCH + col] = pair_lo(v[e]);
+      tile[(2 * k + 1) * SC_PITCH + col] = pair_hi(v[e]);
     }
   }
-  __syncwarp();
 }
 
-template <typename T, bool INV>
+// Columns c0 and c0 + 1 (wm = 256) as the pair.
+template <bool INV>
+__device__ __forceinline__ void scol256(float2* tile, int c0, int n, const eqk::PairAcc& acc,
+                                        const eqk::TwStaged<float>& tw, const float2* chs,
+                                        const float2* bhs, int lane, int* err) {
+  const bool blue = n != 256;
+  eqk::CPair v[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int j = lane + 32 * e;
+    float2 x0 = make_float2(0.f, 0.f), x1 = x0;
+    if (j < n && eqk::in_bounds((long long)j * SC_PITCH + c0 + 1, (long long)SC_MAXN * SC_PITCH, err)) {
+      x0 = tile[j * SC_PITCH + c0];
+      x1 = tile[j * SC_PITCH + c0 + 1];
+      if (blue) {
+        if (INV) { x0.y = -x0.y; x1.y = -x1.y; }
+        const float2 c = chs[j];
+        x0 = cmul(x0, c);
+        x1 = cmul(x1, c);
+      }
+    }
+    v[e] = cpair(x0, x1);
+  }
+  if (blue) {
+    eqk::pfft_column<256, 8, false>(v, lane, acc, tw);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float2 b = bhs[lane + 32 * e];
+      v[e] = eqk::pmul_cs(v[e], b.x, b.y);
+    }
+    eqk::pfft_column<256, 8, true>(v, lane, acc, tw);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int j = lane + 32 * e;
+      if (j < n) {
+        const float2 c = chs[j];
+        float2 y0 = cmul(pair_lo(v[e]), c), y1 = cmul(pair_hi(v[e]), c);
+        if (INV) { y0.y = -y0.y; y1.y = -y1.y; }
+        tile[j * SC_PITCH + c0] = y0;
+        tile[j * SC_PITCH + c0 + 1] = y1;
+      }
+    }
+  } else {
+    eqk::pfft_column<256, 8, INV>(v, lane, acc, tw);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = lane + 32 * e;
+      tile[k * SC_PITCH + c0] = pair_lo(v[e]);
+      tile[k * SC_PITCH + c0 + 1] = pair_hi(v[e]);
+    }
+  }
+}
+
+template <bool INV>
 __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
-  using T2 = typename eqk::V2<T>::t;
+  using T = float;
+  using T2 = float2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int TWS = eqk::staged_size(512);
-  T2* tile = reinterpret_cast<T2*>(smem_raw);               // [point][SC_PITCH]
-  T2* chs = tile + SC_MAXN * SC_PITCH;
-  T2* bhs = chs + 256;
-  T* rows = reinterpret_cast<T*>(bhs + 512);                // [warp][re 512 | im 512]
-  T* twc = rows + SC_WARPS * 2 * 512;
+  constexpr int TWS = eqk::staged_size(256);
+  float4* rows = reinterpret_cast<float4*>(smem_raw);      // [warp][256] exchange entries
+  T2* tile = reinterpret_cast<T2*>(rows + SC_WARPS * 256); // [point][SC_PITCH]
+  T2* chs = tile + SC_MAXN * SC_PITCH;                     // chirp (n <= 256)
+  T2* bhs = chs + 256;                                     // chirp transform (wm entries)
+  T2* w512 = bhs + 512;                                    // W512^j, j < 256
+  T* twc = reinterpret_cast<T*>(w512 + 256);
   T* tws = twc + TWS;
   const T2* cpool = reinterpret_cast<const T2*>(a.cpool);
-  const int tid = threadIdx.x, w = tid >> 5, nw = SC_WARPS;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int lc = tid % SC_COLS, lj = tid / SC_COLS, jstep = SC_THREADS / SC_COLS;
-  const eqk::SoaAcc<T> acc{rows + w * 2 * 512, rows + w * 2 * 512 + 512};
+  for (int i = tid; i < TWS; i += blockDim.x) {
+    const T2 t = cpool[a.tw256 + i];
+    twc[i] = t.x;
+    tws[i] = t.y;
+  }
+  for (int i = tid; i < 256; i += blockDim.x) w512[i] = cpool[a.w512 + i];
+  const eqk::TwStaged<T> tw{twc, tws};
+  const eqk::PairAcc acc{rows + w * 256};
   int cur_ax = -1;
   for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
     const int f = find_field(a.item0, a.nfields, item);
@@ -514,14 +608,8 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
     const int axi = fd.ax[a.axis];
     const AxisPlan& ap = a.axes[axi];
     const int n = ap.n, wm = ap.wm;
-    if (axi != cur_ax) {                  // tables of this axis length into shared memory
+    if (axi != cur_ax) {                  // chirp tables of this axis length into shared memory
       __syncthreads();
-      const int ts = eqk::staged_size(wm);
-      for (int i = tid; i < ts; i += blockDim.x) {
-        const T2 t = cpool[ap.wtw + i];
-        twc[i] = t.x;
-        tws[i] = t.y;
-      }
       if (wm != n) {
         for (int i = tid; i < n; i += blockDim.x) chs[i] = cpool[ap.wchirp + i];
         for (int i = tid; i < wm; i += blockDim.x) bhs[i] = cpool[ap.wbhat + i];
@@ -529,7 +617,6 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
       __syncthreads();
       cur_ax = axi;
     }
-    const eqk::TwStaged<T> tw{twc, tws};
     long long inner, nstride, outer_stride, ncols;
     if (a.axis == 2) { inner = (long long)fd.nx * fd.ny; nstride = inner; outer_stride = 0; ncols = inner; }
     else { inner = fd.nx; nstride = fd.nx; outer_stride = (long long)fd.nx * fd.ny; ncols = (long long)fd.nz * fd.nx; }
@@ -565,22 +652,25 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
 #pragma unroll
         for (int u = 0; u < LB; ++u) {
           const int j = jb + u * jstep;
-          if (j >= n) break;
-          const T2 x = xb[u];
-          if (a.mode == 1 && valid) {
-            if (!isfinite(x.x) || !isfinite(x.y)) nonfinite += T(1);
-            sa.add(x.x);
-            sb.add(x.y);
-            sq.add(wa * x.x * x.x + wb * x.y * x.y);
+          if (j < n) {
+            const T2 x = xb[u];
+            if (a.mode == 1 && valid) {
+              if (!isfinite(x.x) || !isfinite(x.y)) nonfinite += T(1);
+              sa.add(x.x);
+              sb.add(x.y);
+              sq.add(wa * x.x * x.x + wb * x.y * x.y);
+            }
+            tile[j * SC_PITCH + lc] = x;
           }
-          tile[j * SC_PITCH + lc] = x;
         }
       }
       __syncthreads();
-      for (int cc = w; cc < SC_COLS; cc += nw) {
-        if (tl * SC_COLS + cc >= ncols) continue;             // warp-uniform
-        if (wm == 512) scol_transform<T, 512, INV>(tile, cc, n, acc, tw, chs, bhs, a.err);
-        else scol_transform<T, 256, INV>(tile, cc, n, acc, tw, chs, bhs, a.err);
+      if (wm == 512) {
+        for (int cc = w; cc < SC_COLS; cc += SC_WARPS)
+          if (tl * SC_COLS + cc < ncols)                    // warp-uniform
+            scol512<INV>(tile, cc, n, acc, tw, w512, chs, reinterpret_cast<const float4*>(bhs), lane, a.err);
+      } else if (tl * SC_COLS + 2 * w < ncols) {
+        scol256<INV>(tile, 2 * w, n, acc, tw, chs, bhs, lane, a.err);
       }
       __syncthreads();
       // coalesced tile store (+ the residual of the last pass against the input)
@@ -599,15 +689,15 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
 #pragma unroll
           for (int u = 0; u < LB; ++u) {
             const int k = kb + u * jstep;
-            if (k >= n) break;
             const long long off = base + (long long)k * nstride;
-            if (!eqk::in_bounds(off, fd.V, a.err)) continue;
-            const T2 y = tile[k * SC_PITCH + lc];
-            out_re[off] = y.x;
-            out_im[off] = y.y;
-            if (ref_re) {
-              linf = fmax(linf, fabs(rb[u].x - y.x));
-              linf = fmax(linf, fabs(rb[u].y - y.y));
+            if (k < n && eqk::in_bounds(off, fd.V, a.err)) {
+              const T2 y = tile[k * SC_PITCH + lc];
+              out_re[off] = y.x;
+              out_im[off] = y.y;
+              if (ref_re) {
+                linf = fmax(linf, fabs(rb[u].x - y.x));
+                linf = fmax(linf, fabs(rb[u].y - y.y));
+              }
             }
           }
         }
@@ -617,14 +707,14 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
     if (a.mode == 1) {
       double v[4] = {sa.value(), sb.value(), sq.value(), double(nonfinite)};
       warp_partials<4>(v, a.partials + item * WARPS_MAX * 4);
-      for (int k = nw * 4 + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
+      for (int k = SC_WARPS * 4 + tid; k < WARPS_MAX * 4; k += blockDim.x)
         a.partials[item * WARPS_MAX * 4 + k] = 0.0;
     } else if (a.mode == 2) {
       double v = double(linf);
 #pragma unroll
       for (int o2 = 16; o2 > 0; o2 >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o2));
-      if ((threadIdx.x & 31) == 0) a.partials[item * WARPS_MAX * 4 + (threadIdx.x >> 5)] = v;
-      for (int k = nw + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
+      if (lane == 0) a.partials[item * WARPS_MAX * 4 + w] = v;
+      for (int k = SC_WARPS + tid; k < WARPS_MAX * 4; k += blockDim.x)
         a.partials[item * WARPS_MAX * 4 + k] = 0.0;
     }
   }

@@ -176,6 +176,7 @@ struct GenPlan {
   size_t wbytes = 0;
   GenTune tune;
   std::string key;             // tuning-cache key
+  int tw256 = -1, w512 = -1;   // complex-pool offsets of the paired-transform tables
 };
 
 namespace {
@@ -333,6 +334,12 @@ void build_tables(GenPlan* g, const std::vector<int>& lens, std::vector<unsigned
     axis_of_len[n] = (int)g->ah.size();
     g->ah.push_back(ap);
   }
+  // tables of the paired 256-point transforms of the warp-per-column strided kernel: staged
+  // twiddles of length 256 and W512^j (j < 256), the twiddle of a 512-point transform's
+  // even / odd split
+  g->tw256 = staged(256);
+  g->w512 = int(cpool.size() / (2 * sizeof(T)));
+  for (int j = 0; j < 256; ++j) push_complex<T>(cpool, std::polar(1.0, -two_pi * j / 512.0));
 }
 
 template <typename T>
@@ -510,9 +517,10 @@ bool xrows_supported(const GenPlan* g) {
   return true;
 }
 
-// Every field's length on this axis (1 = y, 2 = z) is served by the warp-per-column strided
-// kernel (the same 256- or 512-point register transforms).
+// An FP32 plan whose every field's length on this axis (1 = y, 2 = z) is served by the
+// warp-per-column strided kernel (transform length wm of 256 or 512).
 bool scols_supported(const GenPlan* g, int axis) {
+  if (g->dtype != EQ_F32) return false;                   // the kernel is FP32
   for (const FieldDesc& fd : g->fh)
     if (g->ah[fd.ax[axis]].wm == 0) return false;
   return true;
@@ -523,8 +531,8 @@ GenTune gen_default_tune(const GenPlan* g) {
   GenTune t;
   t.zc = es == 4 ? (g->mx[2] > 256 ? 8 : 16) : (g->mx[2] > 256 ? 4 : 8);
   t.yc = es == 4 ? (g->mx[1] > 256 ? 8 : 16) : (g->mx[1] > 256 ? 4 : 8);
-  if (es == 4 && scols_supported(g, 2)) t.zc = 0;
-  if (es == 4 && scols_supported(g, 1)) t.yc = 0;
+  if (scols_supported(g, 2)) t.zc = 0;
+  if (scols_supported(g, 1)) t.yc = 0;
   t.zt = t.yt = 256;
   t.xp = xrows_supported(g) ? 0 : (g->mx[0] > 256 ? 1 : 2);
   return t;
@@ -559,7 +567,7 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
   PassShape* ps[3] = {&z, &y, &x};
   for (PassShape* p : ps) {
     p->smem = p->kind == 3   ? (g->dtype == EQ_F32 ? xrows_smem<float>() : xrows_smem<double>())
-              : p->kind == 4 ? (g->dtype == EQ_F32 ? scols_smem<float>() : scols_smem<double>())
+              : p->kind == 4 ? scols_smem()
                              : (2 * (size_t)p->mmax * p->pitch + 3 * (size_t)p->mmax) * cs;
     if (p->smem > limit || p->threads > 512 || p->threads % p->cols != 0 || p->cols < 1) {
       *err = "pass shape does not fit (tile columns, threads or shared memory)";
@@ -658,6 +666,7 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   a.pairpool = g->pairpool; a.mean = g->mean; a.nfields = g->F;
   a.nyq_zero = g->opts.nyq == EQ_NYQ_ZERO;
   a.err = g->err;
+  a.tw256 = g->tw256; a.w512 = g->w512;
   a.compat = g->opts.target == EQ_TARGET_COMPATIBILITY;
   auto shape = [&](const PassShape& p) {
     a.item0 = p.item0; a.nitems = p.nitems; a.tiles_per_item = p.tpi; a.cols = p.cols;
@@ -784,6 +793,7 @@ static float time_pass(GenPlan* g, int which, const void* d_in, void* d_out, cud
   a.pairpool = g->pairpool; a.mean = g->mean; a.nfields = g->F;
   a.nyq_zero = g->opts.nyq == EQ_NYQ_ZERO;
   a.err = g->err;
+  a.tw256 = g->tw256; a.w512 = g->w512;
   a.compat = g->opts.target == EQ_TARGET_COMPATIBILITY;
   const PassShape& p = which == 0 ? g->z : (which == 1 ? g->y : g->x);
   a.item0 = p.item0; a.nitems = p.nitems; a.tiles_per_item = p.tpi; a.cols = p.cols;

@@ -1,5 +1,7 @@
 // eq_gen_inst.cuh - launch wrappers of the runtime-length passes, included once per dtype.
 #pragma once
+#include <type_traits>
+
 #include "eq_gen.cuh"
 
 namespace eqg {
@@ -9,8 +11,12 @@ template <typename T> struct GenInst {
     if (kind == 0) return reinterpret_cast<const void*>(&k_gen_strided<T, false>);
     if (kind == 1) return reinterpret_cast<const void*>(&k_gen_strided<T, true>);
     if (kind == 3) return reinterpret_cast<const void*>(&k_gen_xrows<T>);
-    if (kind == 4) return reinterpret_cast<const void*>(&k_gen_scols<T, false>);
-    if (kind == 5) return reinterpret_cast<const void*>(&k_gen_scols<T, true>);
+    if constexpr (std::is_same<T, float>::value) {       // the warp-per-column kernel is FP32
+      if (kind == 4) return reinterpret_cast<const void*>(&k_gen_scols<false>);
+      if (kind == 5) return reinterpret_cast<const void*>(&k_gen_scols<true>);
+    } else if (kind == 4 || kind == 5) {
+      return nullptr;
+    }
     return reinterpret_cast<const void*>(&k_gen_xproj<T>);
   }
   static cudaError_t occupancy(int kind, int threads, size_t smem, int* blocks) {
@@ -18,7 +24,7 @@ template <typename T> struct GenInst {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess && (size_t)optin < smem) return cudaErrorInvalidValue;
+    if (e == cudaSuccess && ((size_t)optin < smem || !fn(kind))) return cudaErrorInvalidValue;
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fn(kind), cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
@@ -29,8 +35,14 @@ template <typename T> struct GenInst {
     if (kind == 0) k_gen_strided<T, false><<<grid, threads, smem, s>>>(a);
     else if (kind == 1) k_gen_strided<T, true><<<grid, threads, smem, s>>>(a);
     else if (kind == 3) k_gen_xrows<T><<<grid, threads, smem, s>>>(a);
-    else if (kind == 4) k_gen_scols<T, false><<<grid, threads, smem, s>>>(a);
-    else if (kind == 5) k_gen_scols<T, true><<<grid, threads, smem, s>>>(a);
+    else if (kind == 4 || kind == 5) {
+      if constexpr (std::is_same<T, float>::value) {
+        if (kind == 4) k_gen_scols<false><<<grid, threads, smem, s>>>(a);
+        else k_gen_scols<true><<<grid, threads, smem, s>>>(a);
+      } else {
+        return cudaErrorInvalidValue;
+      }
+    }
     else k_gen_xproj<T><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
   }
