@@ -470,26 +470,27 @@ __device__ __forceinline__ eqk::CPair pmul_lanes(eqk::CPair v, float2 w0, float2
                     __ffma2_rn(v.r, S, __fmul2_rn(v.i, C))};
 }
 
-// One column (wm = 512) through the even / odd split.  On entry no lane reads `acc`; on return the
-// column's n outputs are in the tile and `acc` is free.
-template <bool INV>
-__device__ __forceinline__ void scol512(float2* tile, int col, int n, const eqk::PairAcc& acc,
-                                        const eqk::TwStaged<float>& tw, const float2* w512,
-                                        const float2* chs, const float4* bhs2, int lane, int* err) {
+// Length-n DFT of one sequence through the 512-point split (wm = 512: n = 512 directly, or
+// Bluestein for n <= 256).  in(j) gives x_j (j < n); out(k, X_k) takes the n outputs; INV: the
+// exponent's sign is +, unnormalised.  All reads of in() precede every call of out().  On entry no
+// lane reads `acc`; it is free again on return.
+template <bool INV, typename IN, typename OUT>
+__device__ __forceinline__ void dft_split512(int n, IN in, OUT out, const eqk::PairAcc& acc,
+                                             const eqk::TwStaged<float>& tw, const float2* w512,
+                                             const float2* chs, const float4* bhs2, int lane) {
   const bool blue = n != 512;
   eqk::CPair v[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int j = lane + 32 * e;
     float2 u0 = make_float2(0.f, 0.f), u1 = make_float2(0.f, 0.f);
-    if (j < n && eqk::in_bounds((long long)j * SC_PITCH + col, (long long)SC_MAXN * SC_PITCH, err))
-      u0 = tile[j * SC_PITCH + col];
+    if (j < n) u0 = in(j);
     float2 w = w512[j];
     if (blue) {
       if (INV) u0.y = -u0.y;
       u0 = cmul(u0, chs[j < n ? j : 0]);
     } else {
-      u1 = tile[(j + 256) * SC_PITCH + col];
+      u1 = in(j + 256);
       if (INV) w.y = -w.y;
     }
     v[e] = cpair(cadd(u0, u1), cmul(csub(u0, u1), w));
@@ -510,7 +511,7 @@ __device__ __forceinline__ void scol512(float2* tile, int col, int n, const eqk:
         float2 y = cadd(pair_lo(v[e]), cmul(pair_hi(v[e]), make_float2(w.x, -w.y)));
         y = cmul(y, chs[j]);
         if (INV) y.y = -y.y;
-        tile[j * SC_PITCH + col] = y;
+        out(j, y);
       }
     }
   } else {
@@ -518,26 +519,27 @@ __device__ __forceinline__ void scol512(float2* tile, int col, int n, const eqk:
 #pragma unroll
     for (int e = 0; e < 8; ++e) {                 // outputs 2k and 2k + 1, k = lane + 32 e
       const int k = lane + 32 * e;
-      tile[(2 * k) * SC_PITCH + col] = pair_lo(v[e]);
-      tile[(2 * k + 1) * SC_PITCH + col] = pair_hi(v[e]);
+      out(2 * k, pair_lo(v[e]));
+      out(2 * k + 1, pair_hi(v[e]));
     }
   }
 }
 
-// Columns c0 and c0 + 1 (wm = 256) as the pair.
-template <bool INV>
-__device__ __forceinline__ void scol256(float2* tile, int c0, int n, const eqk::PairAcc& acc,
-                                        const eqk::TwStaged<float>& tw, const float2* chs,
-                                        const float2* bhs, int lane, int* err) {
+// Length-n DFTs of two sequences at once (wm = 256: n = 256 directly, or Bluestein for
+// n <= 128); in0 / in1 and out0 / out1 as in dft_split512.
+template <bool INV, typename IN0, typename IN1, typename OUT0, typename OUT1>
+__device__ __forceinline__ void dft_pair256(int n, IN0 in0, IN1 in1, OUT0 out0, OUT1 out1,
+                                            const eqk::PairAcc& acc, const eqk::TwStaged<float>& tw,
+                                            const float2* chs, const float2* bhs, int lane) {
   const bool blue = n != 256;
   eqk::CPair v[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int j = lane + 32 * e;
     float2 x0 = make_float2(0.f, 0.f), x1 = x0;
-    if (j < n && eqk::in_bounds((long long)j * SC_PITCH + c0 + 1, (long long)SC_MAXN * SC_PITCH, err)) {
-      x0 = tile[j * SC_PITCH + c0];
-      x1 = tile[j * SC_PITCH + c0 + 1];
+    if (j < n) {
+      x0 = in0(j);
+      x1 = in1(j);
       if (blue) {
         if (INV) { x0.y = -x0.y; x1.y = -x1.y; }
         const float2 c = chs[j];
@@ -562,8 +564,8 @@ __device__ __forceinline__ void scol256(float2* tile, int c0, int n, const eqk::
         const float2 c = chs[j];
         float2 y0 = cmul(pair_lo(v[e]), c), y1 = cmul(pair_hi(v[e]), c);
         if (INV) { y0.y = -y0.y; y1.y = -y1.y; }
-        tile[j * SC_PITCH + c0] = y0;
-        tile[j * SC_PITCH + c0 + 1] = y1;
+        out0(j, y0);
+        out1(j, y1);
       }
     }
   } else {
@@ -571,10 +573,41 @@ __device__ __forceinline__ void scol256(float2* tile, int c0, int n, const eqk::
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int k = lane + 32 * e;
-      tile[k * SC_PITCH + c0] = pair_lo(v[e]);
-      tile[k * SC_PITCH + c0 + 1] = pair_hi(v[e]);
+      out0(k, pair_lo(v[e]));
+      out1(k, pair_hi(v[e]));
     }
   }
+}
+
+// A column of the tile (wm = 512), and columns c0, c0 + 1 (wm = 256), transformed in place.
+template <bool INV>
+__device__ __forceinline__ void scol512(float2* tile, int col, int n, const eqk::PairAcc& acc,
+                                        const eqk::TwStaged<float>& tw, const float2* w512,
+                                        const float2* chs, const float4* bhs2, int lane, int* err) {
+  const long long lim = (long long)SC_MAXN * SC_PITCH;
+  auto in = [&](int j) {
+    return eqk::in_bounds((long long)j * SC_PITCH + col, lim, err) ? tile[j * SC_PITCH + col]
+                                                                   : make_float2(0.f, 0.f);
+  };
+  auto out = [&](int k, float2 y) { tile[k * SC_PITCH + col] = y; };
+  dft_split512<INV>(n, in, out, acc, tw, w512, chs, bhs2, lane);
+}
+template <bool INV>
+__device__ __forceinline__ void scol256(float2* tile, int c0, int n, const eqk::PairAcc& acc,
+                                        const eqk::TwStaged<float>& tw, const float2* chs,
+                                        const float2* bhs, int lane, int* err) {
+  const long long lim = (long long)SC_MAXN * SC_PITCH;
+  auto in0 = [&](int j) {
+    return eqk::in_bounds((long long)j * SC_PITCH + c0 + 1, lim, err) ? tile[j * SC_PITCH + c0]
+                                                                      : make_float2(0.f, 0.f);
+  };
+  auto in1 = [&](int j) {
+    return eqk::in_bounds((long long)j * SC_PITCH + c0 + 1, lim, err) ? tile[j * SC_PITCH + c0 + 1]
+                                                                      : make_float2(0.f, 0.f);
+  };
+  auto out0 = [&](int k, float2 y) { tile[k * SC_PITCH + c0] = y; };
+  auto out1 = [&](int k, float2 y) { tile[k * SC_PITCH + c0 + 1] = y; };
+  dft_pair256<INV>(n, in0, in1, out0, out1, acc, tw, chs, bhs, lane);
 }
 
 template <bool INV>
@@ -717,6 +750,151 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
       for (int k = SC_WARPS + tid; k < WARPS_MAX * 4; k += blockDim.x)
         a.partials[item * WARPS_MAX * 4 + k] = 0.0;
     }
+  }
+}
+
+// ---- x pass, a warp per Voigt pair (FP32; every x length served by wm in {256, 512}) ----------
+//
+// Item = (field, tiles_per_item row pairs).  A block of three warps takes a row pair (k, -k):
+// warp c loads rows A and B of complex plane pair c, takes their x transforms with the paired
+// 256-point transforms (dft_pair256 for both rows at once when wm = 256; dft_split512 for one row
+// after the other when wm = 512) and leaves the n spectrum values of each row in shared memory;
+// the block meets; the mode pairs are projected across the three planes; the block meets again;
+// every warp takes the inverse transforms of its two rows and stores them.
+constexpr int XQ_THREADS = 96, XQ_MAXN = 512;
+constexpr size_t xpair_smem() {
+  return sizeof(float4) * 3 * 256 +                                 // exchange rows
+         sizeof(float2) * (6 * XQ_MAXN + 256 + 512 + 256) +         // spectra, chirp, chirp
+                                                                    // transform, W512^j
+         2 * sizeof(float) * size_t(eqk::staged_size(256)) + sizeof(float) * XQ_MAXN;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(XQ_THREADS, 4) k_gen_xpair(const GenArgs a) {
+  static_assert(sizeof(T) == 4, "FP32 kernel");
+  using T2 = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int TWS = eqk::staged_size(256);
+  float4* rows = reinterpret_cast<float4*>(smem_raw);       // [warp][256] exchange entries
+  T2* spec = reinterpret_cast<T2*>(rows + 3 * 256);         // [plane pair][side][XQ_MAXN]
+  T2* chs = spec + 6 * XQ_MAXN;
+  T2* bhs = chs + 256;
+  T2* w512 = bhs + 512;
+  T* twc = reinterpret_cast<T*>(w512 + 256);
+  T* tws = twc + TWS;
+  T* xix = tws + TWS;
+  const T2* cpool = reinterpret_cast<const T2*>(a.cpool);
+  const T* xipool = reinterpret_cast<const T*>(a.xipool);
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < TWS; i += blockDim.x) {
+    const T2 t = cpool[a.tw256 + i];
+    twc[i] = t.x;
+    tws[i] = t.y;
+  }
+  for (int i = tid; i < 256; i += blockDim.x) w512[i] = cpool[a.w512 + i];
+  const eqk::TwStaged<T> tw{twc, tws};
+  const eqk::PairAcc acc{rows + w * 256};
+  T2* sA = spec + (2 * w) * XQ_MAXN;                         // this warp's spectra
+  T2* sB = sA + XQ_MAXN;
+  int cur_f = -1;
+  for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    const int f = find_field(a.item0, a.nfields, item);
+    const FieldDesc fd = a.fields[f];
+    const AxisPlan& ap = a.axes[fd.ax[0]];
+    const int n = fd.nx, wm = ap.wm, ny = fd.ny, nz = fd.nz;
+    if (f != cur_f) {                     // this field's x tables into shared memory
+      __syncthreads();
+      for (int i = tid; i < n; i += blockDim.x) xix[i] = xipool[fd.xi[0] + i];
+      if (wm != n) {
+        for (int i = tid; i < n; i += blockDim.x) chs[i] = cpool[ap.wchirp + i];
+        for (int i = tid; i < wm; i += blockDim.x) bhs[i] = cpool[ap.wbhat + i];
+      }
+      __syncthreads();
+      cur_f = f;
+    }
+    T* base = reinterpret_cast<T*>(a.out) + fd.out_off;
+    const T* xiy = xipool + fd.xi[1];
+    const T* xiz = xipool + fd.xi[2];
+    T zmv[6];
+    eqk::zero_mode_values(a.mean + f * 6, double(fd.V), zmv);
+    const T inv_v = T(1.0 / double(fd.V));
+    Kahan<T> r2, di2, do2, o2;
+    const long long local = item - a.item0[f];
+    const long long lim = 6 * fd.V;
+    for (int g = (int)(local * a.tiles_per_item);
+         g < fd.npairs && g < (local + 1) * a.tiles_per_item; ++g) {
+      const int rA = a.pairpool[fd.pairs + g];
+      const int kz = rA / ny, ky = rA - kz * ny;
+      const int rB = (kz == 0 ? 0 : nz - kz) * ny + (ky == 0 ? 0 : ny - ky);
+      const bool self = rA == rB;
+      const long long oA = (long long)rA * n + 2LL * w * fd.V, oB = (long long)rB * n + 2LL * w * fd.V;
+      auto load = [&](long long o) {
+        return [=](int j) {
+          return eqk::in_bounds(o + j + fd.V, lim, a.err) ? make_float2(base[o + j], base[o + j + fd.V])
+                                                          : make_float2(0.f, 0.f);
+        };
+      };
+      auto keep = [](T2* s) { return [=](int k, float2 y) { s[k] = y; }; };
+      // forward transforms of rows A and B of plane pair w into sA, sB
+      __syncwarp();
+      if (wm == 256) {
+        dft_pair256<false>(n, load(oA), load(oB), keep(sA), keep(sB), acc, tw, chs, bhs, lane);
+      } else {
+        const float4* bh2 = reinterpret_cast<const float4*>(bhs);
+        dft_split512<false>(n, load(oA), keep(sA), acc, tw, w512, chs, bh2, lane);
+        if (!self) dft_split512<false>(n, load(oB), keep(sB), acc, tw, w512, chs, bh2, lane);
+      }
+      __syncthreads();
+      // projector over the mode pairs (kx, B at -kx)
+      const T xi_y = xiy[ky], xi_z = xiz[kz];
+      eqk::PlainSum<T> ps[4];
+      for (int kx = tid; kx < n; kx += blockDim.x) {
+        const int kxm = kx == 0 ? 0 : n - kx;
+        if (self && kx > kxm) continue;
+        T2 av[3], bv[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          av[c] = spec[(2 * c) * XQ_MAXN + kx];
+          bv[c] = spec[(2 * c + (self ? 0 : 1)) * XQ_MAXN + kxm];
+        }
+        const bool selfmode = self && kx == kxm;
+        eqk::project_pair<T>(av, bv, xix[kx], xi_y, xi_z, rA == 0 && kx == 0, zmv, a.nyq_zero != 0,
+                             a.compat != 0, inv_v, selfmode ? T(1) : T(2), ps[0], ps[1], ps[2], ps[3]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          spec[(2 * c) * XQ_MAXN + kx] = av[c];
+          if (!selfmode) spec[(2 * c + (self ? 0 : 1)) * XQ_MAXN + kxm] = bv[c];
+        }
+      }
+      r2.add(ps[0].s);
+      di2.add(ps[1].s);
+      do2.add(ps[2].s);
+      o2.add(ps[3].s);
+      __syncthreads();
+      // inverse transforms of the two rows, stored
+      auto read = [](const T2* s) { return [=](int k) { return s[k]; }; };
+      auto store = [&](long long o) {
+        return [=](int j, float2 y) {
+          if (eqk::in_bounds(o + j + fd.V, lim, a.err)) {
+            base[o + j] = y.x;
+            base[o + j + fd.V] = y.y;
+          }
+        };
+      };
+      if (wm == 256) {
+        auto skip = [](int, float2) {};
+        if (self) dft_pair256<true>(n, read(sA), read(sA), store(oA), skip, acc, tw, chs, bhs, lane);
+        else dft_pair256<true>(n, read(sA), read(sB), store(oA), store(oB), acc, tw, chs, bhs, lane);
+      } else {
+        const float4* bh2 = reinterpret_cast<const float4*>(bhs);
+        dft_split512<true>(n, read(sA), store(oA), acc, tw, w512, chs, bh2, lane);
+        if (!self) dft_split512<true>(n, read(sB), store(oB), acc, tw, w512, chs, bh2, lane);
+      }
+    }
+    double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
+    warp_partials<4>(v, a.partials + item * WARPS_MAX * 4);
+    for (int k = 3 * 4 + tid; k < WARPS_MAX * 4; k += blockDim.x)
+      a.partials[item * WARPS_MAX * 4 + k] = 0.0;
   }
 }
 

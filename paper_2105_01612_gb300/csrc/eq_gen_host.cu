@@ -534,7 +534,7 @@ GenTune gen_default_tune(const GenPlan* g) {
   if (scols_supported(g, 2)) t.zc = 0;
   if (scols_supported(g, 1)) t.yc = 0;
   t.zt = t.yt = 256;
-  t.xp = xrows_supported(g) ? 0 : (g->mx[0] > 256 ? 1 : 2);
+  t.xp = xrows_supported(g) ? (es == 4 ? 4 : 0) : (g->mx[0] > 256 ? 1 : 2);
   return t;
 }
 
@@ -555,12 +555,22 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
     }
     p.kind = 4; p.cols = SC_COLS; p.pitch = SC_PITCH; p.threads = SC_THREADS;
   }
-  if (t.xp == 0 && !xrows_supported(g)) {
-    *err = "x pass: the warp-per-row kernel serves x lengths up to 256 and 512 only";
+  if ((t.xp == 0 || t.xp == 4) && !xrows_supported(g)) {
+    *err = "x pass: the warp-per-row kernels serve x lengths up to 256 and 512 only";
+    return EQ_ERR_INVALID;
+  }
+  if (t.xp == 4 && g->dtype != EQ_F32) {
+    *err = "x pass: the warp-per-plane-pair kernel is FP32";
+    return EQ_ERR_INVALID;
+  }
+  if (t.xp < 0 || t.xp > 4) {
+    *err = "x pass: unknown kernel choice";
     return EQ_ERR_INVALID;
   }
   if (t.xp == 0) {
     x.kind = 3; x.mmax = g->mx[0]; x.cols = 6; x.pitch = 0; x.threads = XR_THREADS;
+  } else if (t.xp == 4) {
+    x.kind = 6; x.mmax = g->mx[0]; x.cols = 6; x.pitch = 0; x.threads = XQ_THREADS;
   } else {
     x.kind = 2; x.mmax = g->mx[0]; x.cols = 6 * t.xp; x.pitch = 6 * t.xp + 1; x.threads = 32 * x.cols;
   }
@@ -568,6 +578,7 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
   for (PassShape* p : ps) {
     p->smem = p->kind == 3   ? (g->dtype == EQ_F32 ? xrows_smem<float>() : xrows_smem<double>())
               : p->kind == 4 ? scols_smem()
+              : p->kind == 6 ? xpair_smem()
                              : (2 * (size_t)p->mmax * p->pitch + 3 * (size_t)p->mmax) * cs;
     if (p->smem > limit || p->threads > 512 || p->threads % p->cols != 0 || p->cols < 1) {
       *err = "pass shape does not fit (tile columns, threads or shared memory)";
@@ -843,7 +854,7 @@ eq_status gen_autotune(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s
         cands.push_back(u);
       }
     } else {
-      for (int xp : {0, 1, 2, 3}) {
+      for (int xp : {0, 1, 2, 3, 4}) {
         GenTune u = best;
         u.xp = xp;
         cands.push_back(u);

@@ -22,7 +22,8 @@ struct GenTune {
                            // warp-per-column kernel (k_gen_scols, its own block shape)
   int yc = 16, yt = 256;   // y pass, the same
   int xp = 2;              // x pass: row pairs per block (6 xp transforms, 32 threads each) of
-                           // the shared-memory kernel; 0 = the warp-per-row kernel (k_gen_xrows)
+                           // the shared-memory kernel (1..3); 0 = the warp-per-row kernel
+                           // (k_gen_xrows); 4 = the warp-per-plane-pair kernel (k_gen_xpair, FP32)
 };
 
 // Largest supported axis length and the rule for it (for error messages).

@@ -14,7 +14,8 @@ template <typename T> struct GenInst {
     if constexpr (std::is_same<T, float>::value) {       // the warp-per-column kernel is FP32
       if (kind == 4) return reinterpret_cast<const void*>(&k_gen_scols<false>);
       if (kind == 5) return reinterpret_cast<const void*>(&k_gen_scols<true>);
-    } else if (kind == 4 || kind == 5) {
+      if (kind == 6) return reinterpret_cast<const void*>(&k_gen_xpair<float>);
+    } else if (kind == 4 || kind == 5 || kind == 6) {
       return nullptr;
     }
     return reinterpret_cast<const void*>(&k_gen_xproj<T>);
@@ -35,10 +36,11 @@ template <typename T> struct GenInst {
     if (kind == 0) k_gen_strided<T, false><<<grid, threads, smem, s>>>(a);
     else if (kind == 1) k_gen_strided<T, true><<<grid, threads, smem, s>>>(a);
     else if (kind == 3) k_gen_xrows<T><<<grid, threads, smem, s>>>(a);
-    else if (kind == 4 || kind == 5) {
+    else if (kind == 4 || kind == 5 || kind == 6) {
       if constexpr (std::is_same<T, float>::value) {
         if (kind == 4) k_gen_scols<false><<<grid, threads, smem, s>>>(a);
-        else k_gen_scols<true><<<grid, threads, smem, s>>>(a);
+        else if (kind == 5) k_gen_scols<true><<<grid, threads, smem, s>>>(a);
+        else k_gen_xpair<float><<<grid, threads, smem, s>>>(a);
       } else {
         return cudaErrorInvalidValue;
       }

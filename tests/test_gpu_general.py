@@ -160,7 +160,8 @@ def test_pass_timing_covers_the_asked_calls_then_turns_off(dims):
 
 def test_every_pass_kernel_choice_matches_the_oracle(tmp_path, monkeypatch):
     """The tuning cache picks each pass's kernel: the shared-memory strided kernel or the
-    warp-per-column one (z, y), the shared-memory x kernel or the warp-per-row one.  Every
+    warp-per-column one (z, y), the shared-memory x kernel, the warp-per-row one or the
+    warp-per-plane-pair one.  Every
     combination gives the oracle's result on lengths served directly (256) and by Bluestein
     (18..130 through 256- and 512-point transforms); an entry that does not fit is passed over."""
     cache = tmp_path / "tune.json"
@@ -177,7 +178,7 @@ def test_every_pass_kernel_choice_matches_the_oracle(tmp_path, monkeypatch):
     key = json.loads(cache.read_text())
     assert len(key) == 1
     key = next(iter(key))
-    for zc, yc, xp in [(0, 0, 0), (16, 16, 2), (0, 8, 2), (8, 0, 0), (0, 0, 1)]:
+    for zc, yc, xp in [(0, 0, 4), (0, 0, 0), (16, 16, 2), (0, 8, 2), (8, 0, 0), (0, 0, 1), (16, 8, 4)]:
         cache.write_text(json.dumps({key: [zc, 256, yc, 256, xp]}))
         plan = eq.VarlenPlan(dims, torch.float32, "ddo")
         out = torch.empty_like(flat)
