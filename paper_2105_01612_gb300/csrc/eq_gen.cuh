@@ -432,9 +432,10 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
 
 // ---- strided pass, a warp per column (lengths served by a 256- or 512-point transform) ------
 //
-// FP32.  Same items, partial records and modes as k_gen_strided.  A tile of SC_COLS adjacent
-// columns (n points each) comes into shared memory by coalesced loads (SC_COLS consecutive
-// elements of a plane per point), eight loads in flight a thread; the warps then transform whole
+// FP32.  Same items, partial records and modes as k_gen_strided.  A tile of C adjacent columns
+// (n points each; C = 32 for n <= 256, else 16) comes into shared memory by coalesced loads (C
+// consecutive elements of a plane per point), eight loads in flight a thread; the warps then
+// transform whole
 // columns with paired 256-point transforms (two sequences in one warp, packed two-lane
 // arithmetic, eq_fft_pair.cuh) and write the n outputs back into the tile, which leaves by
 // coalesced stores (with the L-infinity residual of the last pass).  Every field of a launch has
@@ -449,11 +450,15 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
 //     the outputs j < 256, y_j = P_j + W512^-j Q_j from the inverse transforms P, Q of the even
 //     and odd halves of the product.
 // The inverse direction of a Bluestein length goes by conjugation of input and output.
-constexpr int SC_COLS = 16, SC_WARPS = 8, SC_THREADS = 32 * SC_WARPS, SC_PITCH = SC_COLS + 1;
+constexpr int SC_WARPS = 8, SC_THREADS = 32 * SC_WARPS;
 constexpr int SC_MAXN = 512;          // longest column (n = wm = 512)
+constexpr int SC_TILE = SC_MAXN * 17; // tile entries: 16 columns of 512 points or 32 of 256, pitch
+                                      // columns + 1
+// columns of a tile for axis length n
+__host__ __device__ constexpr int scols_cols(int n) { return n <= 256 ? 32 : 16; }
 constexpr size_t scols_smem() {
   return sizeof(float4) * size_t(SC_WARPS) * 256 +                          // exchange rows
-         sizeof(float2) * (size_t(SC_MAXN) * SC_PITCH + 256 + 512 + 256) +   // tile, chirp, chirp
+         sizeof(float2) * (size_t(SC_TILE) + 256 + 512 + 256) +             // tile, chirp, chirp
                                                                              // transform, W512^j
          2 * sizeof(float) * size_t(eqk::staged_size(256));                 // staged twiddles
 }
@@ -581,32 +586,31 @@ __device__ __forceinline__ void dft_pair256(int n, IN0 in0, IN1 in1, OUT0 out0, 
 
 // A column of the tile (wm = 512), and columns c0, c0 + 1 (wm = 256), transformed in place.
 template <bool INV>
-__device__ __forceinline__ void scol512(float2* tile, int col, int n, const eqk::PairAcc& acc,
-                                        const eqk::TwStaged<float>& tw, const float2* w512,
-                                        const float2* chs, const float4* bhs2, int lane, int* err) {
-  const long long lim = (long long)SC_MAXN * SC_PITCH;
+__device__ __forceinline__ void scol512(float2* tile, int pitch, int col, int n,
+                                        const eqk::PairAcc& acc, const eqk::TwStaged<float>& tw,
+                                        const float2* w512, const float2* chs, const float4* bhs2,
+                                        int lane, int* err) {
   auto in = [&](int j) {
-    return eqk::in_bounds((long long)j * SC_PITCH + col, lim, err) ? tile[j * SC_PITCH + col]
-                                                                   : make_float2(0.f, 0.f);
+    return eqk::in_bounds((long long)j * pitch + col, SC_TILE, err) ? tile[j * pitch + col]
+                                                                     : make_float2(0.f, 0.f);
   };
-  auto out = [&](int k, float2 y) { tile[k * SC_PITCH + col] = y; };
+  auto out = [&](int k, float2 y) { tile[k * pitch + col] = y; };
   dft_split512<INV>(n, in, out, acc, tw, w512, chs, bhs2, lane);
 }
 template <bool INV>
-__device__ __forceinline__ void scol256(float2* tile, int c0, int n, const eqk::PairAcc& acc,
-                                        const eqk::TwStaged<float>& tw, const float2* chs,
-                                        const float2* bhs, int lane, int* err) {
-  const long long lim = (long long)SC_MAXN * SC_PITCH;
+__device__ __forceinline__ void scol256(float2* tile, int pitch, int c0, int n,
+                                        const eqk::PairAcc& acc, const eqk::TwStaged<float>& tw,
+                                        const float2* chs, const float2* bhs, int lane, int* err) {
   auto in0 = [&](int j) {
-    return eqk::in_bounds((long long)j * SC_PITCH + c0 + 1, lim, err) ? tile[j * SC_PITCH + c0]
-                                                                      : make_float2(0.f, 0.f);
+    return eqk::in_bounds((long long)j * pitch + c0 + 1, SC_TILE, err) ? tile[j * pitch + c0]
+                                                                        : make_float2(0.f, 0.f);
   };
   auto in1 = [&](int j) {
-    return eqk::in_bounds((long long)j * SC_PITCH + c0 + 1, lim, err) ? tile[j * SC_PITCH + c0 + 1]
-                                                                      : make_float2(0.f, 0.f);
+    return eqk::in_bounds((long long)j * pitch + c0 + 1, SC_TILE, err) ? tile[j * pitch + c0 + 1]
+                                                                        : make_float2(0.f, 0.f);
   };
-  auto out0 = [&](int k, float2 y) { tile[k * SC_PITCH + c0] = y; };
-  auto out1 = [&](int k, float2 y) { tile[k * SC_PITCH + c0 + 1] = y; };
+  auto out0 = [&](int k, float2 y) { tile[k * pitch + c0] = y; };
+  auto out1 = [&](int k, float2 y) { tile[k * pitch + c0 + 1] = y; };
   dft_pair256<INV>(n, in0, in1, out0, out1, acc, tw, chs, bhs, lane);
 }
 
@@ -617,15 +621,14 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int TWS = eqk::staged_size(256);
   float4* rows = reinterpret_cast<float4*>(smem_raw);      // [warp][256] exchange entries
-  T2* tile = reinterpret_cast<T2*>(rows + SC_WARPS * 256); // [point][SC_PITCH]
-  T2* chs = tile + SC_MAXN * SC_PITCH;                     // chirp (n <= 256)
+  T2* tile = reinterpret_cast<T2*>(rows + SC_WARPS * 256); // [point][pitch]
+  T2* chs = tile + SC_TILE;                     // chirp (n <= 256)
   T2* bhs = chs + 256;                                     // chirp transform (wm entries)
   T2* w512 = bhs + 512;                                    // W512^j, j < 256
   T* twc = reinterpret_cast<T*>(w512 + 256);
   T* tws = twc + TWS;
   const T2* cpool = reinterpret_cast<const T2*>(a.cpool);
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int lc = tid % SC_COLS, lj = tid / SC_COLS, jstep = SC_THREADS / SC_COLS;
   for (int i = tid; i < TWS; i += blockDim.x) {
     const T2 t = cpool[a.tw256 + i];
     twc[i] = t.x;
@@ -641,6 +644,8 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
     const int axi = fd.ax[a.axis];
     const AxisPlan& ap = a.axes[axi];
     const int n = ap.n, wm = ap.wm;
+    const int C = scols_cols(n), pitch = C + 1;
+    const int lc = tid % C, lj = tid / C, jstep = SC_THREADS / C;
     if (axi != cur_ax) {                  // chirp tables of this axis length into shared memory
       __syncthreads();
       if (wm != n) {
@@ -653,7 +658,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
     long long inner, nstride, outer_stride, ncols;
     if (a.axis == 2) { inner = (long long)fd.nx * fd.ny; nstride = inner; outer_stride = 0; ncols = inner; }
     else { inner = fd.nx; nstride = fd.nx; outer_stride = (long long)fd.nx * fd.ny; ncols = (long long)fd.nz * fd.nx; }
-    const long long ntiles = (ncols + SC_COLS - 1) / SC_COLS;
+    const long long ntiles = (ncols + C - 1) / C;
     const long long chunks = (ntiles + a.tiles_per_item - 1) / a.tiles_per_item;
     const long long local = item - a.item0[f];
     const int comp = (int)(local / chunks);
@@ -667,7 +672,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
     Kahan<T> sa, sb, sq;
     T nonfinite = T(0), linf = T(0);
     for (long long tl = chunk * a.tiles_per_item; tl < ntiles && tl < (chunk + 1) * a.tiles_per_item; ++tl) {
-      const long long c = tl * SC_COLS + lc;
+      const long long c = tl * C + lc;
       const bool valid = c < ncols;
       const long long o = valid ? c / inner : 0;
       const long long base = o * outer_stride + (valid ? c - o * inner : 0);
@@ -693,17 +698,20 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
               sb.add(x.y);
               sq.add(wa * x.x * x.x + wb * x.y * x.y);
             }
-            tile[j * SC_PITCH + lc] = x;
+            tile[j * pitch + lc] = x;
           }
         }
       }
       __syncthreads();
       if (wm == 512) {
-        for (int cc = w; cc < SC_COLS; cc += SC_WARPS)
-          if (tl * SC_COLS + cc < ncols)                    // warp-uniform
-            scol512<INV>(tile, cc, n, acc, tw, w512, chs, reinterpret_cast<const float4*>(bhs), lane, a.err);
-      } else if (tl * SC_COLS + 2 * w < ncols) {
-        scol256<INV>(tile, 2 * w, n, acc, tw, chs, bhs, lane, a.err);
+        for (int cc = w; cc < C; cc += SC_WARPS)
+          if (tl * C + cc < ncols)                          // warp-uniform
+            scol512<INV>(tile, pitch, cc, n, acc, tw, w512, chs, reinterpret_cast<const float4*>(bhs),
+                         lane, a.err);
+      } else {
+        for (int c0 = 2 * w; c0 < C; c0 += 2 * SC_WARPS)
+          if (tl * C + c0 < ncols)
+            scol256<INV>(tile, pitch, c0, n, acc, tw, chs, bhs, lane, a.err);
       }
       __syncthreads();
       // coalesced tile store (+ the residual of the last pass against the input)
@@ -724,7 +732,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
             const int k = kb + u * jstep;
             const long long off = base + (long long)k * nstride;
             if (k < n && eqk::in_bounds(off, fd.V, a.err)) {
-              const T2 y = tile[k * SC_PITCH + lc];
+              const T2 y = tile[k * pitch + lc];
               out_re[off] = y.x;
               out_im[off] = y.y;
               if (ref_re) {

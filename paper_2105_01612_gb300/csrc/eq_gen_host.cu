@@ -553,7 +553,7 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
       *err = "strided pass: the warp-per-column kernel serves lengths up to 256 and 512 only";
       return EQ_ERR_INVALID;
     }
-    p.kind = 4; p.cols = SC_COLS; p.pitch = SC_PITCH; p.threads = SC_THREADS;
+    p.kind = 4; p.cols = 32; p.pitch = 33; p.threads = SC_THREADS;   // columns per field: scols_cols
   }
   if ((t.xp == 0 || t.xp == 4) && !xrows_supported(g)) {
     *err = "x pass: the warp-per-row kernels serve x lengths up to 256 and 512 only";
@@ -603,7 +603,8 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
       if (pi == 2) total_tiles += (fd.npairs + (p->cols / 6) - 1) / (p->cols / 6);
       else {
         const long long ncols = pi == 0 ? (long long)fd.nx * fd.ny : (long long)fd.nz * fd.nx;
-        total_tiles += 3 * ((ncols + p->cols - 1) / p->cols);
+        const int cols = p->kind == 4 ? scols_cols(g->ah[fd.ax[pi == 0 ? 2 : 1]].n) : p->cols;
+        total_tiles += 3 * ((ncols + cols - 1) / cols);
       }
     }
     p->tpi = (int)std::max(1LL, total_tiles / (8 * resident));
@@ -616,7 +617,8 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
         items = (groups + p->tpi - 1) / p->tpi;
       } else {
         const long long ncols = pi == 0 ? (long long)fd.nx * fd.ny : (long long)fd.nz * fd.nx;
-        const long long ntiles = (ncols + p->cols - 1) / p->cols;
+        const int cols = p->kind == 4 ? scols_cols(g->ah[fd.ax[pi == 0 ? 2 : 1]].n) : p->cols;
+        const long long ntiles = (ncols + cols - 1) / cols;
         items = 3 * ((ntiles + p->tpi - 1) / p->tpi);
       }
       pre[pi][f + 1] = pre[pi][f] + items;
