@@ -45,6 +45,9 @@ def parse():
                     help="profiling cases: a non-cubic grid instead of size^3")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64, cuFFT, e2e and CPU comparison legs")
+    ap.add_argument("--batch-fields", type=int, default=0, metavar="K",
+                    help="profiling case: only the uneven-batch leg, on the first K of its 64 "
+                         "fields, with the plan's default pass shapes (no autotuning)")
     return ap.parse_args()
 
 
@@ -623,16 +626,17 @@ def grain_leg(x, out, plan, n, dev, stream, peak):
             "value": vox / (ms_both / 1e3), "unit": UNIT, "grain_map_setup_s": setup_s}
 
 
-def batch_leg(dev, steps: int):
+def batch_leg(dev, steps: int, nfields: int = 64, tune: bool = True):
     """64 fields, each axis uniform in 64..256, Voronoi 50..2000 grains ~ N(0,150 MPa), FP32, DDO:
-    one launch per pass over all fields, replayed from a captured CUDA graph."""
+    one launch per pass over all fields, replayed from a captured CUDA graph.  nfields < 64 keeps
+    the first fields of the same draw (profiling cases); tune=False keeps the default shapes."""
     import numpy as np
     import torch
     from fieldgen import voronoi_stress_field
     import paper_2105_01612_gb300 as eq
     rng = np.random.Generator(np.random.PCG64(210501612 + 3))
-    dims = [tuple(int(v) for v in rng.integers(64, 257, size=3)) for _ in range(64)]
-    grains = [int(g) for g in rng.integers(50, 2001, size=64)]
+    dims = [tuple(int(v) for v in rng.integers(64, 257, size=3)) for _ in range(64)][:nfields]
+    grains = [int(g) for g in rng.integers(50, 2001, size=64)][:nfields]
     plan = eq.VarlenPlan(dims, torch.float32, "ddo", device=dev)
     flat = torch.empty(plan.numel, dtype=torch.float32, device=dev)
     off = 0
@@ -647,7 +651,8 @@ def batch_leg(dev, steps: int):
     # the run's temporary directory unless the caller names one)
     os.environ.setdefault("EQ_TUNE_CACHE", os.path.join("/tmp", f"eq_tune_{os.getpid()}.txt"))
     t0 = time.perf_counter()
-    plan.autotune(flat, out)
+    if tune:
+        plan.autotune(flat, out)
     tune_s = time.perf_counter() - t0
     for _ in range(3):
         plan.project(flat, out)
@@ -666,8 +671,8 @@ def batch_leg(dev, steps: int):
     per_pass, _ = plan.pass_ms()
     plan.close()
     peak, _ = measured_peaks()
-    return {"workload": "64 fields, axes uniform 64..256, 50..2000 Voronoi grains, FP32, DDO; "
-                        "one launch per pass over all fields, CUDA graph replay",
+    return {"workload": f"{nfields} fields, axes uniform 64..256, 50..2000 Voronoi grains, FP32, "
+                        "DDO; one launch per pass over all fields, CUDA graph replay",
             "voxels": vox, "value": vox / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "steps": steps, "pass_ms": per_pass, "autotune_s": tune_s,
             "pass_frac": {k: BYTES_PER_VOXEL_PASS * vox / (v / 1e3) / 1e9 / peak
@@ -784,6 +789,11 @@ def serving_leg(dev, rate: float = 200.0, warm: int = 200, measured: int = 2000,
 
 def main():
     args = parse()
+    if args.batch_fields:
+        import torch
+        print(json.dumps(batch_leg(torch.device("cuda", 0), args.steps, args.batch_fields,
+                                   tune=False)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
