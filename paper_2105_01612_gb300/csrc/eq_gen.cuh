@@ -15,7 +15,7 @@
 
 #include "../../include/eq.h"
 #include "eq_kernels.cuh"
-#include "eq_fft_pair.cuh"
+#include "eq_pfft.cuh"
 
 namespace eqg {
 
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
 // consecutive elements of a plane per point), eight loads in flight a thread; the warps then
 // transform whole
 // columns with paired 256-point transforms (two sequences in one warp, packed two-lane
-// arithmetic, eq_fft_pair.cuh) and write the n outputs back into the tile, which leaves by
+// arithmetic, eq_pfft.cuh) and write the n outputs back into the tile, which leaves by
 // coalesced stores (with the L-infinity residual of the last pass).  Every field of a launch has
 // its axis served by a transform length wm in {256, 512}:
 //   wm = 256: a warp takes two adjacent columns as the pair, either transformed directly (n = 256)
