@@ -22,7 +22,7 @@ LIB_CHECK = os.path.join(HERE, "libeq_check.so")
 MEASURE_SRC = os.path.join(CSRC, "measure", "eqm.cu")
 MEASURE_LIB = os.path.join(HERE, "libeqm.so")
 
-SOURCES = ["eq_f32.cu", "eq_f64.cu", "eq_gen_f32.cu", "eq_gen_f64.cu", "eq_gen_host.cu", "eq_api.cu", "eq_serve.cu", "eq_static.cu",
+SOURCES = ["eq_f32.cu", "eq_f64.cu", "eq_gen_f32.cu", "eq_gen_f64.cu", "eq_gen_dd.cu", "eq_gen_host.cu", "eq_api.cu", "eq_serve.cu", "eq_static.cu",
            "eq_grains.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

@@ -16,6 +16,7 @@
 #include "../../include/eq.h"
 #include "eq_kernels.cuh"
 #include "eq_pfft.cuh"
+#include "eq_dd.cuh"
 
 namespace eqg {
 
@@ -82,7 +83,21 @@ struct GenArgs {
   int* err;                // plan error word (bounds-checked builds)
   int tw256;               // complex pool: staged twiddles of length 256 (k_gen_scols)
   int w512;                // complex pool: W512^j, j < 256 (k_gen_scols)
+  int io;                  // double-float plans: bit 0 this pass reads FP64, bit 1 it writes FP64
+                           // (the pipeline's ends); the passes between hold double-float pairs
 };
+
+// Element loads and stores of the strided passes: the plan's type, or for double-float
+// arithmetic FP64 at the pipeline's ends, converted on the bits.
+template <typename T> __device__ __forceinline__ T ld_elem(const T* p, long long i, bool) { return p[i]; }
+template <> __device__ __forceinline__ eqk::dd ld_elem<eqk::dd>(const eqk::dd* p, long long i, bool f64) {
+  return f64 ? eqk::dd_from_bits(reinterpret_cast<const double*>(p)[i]) : p[i];
+}
+template <typename T> __device__ __forceinline__ void st_elem(T* p, long long i, T v, bool) { p[i] = v; }
+template <> __device__ __forceinline__ void st_elem<eqk::dd>(eqk::dd* p, long long i, eqk::dd v, bool f64) {
+  if (f64) reinterpret_cast<double*>(p)[i] = eqk::dd_to_bits(v);
+  else p[i] = v;
+}
 
 // ---- small DFTs -------------------------------------------------------------------------
 
@@ -346,6 +361,7 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
     Kahan<T> sa, sb, sq;
     T nonfinite = T(0), linf = T(0);
     const bool inv = INV;
+    const bool in64 = a.io & 1, out64 = a.io & 2;
     for (long long tile = chunk * a.tiles_per_item;
          tile < ntiles && tile < (chunk + 1) * a.tiles_per_item; ++tile) {
       const long long c = tile * C + col;
@@ -361,8 +377,8 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
         for (int u = 0; u < LB; ++u) {
           const int j = jb + u * jstep;
           const long long off = base + (long long)j * nstride;
-          xb[u] = (j < n && valid && eqk::in_bounds(off, fd.V, a.err)) ? T2{in_re[off], in_im[off]}
-                                                                       : T2{T(0), T(0)};
+          xb[u] = (j < n && valid && eqk::in_bounds(off, fd.V, a.err))
+                      ? T2{ld_elem(in_re, off, in64), ld_elem(in_im, off, in64)} : T2{T(0), T(0)};
         }
 #pragma unroll
         for (int u = 0; u < LB; ++u) {
@@ -393,7 +409,8 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
               const int k = kb + u * jstep;
               const long long off = base + (long long)k * nstride;
               rb[u] = (k < n && eqk::in_bounds(off, fd.V, a.err))
-                          ? T2{ref_re[off], ref_re[off + fd.V]} : T2{T(0), T(0)};
+                          ? T2{ld_elem(ref_re, off, true), ld_elem(ref_re, off + fd.V, true)}
+                          : T2{T(0), T(0)};
             }
           }
 #pragma unroll
@@ -403,8 +420,8 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
             const long long off = base + (long long)k * nstride;
             if (!eqk::in_bounds(off, fd.V, a.err)) continue;
             const T2 y = post(r[k * pitch + col], k, ap, sm.ch, inv);
-            out_re[off] = y.x;
-            out_im[off] = y.y;
+            st_elem(out_re, off, y.x, out64);
+            st_elem(out_im, off, y.y, out64);
             if (ref_re) {
               linf = fmax(linf, fabs(rb[u].x - y.x));
               linf = fmax(linf, fabs(rb[u].y - y.y));
@@ -756,6 +773,214 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
       for (int o2 = 16; o2 > 0; o2 >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o2));
       if (lane == 0) a.partials[item * WARPS_MAX * 4 + w] = v;
       for (int k = SC_WARPS + tid; k < WARPS_MAX * 4; k += blockDim.x)
+        a.partials[item * WARPS_MAX * 4 + k] = 0.0;
+    }
+  }
+}
+
+// ---- strided pass of double-float plans, a warp per column (wm in {256, 512}) -------------
+//
+// FP64 plans in double-float arithmetic (FP64 in HBM at the pipeline's ends: the first pass
+// converts its loads, the last its stores and the residual's re-read input; double-float pairs
+// between the passes).  Same items, partial records and modes as k_gen_strided.  One block of
+// SD_WARPS warps per SM (254 registers, no spills).  A tile of SD_COLS adjacent columns (n points
+// each) comes into shared memory by coalesced loads (SD_COLS consecutive elements of a plane per
+// point), eight loads in flight a thread; each warp then takes whole columns: lane l
+// holds points l + 32 e of a length-wm register transform (radix-8 stages through the warp's own
+// row), directly when n = wm, else Bluestein's convolution (pre-chirp, transform, product with
+// the chirp transform, inverse transform, post-chirp; the inverse direction by conjugation), and
+// writes the n outputs back into the tile, which leaves by coalesced stores (with the L-infinity
+// residual of the last pass).  All fields of a launch have their axis served (wm in {256, 512}).
+constexpr int SD_COLS = 8, SD_WARPS = 8, SD_THREADS = 32 * SD_WARPS, SD_PITCH = SD_COLS + 1;
+constexpr int SD_MAXN = 512;          // longest column (n = wm = 512)
+template <typename T> constexpr size_t scold_smem() {
+  return 2 * sizeof(T) * (size_t(SD_MAXN) * SD_PITCH + 256 + 512) +   // tile, chirp, chirp transform
+         sizeof(T) * (size_t(SD_WARPS) * 2 * 512 + 2 * eqk::staged_size(512));
+}
+
+template <typename T, int M, bool INV>
+__device__ __forceinline__ void scold_transform(typename eqk::V2<T>::t* tile, int col, int n,
+                                               const eqk::SoaAcc<T>& acc,
+                                               const eqk::TwStaged<T>& tw,
+                                               const typename eqk::V2<T>::t* chs,
+                                               const typename eqk::V2<T>::t* bhs, int* err) {
+  using T2 = typename eqk::V2<T>::t;
+  constexpr int E = M / 32;
+  const int lane = threadIdx.x & 31;
+  const bool blue = n != M;
+  T2 x[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int j = lane + 32 * e;
+    x[e] = T2{T(0), T(0)};
+    if (j < n && eqk::in_bounds((long long)j * SD_PITCH + col, (long long)SD_MAXN * SD_PITCH, err)) {
+      x[e] = tile[j * SD_PITCH + col];
+      if (blue) {
+        if (INV) x[e].y = -x[e].y;
+        x[e] = cmul(x[e], chs[j]);
+      }
+    }
+  }
+  __syncwarp();                                             // the warp's row is free
+  if (blue) {
+    eqk::fft_column_acc<M, E, false, 0, true>(x, lane, acc, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) x[e] = cmul(x[e], bhs[lane + 32 * e]);
+    __syncwarp();
+    eqk::fft_column_acc<M, E, true, 0, true>(x, lane, acc, tw);
+  } else {
+    eqk::fft_column_acc<M, E, INV, 0, true>(x, lane, acc, tw);
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = lane + 32 * e;
+    if (k < n) {
+      T2 y = x[e];
+      if (blue) {
+        y = cmul(y, chs[k]);
+        if (INV) y.y = -y.y;
+      }
+      tile[k * SD_PITCH + col] = y;
+    }
+  }
+  __syncwarp();
+}
+
+template <typename T, bool INV>
+__global__ void __launch_bounds__(SD_THREADS, 1) k_gen_scold(const GenArgs a) {
+  using T2 = typename eqk::V2<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int TWS = eqk::staged_size(512);
+  T2* tile = reinterpret_cast<T2*>(smem_raw);               // [point][SD_PITCH]
+  T2* chs = tile + SD_MAXN * SD_PITCH;
+  T2* bhs = chs + 256;
+  T* rows = reinterpret_cast<T*>(bhs + 512);                // [warp][re 512 | im 512]
+  T* twc = rows + SD_WARPS * 2 * 512;
+  T* tws = twc + TWS;
+  const T2* cpool = reinterpret_cast<const T2*>(a.cpool);
+  const int tid = threadIdx.x, w = tid >> 5, nw = SD_WARPS;
+  const int lc = tid % SD_COLS, lj = tid / SD_COLS, jstep = SD_THREADS / SD_COLS;
+  const eqk::SoaAcc<T> acc{rows + w * 2 * 512, rows + w * 2 * 512 + 512};
+  int cur_ax = -1;
+  for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    const int f = find_field(a.item0, a.nfields, item);
+    const FieldDesc fd = a.fields[f];
+    const int axi = fd.ax[a.axis];
+    const AxisPlan& ap = a.axes[axi];
+    const int n = ap.n, wm = ap.wm;
+    if (axi != cur_ax) {                  // tables of this axis length into shared memory
+      __syncthreads();
+      const int ts = eqk::staged_size(wm);
+      for (int i = tid; i < ts; i += blockDim.x) {
+        const T2 t = cpool[ap.wtw + i];
+        twc[i] = t.x;
+        tws[i] = t.y;
+      }
+      if (wm != n) {
+        for (int i = tid; i < n; i += blockDim.x) chs[i] = cpool[ap.wchirp + i];
+        for (int i = tid; i < wm; i += blockDim.x) bhs[i] = cpool[ap.wbhat + i];
+      }
+      __syncthreads();
+      cur_ax = axi;
+    }
+    const eqk::TwStaged<T> tw{twc, tws};
+    long long inner, nstride, outer_stride, ncols;
+    if (a.axis == 2) { inner = (long long)fd.nx * fd.ny; nstride = inner; outer_stride = 0; ncols = inner; }
+    else { inner = fd.nx; nstride = fd.nx; outer_stride = (long long)fd.nx * fd.ny; ncols = (long long)fd.nz * fd.nx; }
+    const long long ntiles = (ncols + SD_COLS - 1) / SD_COLS;
+    const long long chunks = (ntiles + a.tiles_per_item - 1) / a.tiles_per_item;
+    const long long local = item - a.item0[f];
+    const int comp = (int)(local / chunks);
+    const long long chunk = local - comp * chunks;
+    const T* in_re = reinterpret_cast<const T*>(a.in) + (a.mode == 1 ? fd.in_off : fd.out_off) + 2LL * comp * fd.V;
+    const T* in_im = in_re + fd.V;
+    T* out_re = reinterpret_cast<T*>(a.out) + fd.out_off + 2LL * comp * fd.V;
+    T* out_im = out_re + fd.V;
+    const T* ref_re = a.ref ? reinterpret_cast<const T*>(a.ref) + fd.in_off + 2LL * comp * fd.V : nullptr;
+    const T wa = comp == 2 ? T(2) : T(1), wb = comp == 0 ? T(1) : T(2);
+    Kahan<T> sa, sb, sq;
+    T nonfinite = T(0), linf = T(0);
+    const bool in64 = a.io & 1, out64 = a.io & 2;
+    for (long long tl = chunk * a.tiles_per_item; tl < ntiles && tl < (chunk + 1) * a.tiles_per_item; ++tl) {
+      const long long c = tl * SD_COLS + lc;
+      const bool valid = c < ncols;
+      const long long o = valid ? c / inner : 0;
+      const long long base = o * outer_stride + (valid ? c - o * inner : 0);
+      // coalesced tile load, eight loads in flight; statistics of the first pass
+      constexpr int LB = 8;
+      for (int jb = lj; jb < n; jb += LB * jstep) {
+        T2 xb[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int j = jb + u * jstep;
+          const long long off = base + (long long)j * nstride;
+          xb[u] = (j < n && valid && eqk::in_bounds(off, fd.V, a.err))
+                      ? T2{ld_elem(in_re, off, in64), ld_elem(in_im, off, in64)} : T2{T(0), T(0)};
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int j = jb + u * jstep;
+          if (j >= n) break;
+          const T2 x = xb[u];
+          if (a.mode == 1 && valid) {
+            if (!isfinite(x.x) || !isfinite(x.y)) nonfinite += T(1);
+            sa.add(x.x);
+            sb.add(x.y);
+            sq.add(wa * x.x * x.x + wb * x.y * x.y);
+          }
+          tile[j * SD_PITCH + lc] = x;
+        }
+      }
+      __syncthreads();
+      for (int cc = w; cc < SD_COLS; cc += nw) {
+        if (tl * SD_COLS + cc >= ncols) continue;             // warp-uniform
+        if (wm == 512) scold_transform<T, 512, INV>(tile, cc, n, acc, tw, chs, bhs, a.err);
+        else scold_transform<T, 256, INV>(tile, cc, n, acc, tw, chs, bhs, a.err);
+      }
+      __syncthreads();
+      // coalesced tile store (+ the residual of the last pass against the input)
+      if (valid) {
+        for (int kb = lj; kb < n; kb += LB * jstep) {
+          T2 rb[LB];
+          if (ref_re) {
+#pragma unroll
+            for (int u = 0; u < LB; ++u) {
+              const int k = kb + u * jstep;
+              const long long off = base + (long long)k * nstride;
+              rb[u] = (k < n && eqk::in_bounds(off, fd.V, a.err))
+                          ? T2{ld_elem(ref_re, off, true), ld_elem(ref_re, off + fd.V, true)}
+                          : T2{T(0), T(0)};
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < LB; ++u) {
+            const int k = kb + u * jstep;
+            if (k >= n) break;
+            const long long off = base + (long long)k * nstride;
+            if (!eqk::in_bounds(off, fd.V, a.err)) continue;
+            const T2 y = tile[k * SD_PITCH + lc];
+            st_elem(out_re, off, y.x, out64);
+            st_elem(out_im, off, y.y, out64);
+            if (ref_re) {
+              linf = fmax(linf, fabs(rb[u].x - y.x));
+              linf = fmax(linf, fabs(rb[u].y - y.y));
+            }
+          }
+        }
+      }
+      __syncthreads();                                      // the tile is free for the next one
+    }
+    if (a.mode == 1) {
+      double v[4] = {sa.value(), sb.value(), sq.value(), double(nonfinite)};
+      warp_partials<4>(v, a.partials + item * WARPS_MAX * 4);
+      for (int k = nw * 4 + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
+        a.partials[item * WARPS_MAX * 4 + k] = 0.0;
+    } else if (a.mode == 2) {
+      double v = double(linf);
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o2));
+      if ((threadIdx.x & 31) == 0) a.partials[item * WARPS_MAX * 4 + (threadIdx.x >> 5)] = v;
+      for (int k = nw + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
         a.partials[item * WARPS_MAX * 4 + k] = 0.0;
     }
   }

@@ -177,6 +177,7 @@ struct GenPlan {
   GenTune tune;
   std::string key;             // tuning-cache key
   int tw256 = -1, w512 = -1;   // complex-pool offsets of the paired-transform tables
+  bool dd = false;             // FP64 plan in double-float arithmetic (tables, kernels, HBM pairs)
 };
 
 namespace {
@@ -367,9 +368,10 @@ void canonical_pairs(int ny, int nz, std::vector<int>& out) {
   }
 }
 
-cudaError_t occupancy(eq_dtype dt, int kind, int threads, size_t smem, int* blocks) {
-  return dt == EQ_F32 ? gen_occupancy_f32(kind, threads, smem, blocks)
-                      : gen_occupancy_f64(kind, threads, smem, blocks);
+cudaError_t occupancy(const GenPlan* g, int kind, int threads, size_t smem, int* blocks) {
+  if (g->dd) return gen_occupancy_dd(kind, threads, smem, blocks);
+  return g->dtype == EQ_F32 ? gen_occupancy_f32(kind, threads, smem, blocks)
+                            : gen_occupancy_f64(kind, threads, smem, blocks);
 }
 
 }  // namespace
@@ -388,7 +390,16 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
   for (int i = 0; i < 3 * count; ++i) lens.push_back(dims[i]);
   std::vector<unsigned char> cpool, xipool;
   std::map<int, int> axis_of_len;
+  // FP64 in double-float arithmetic where every length has a 256- or 512-point register
+  // transform (512, or at most 256); EQ_F64_ARITH=native keeps FP64 instructions (measurements)
+  if (dtype == EQ_F64) {
+    const char* ar = getenv("EQ_F64_ARITH");
+    bool ok = !(ar && std::string(ar) == "native");
+    for (int n : lens) ok = ok && (n == 512 || n <= 256);
+    g->dd = ok;
+  }
   if (dtype == EQ_F32) build_tables<float>(g, lens, cpool, axis_of_len);
+  else if (g->dd) build_tables<eqk::dd>(g, lens, cpool, axis_of_len);
   else build_tables<double>(g, lens, cpool, axis_of_len);
   std::map<std::pair<int, int>, int> xi_of;   // (axis, n) -> offset
   std::map<std::pair<int, int>, std::pair<int, int>> pairs_of;   // (ny, nz) -> (offset, count)
@@ -410,6 +421,7 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
       if (!xi_of.count(key)) {
         xi_of[key] = int(xipool.size() / es);
         if (dtype == EQ_F32) xi_table<float>(xipool, n3[a], hs[a], o.op);
+        else if (g->dd) xi_table<eqk::dd>(xipool, n3[a], hs[a], o.op);
         else xi_table<double>(xipool, n3[a], hs[a], o.op);
       }
       fd.xi[a] = xi_of[key];
@@ -440,7 +452,7 @@ eq_status gen_plan_create(const int* dims, int count, eq_dtype dtype, const eq_p
     for (char& c : gpu) if (c == '"' || c == '\\') c = '_';
     char buf[512];
     snprintf(buf, sizeof(buf), "gen|%s|op%d|nyq%d|%.6g,%.6g,%.6g|n%d|%016llx|%s|%d",
-             dtype == EQ_F32 ? "f32" : "f64", (int)o.op, (int)o.nyq, o.hx, o.hy, o.hz, count, h,
+             dtype == EQ_F32 ? "f32" : (g->dd ? "f64dd" : "f64"), (int)o.op, (int)o.nyq, o.hx, o.hy, o.hz, count, h,
              gpu.c_str(), sms);
     g->key = buf;
   }
@@ -531,10 +543,11 @@ GenTune gen_default_tune(const GenPlan* g) {
   GenTune t;
   t.zc = es == 4 ? (g->mx[2] > 256 ? 8 : 16) : (g->mx[2] > 256 ? 4 : 8);
   t.yc = es == 4 ? (g->mx[1] > 256 ? 8 : 16) : (g->mx[1] > 256 ? 4 : 8);
-  if (scols_supported(g, 2)) t.zc = 0;
-  if (scols_supported(g, 1)) t.yc = 0;
+  if (scols_supported(g, 2) || g->dd) t.zc = 0;
+  if (scols_supported(g, 1) || g->dd) t.yc = 0;
   t.zt = t.yt = 256;
   t.xp = xrows_supported(g) ? (es == 4 ? 4 : 0) : (g->mx[0] > 256 ? 1 : 2);
+  if (g->dd) t.zt = t.yt = SD_THREADS;
   return t;
 }
 
@@ -546,7 +559,15 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
   PassShape z = g->z, y = g->y, x = g->x;
   z.kind = 0; z.mmax = g->mx[2]; z.cols = t.zc; z.pitch = t.zc; z.threads = t.zt;
   y.kind = 0; y.mmax = g->mx[1]; y.cols = t.yc; y.pitch = t.yc; y.threads = t.yt;
-  for (int axis = 1; axis <= 2; ++axis) {
+  if (g->dd && (t.zc != 0 || t.yc != 0 || t.xp != 0)) {
+    *err = "double-float plans run the warp-per-column strided and warp-per-row x kernels only";
+    return EQ_ERR_INVALID;
+  }
+  for (int axis = 1; axis <= 2 && g->dd; ++axis) {
+    PassShape& p = axis == 2 ? z : y;
+    p.kind = 4; p.cols = SD_COLS; p.pitch = SD_PITCH; p.threads = SD_THREADS;
+  }
+  for (int axis = 1; axis <= 2 && !g->dd; ++axis) {
     PassShape& p = axis == 2 ? z : y;
     if ((axis == 2 ? t.zc : t.yc) != 0) continue;
     if (!scols_supported(g, axis)) {
@@ -576,8 +597,9 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
   }
   PassShape* ps[3] = {&z, &y, &x};
   for (PassShape* p : ps) {
-    p->smem = p->kind == 3   ? (g->dtype == EQ_F32 ? xrows_smem<float>() : xrows_smem<double>())
-              : p->kind == 4 ? scols_smem()
+    p->smem = p->kind == 3   ? (g->dtype == EQ_F32 ? xrows_smem<float>()
+                                : g->dd ? xrows_smem<eqk::dd>() : xrows_smem<double>())
+              : p->kind == 4 ? (g->dd ? scold_smem<eqk::dd>() : scols_smem())
               : p->kind == 6 ? xpair_smem()
                              : (2 * (size_t)p->mmax * p->pitch + 3 * (size_t)p->mmax) * cs;
     if (p->smem > limit || p->threads > 512 || p->threads % p->cols != 0 || p->cols < 1) {
@@ -590,8 +612,8 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
   for (int pi = 0; pi < 3; ++pi) {
     PassShape* p = ps[pi];
     int blocks = 0;
-    cudaError_t e = occupancy(g->dtype, p->kind, p->threads, p->smem, &blocks);
-    if (e == cudaSuccess && pi < 2) e = occupancy(g->dtype, p->kind + 1, p->threads, p->smem, &blocks);
+    cudaError_t e = occupancy(g, p->kind, p->threads, p->smem, &blocks);
+    if (e == cudaSuccess && pi < 2) e = occupancy(g, p->kind + 1, p->threads, p->smem, &blocks);
     if (e != cudaSuccess || blocks < 1) {
       cudaGetLastError();
       *err = std::string("occupancy: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "0 blocks");
@@ -603,7 +625,7 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
       if (pi == 2) total_tiles += (fd.npairs + (p->cols / 6) - 1) / (p->cols / 6);
       else {
         const long long ncols = pi == 0 ? (long long)fd.nx * fd.ny : (long long)fd.nz * fd.nx;
-        const int cols = p->kind == 4 ? scols_cols(g->ah[fd.ax[pi == 0 ? 2 : 1]].n) : p->cols;
+        const int cols = p->kind == 4 && !g->dd ? scols_cols(g->ah[fd.ax[pi == 0 ? 2 : 1]].n) : p->cols;
         total_tiles += 3 * ((ncols + cols - 1) / cols);
       }
     }
@@ -617,7 +639,7 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
         items = (groups + p->tpi - 1) / p->tpi;
       } else {
         const long long ncols = pi == 0 ? (long long)fd.nx * fd.ny : (long long)fd.nz * fd.nx;
-        const int cols = p->kind == 4 ? scols_cols(g->ah[fd.ax[pi == 0 ? 2 : 1]].n) : p->cols;
+        const int cols = p->kind == 4 && !g->dd ? scols_cols(g->ah[fd.ax[pi == 0 ? 2 : 1]].n) : p->cols;
         const long long ntiles = (ncols + cols - 1) / cols;
         items = 3 * ((ntiles + p->tpi - 1) / p->tpi);
       }
@@ -671,6 +693,7 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], s); };
   const bool f32 = g->dtype == EQ_F32;
   auto launch = [&](int kind, const GenArgs& a, const PassShape& p) {
+    if (g->dd) return gen_launch_dd(kind, a, p.grid, p.threads, p.smem, s);
     return f32 ? gen_launch_f32(kind, a, p.grid, p.threads, p.smem, s)
                : gen_launch_f64(kind, a, p.grid, p.threads, p.smem, s);
   };
@@ -690,6 +713,7 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   // z forward (d_in -> d_out) with input statistics
   shape(g->z);
   a.in = d_in; a.out = d_out; a.ref = nullptr; a.partials = g->part_first; a.axis = 2; a.mode = 1;
+  a.io = g->dd ? 1 : 0;
   if ((e = launch(g->z.kind, a, g->z)) != cudaSuccess) { *err = std::string("z forward: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
   mark(1);
   k_gen_finalize_mean<<<g->F, FIN_THREADS, 0, s>>>(g->part_first, g->z.item0, g->fields, g->F,
@@ -697,7 +721,7 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   if ((e = cudaGetLastError()) != cudaSuccess) { *err = std::string("mean: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
   mark(2);
   shape(g->y);
-  a.in = d_out; a.partials = nullptr; a.axis = 1; a.mode = 0;
+  a.in = d_out; a.partials = nullptr; a.axis = 1; a.mode = 0; a.io = 0;
   if ((e = launch(g->y.kind, a, g->y)) != cudaSuccess) { *err = std::string("y forward: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
   mark(3);
   shape(g->x);
@@ -711,6 +735,7 @@ eq_status gen_enqueue(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s,
   const bool linf = g->opts.want_linf && d_in != d_out;
   shape(g->z);
   a.ref = linf ? d_in : nullptr; a.partials = g->part_last; a.axis = 2; a.mode = linf ? 2 : 0;
+  a.io = g->dd ? 2 : 0;
   if ((e = launch(g->z.kind + 1, a, g->z)) != cudaSuccess) { *err = std::string("z inverse: ") + cudaGetErrorString(e); return EQ_ERR_CUDA; }
   mark(6);
   k_gen_finalize_norms<<<g->F, FIN_THREADS, 0, s>>>(
@@ -816,11 +841,13 @@ static float time_pass(GenPlan* g, int which, const void* d_in, void* d_out, cud
   a.axis = which == 0 ? 2 : 1;
   a.mode = which == 0 ? 1 : 0;
   a.partials = which == 0 ? g->part_first : (which == 2 ? g->part_x : nullptr);
+  a.io = g->dd && which == 0 ? 1 : 0;
   const int kind = p.kind;
   float best[3];
   for (int r = 0; r < 4; ++r) {
     cudaEventRecord(e0, s);
-    if (g->dtype == EQ_F32) gen_launch_f32(kind, a, p.grid, p.threads, p.smem, s);
+    if (g->dd) gen_launch_dd(kind, a, p.grid, p.threads, p.smem, s);
+    else if (g->dtype == EQ_F32) gen_launch_f32(kind, a, p.grid, p.threads, p.smem, s);
     else gen_launch_f64(kind, a, p.grid, p.threads, p.smem, s);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);

@@ -13,6 +13,8 @@ cudaError_t gen_occupancy_f32(int kind, int threads, size_t smem, int* blocks);
 cudaError_t gen_occupancy_f64(int kind, int threads, size_t smem, int* blocks);
 cudaError_t gen_launch_f32(int kind, const GenArgs& a, int grid, int threads, size_t smem, cudaStream_t s);
 cudaError_t gen_launch_f64(int kind, const GenArgs& a, int grid, int threads, size_t smem, cudaStream_t s);
+cudaError_t gen_occupancy_dd(int kind, int threads, size_t smem, int* blocks);
+cudaError_t gen_launch_dd(int kind, const GenArgs& a, int grid, int threads, size_t smem, cudaStream_t s);
 
 struct GenPlan;
 

@@ -14,7 +14,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "eq_fft.cuh"
+#include "eq_dd.cuh"
 
 namespace eqk {
 
@@ -353,6 +356,35 @@ __device__ __forceinline__ void project_pair(T2 (&a)[3], T2 (&bb)[3], T xi0, T x
   if constexpr (sizeof(T) == 4) {
     project_pair_f32x2(a, bb, xi0, xi1, xi2, zero_mode, zm, nyq_zero, compat, inv_v, mult,
                        r2, di2, do2, o2);
+  } else if constexpr (std::is_same<T, double>::value) {
+    // FP64: the same arithmetic in double-float (FP32 instructions, about 2^-48 relative per
+    // operation), inputs and outputs converted on the bits.  FP64 instructions issue at a small
+    // fraction of the FP32 rate on this GPU, and this is the FP64 path's densest arithmetic.
+    dd2 ad[3], bd[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ad[c] = dd2{dd_from_bits(a[c].x), dd_from_bits(a[c].y)};
+      bd[c] = dd2{dd_from_bits(bb[c].x), dd_from_bits(bb[c].y)};
+    }
+    dd zmd[6];
+    const bool zmode = zero_mode && zm;
+    if (zmode) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) zmd[j] = dd_from_bits(zm[j]);
+    }
+    PlainSum<dd> pr, pdi, pdo, po;
+    project_pair<dd, dd2>(ad, bd, dd_from_bits(xi0), dd_from_bits(xi1), dd_from_bits(xi2),
+                          zero_mode, zmode ? zmd : nullptr, nyq_zero, compat, dd_from_bits(inv_v),
+                          dd_from_bits(mult), pr, pdi, pdo, po);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      a[c] = T2{dd_to_bits(ad[c].x), dd_to_bits(ad[c].y)};
+      bb[c] = T2{dd_to_bits(bd[c].x), dd_to_bits(bd[c].y)};
+    }
+    r2.add(dd_to_bits(pr.s));
+    di2.add(dd_to_bits(pdi.s));
+    do2.add(dd_to_bits(pdo.s));
+    o2.add(dd_to_bits(po.s));
   } else {
     // 2 S_2c = A + conj B, 2 S_2c+1 = -i (A - conj B)
     T sr[6], si[6];
