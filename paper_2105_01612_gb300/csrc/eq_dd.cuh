@@ -19,9 +19,9 @@
 
 #include <cmath>
 
-#include "eq_fft.cuh"
-
 namespace eqk {
+
+template <typename T> struct V2;    // complex type of a real type (eq_fft.cuh)
 
 #if defined(__CUDA_ARCH__)
 __device__ __forceinline__ float dd_add(float a, float b) { return __fadd_rn(a, b); }

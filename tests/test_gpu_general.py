@@ -196,3 +196,33 @@ def test_every_pass_kernel_choice_matches_the_oracle(tmp_path, monkeypatch):
     for o, r in zip(plan.unpack(out), refs):
         assert rel(o.double().cpu().numpy(), r) <= 2e-6
     plan.close()
+
+
+def test_fp64_runtime_length_plans_in_double_float_match_the_oracle(monkeypatch):
+    """FP64 runtime-length plans whose lengths are 512 or at most 256 run every pass in
+    double-float arithmetic (FP64 at the ends, FP32 pairs between the passes).  Their results and
+    norms agree with the FP64 oracle to 1e-12 and with the FP64-instruction passes to 1e-13."""
+    dims = [(24, 20, 18), (130, 5, 256), (7, 256, 129), (512, 4, 6), (1, 1, 7)]
+    fields = [voronoi_stress_field((nz, ny, nx), 6, 100.0, 5.0, 7300 + i, dtype=torch.float64)
+              for i, (nx, ny, nz) in enumerate(dims)]
+    results = {}
+    for arith in ("native", "paired"):
+        if arith == "native":
+            monkeypatch.setenv("EQ_F64_ARITH", "native")
+        else:
+            monkeypatch.delenv("EQ_F64_ARITH", raising=False)
+        plan = eq.VarlenPlan(dims, torch.float64, "ddo")
+        flat = plan.pack([f.cuda() for f in fields])
+        out = torch.empty_like(flat)
+        plan.project(flat, out)
+        results[arith] = ([o.cpu().numpy() for o in plan.unpack(out)], plan.norms())
+        plan.close()
+    for i, f in enumerate(fields):
+        ref = oracle.project(f.numpy(), "ddo")
+        ref_n = oracle.norms(f.numpy(), ref, "ddo")
+        o, nrm = results["paired"][0][i], results["paired"][1][i]
+        assert rel(o, ref) <= 1e-12, dims[i]
+        assert rel(o, results["native"][0][i]) <= 1e-13, dims[i]
+        for k in ("norm_in", "norm_out", "resid_l2"):
+            assert abs(nrm[k] - ref_n[k]) <= 1e-12 * ref_n["norm_in"], (dims[i], k)
+        assert nrm["div_out_l2"] <= 1e-12 * nrm["div_in_l2"]
