@@ -310,6 +310,12 @@ struct eq_plan {
   int tcap = 0, tused = 0;
   // runtime-length path (sizes other than powers of two, uneven batches); null = fast path
   eqg::GenPlan* gen = nullptr;
+  // FP64 plans with every length 512 or at most 256: plain projections run the runtime-length
+  // passes in double-float arithmetic (this sub-plan); the Hodge and padded forms keep the FP64
+  // passes of this plan
+  eqg::GenPlan* ddgen = nullptr;
+  bool native_only = false;   // set while a padded projection runs: FP64 instructions throughout
+  bool g_dd = false;          // the captured graph's passes were the double-float ones
   long long total_elems = 0;   // elements of one call's buffer (all fields, 6 planes)
   // captured CUDA graph of the passes for one (d_in, d_out) pair
   cudaStream_t cap = nullptr;
@@ -529,15 +535,20 @@ bool try_tma(eq_plan* p, bool on, int axis, bool inv, int mode, const void* src,
 // (eq_project_padded): the first z pass reads d_in with zeros past its edges into the plan's
 // padded workspace, the middle passes work there, and the last z pass writes the specimen region
 // of the result into d_final.  Needs the TMA z passes with tiled stores (checked by the caller).
+// Plain projections of FP64 plans with a double-float sub-plan run its passes.
+bool use_dd(const eq_plan* p, const void* d_y, const int* spec) {
+  return p->ddgen && !p->native_only && !d_y && !spec;
+}
+
 eq_status enqueue_passes(eq_plan* p, const void* d_in, void* d_final, cudaStream_t s, void* d_y,
                          const int* spec) {
   const bool f32 = p->dtype == EQ_F32;
   void* d_out = spec ? p->pad_ws : d_final;
   cudaEvent_t* ev = nullptr;
   if (p->tused < p->tcap) ev = &p->tev[(size_t)p->tused++ * (EQ_NUM_PASSES + 1)];
-  if (p->gen) {
+  if (p->gen || use_dd(p, d_y, spec)) {
     std::string err;
-    eq_status st = eqg::gen_enqueue(p->gen, d_in, d_out, s, ev, &err);
+    eq_status st = eqg::gen_enqueue(p->gen ? p->gen : p->ddgen, d_in, d_out, s, ev, &err);
     if (st != EQ_OK) return fail(st, "eq_project: " + err);
     return EQ_OK;
   }
@@ -739,9 +750,11 @@ eq_status enqueue_passes(eq_plan* p, const void* d_in, void* d_final, cudaStream
 }
 
 // The norms of the last call (and the error flag) into the plan's host mirror.
-eq_status publish(eq_plan* p, cudaStream_t s) {
-  const eq_norms_t* src = p->gen ? eqg::gen_norms_device(p->gen) : p->norms;
-  k_publish<<<1, 128, 0, s>>>(src, p->batch, p->err, p->hnorms_dev, p->herr_dev);
+eq_status publish(eq_plan* p, cudaStream_t s, bool dd = false) {
+  const eq_norms_t* src = p->gen ? eqg::gen_norms_device(p->gen)
+                                 : (dd ? eqg::gen_norms_device(p->ddgen) : p->norms);
+  int* err = dd ? eqg::gen_err_device(p->ddgen) : p->err;
+  k_publish<<<1, 128, 0, s>>>(src, p->batch, err, p->hnorms_dev, p->herr_dev);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? EQ_OK : fail_cuda(e, "norms publish");
 }
@@ -750,7 +763,7 @@ eq_status publish(eq_plan* p, cudaStream_t s) {
 eq_status enqueue(eq_plan* p, const void* d_in, void* d_final, cudaStream_t s, void* d_y = nullptr,
                   const int* spec = nullptr) {
   eq_status st = enqueue_passes(p, d_in, d_final, s, d_y, spec);
-  return st == EQ_OK ? publish(p, s) : st;
+  return st == EQ_OK ? publish(p, s, use_dd(p, d_y, spec)) : st;
 }
 
 // Mapped pinned memory for the host mirror of the norms and the error flag.
@@ -780,7 +793,8 @@ eq_status run(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, void* d
   const bool timed = p->tused < p->tcap;
   const int sp[3] = {spec ? spec[0] : 0, spec ? spec[1] : 0, spec ? spec[2] : 0};
   if (p->opts.graph && !timed) {
-    if (!p->gexec || p->g_in != d_in || p->g_out != d_out || p->g_y != d_y ||
+    const bool dd = use_dd(p, d_y, spec);
+    if (!p->gexec || p->g_in != d_in || p->g_out != d_out || p->g_y != d_y || p->g_dd != dd ||
         p->g_spec[0] != sp[0] || p->g_spec[1] != sp[1] || p->g_spec[2] != sp[2]) {
       if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
       if (!p->cap && (e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess)
@@ -798,6 +812,7 @@ eq_status run(eq_plan* p, const void* d_in, void* d_out, cudaStream_t s, void* d
       p->g_in = d_in;
       p->g_out = d_out;
       p->g_y = d_y;
+      p->g_dd = dd;
       for (int i = 0; i < 3; ++i) p->g_spec[i] = sp[i];
     }
     if ((e = cudaGraphLaunch(p->gexec, s)) != cudaSuccess) return fail_cuda(e, "graph launch");
@@ -821,6 +836,7 @@ void release(eq_plan* p) {
   if (p->stage) cudaFree(p->stage);
   if (p->pad_ws) cudaFree(p->pad_ws);
   if (p->gen) eqg::gen_destroy(p->gen);
+  if (p->ddgen) eqg::gen_destroy(p->ddgen);
   delete p;
 }
 
@@ -1057,6 +1073,23 @@ eq_status eq_plan_create(int nx, int ny, int nz, eq_dtype dtype, int batch,
     release(p);
     return fail_cuda(e, "cudaEventCreate");
   }
+  if (dtype == EQ_F64) {                 // the double-float sub-plan of plain projections
+    std::vector<int> dims;
+    for (int b = 0; b < batch; ++b) { dims.push_back(nx); dims.push_back(ny); dims.push_back(nz); }
+    std::string err;
+    eqg::GenPlan* g = nullptr;
+    if (eqg::gen_plan_create(dims.data(), batch, dtype, o, p->sms, &g, &err) == EQ_OK) {
+      if (eqg::gen_is_dd(g)) {
+        p->ddgen = g;
+        p->dbytes += eqg::gen_device_bytes(g);
+      } else {
+        eqg::gen_destroy(g);
+      }
+    } else {
+      cudaGetLastError();
+      eqk::log(1, "eq_plan_create: no double-float sub-plan (%s)", err.c_str());
+    }
+  }
   eqk::log(1, "eq_plan_create %dx%dx%d %s batch %d: z %s variant %d grid %d, y %s variant %d grid %d, "
               "x %s variant %d grid %d, %zu workspace bytes",
            nx, ny, nz, dtype == EQ_F32 ? "f32" : "f64", batch, p->tma_z ? "tma" : "plain", p->vz,
@@ -1167,7 +1200,9 @@ eq_status eq_project_padded(eq_plan* p, int sx, int sy, int sz, const void* d_in
     k_pad<double><<<pgrid, 256, 0, s>>>(static_cast<const double*>(d_in), static_cast<double*>(p->pad_ws),
                                          sx, sy, sz, p->nx, p->ny, p->nz, rows);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "eq_project_padded: pad");
+  p->native_only = true;                 // padded projections: FP64 instructions in both forms
   eq_status st = run(p, p->pad_ws, p->pad_ws, s);
+  p->native_only = false;
   if (st != EQ_OK) return st;
   dim3 cgrid(PAD_GRID, p->batch);
   if (p->dtype == EQ_F32)

@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
 // the chirp transform, inverse transform, post-chirp; the inverse direction by conjugation), and
 // writes the n outputs back into the tile, which leaves by coalesced stores (with the L-infinity
 // residual of the last pass).  All fields of a launch have their axis served (wm in {256, 512}).
-constexpr int SD_COLS = 8, SD_WARPS = 8, SD_THREADS = 32 * SD_WARPS, SD_PITCH = SD_COLS + 1;
+constexpr int SD_COLS = 16, SD_WARPS = 8, SD_THREADS = 32 * SD_WARPS, SD_PITCH = SD_COLS + 1;
 constexpr int SD_MAXN = 512;          // longest column (n = wm = 512)
 template <typename T> constexpr size_t scold_smem() {
   return 2 * sizeof(T) * (size_t(SD_MAXN) * SD_PITCH + 256 + 512) +   // tile, chirp, chirp transform

@@ -904,6 +904,7 @@ eq_status gen_autotune(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s
   return EQ_OK;
 }
 size_t gen_device_bytes(const GenPlan* g) { return g->dbytes + g->wbytes; }
+bool gen_is_dd(const GenPlan* g) { return g->dd; }
 long long gen_total_elems(const GenPlan* g) { return g->total_elems; }
 int gen_count(const GenPlan* g) { return g->F; }
 

@@ -47,6 +47,7 @@ eq_status gen_autotune(GenPlan* g, const void* d_in, void* d_out, cudaStream_t s
 bool gen_cache_lookup(const GenPlan* g, GenTune* t);
 GenTune gen_current_tune(const GenPlan* g);
 size_t gen_device_bytes(const GenPlan* g);
+bool gen_is_dd(const GenPlan* g);           // FP64 plan in double-float arithmetic
 long long gen_total_elems(const GenPlan* g);   // 6 * sum of voxels
 int gen_count(const GenPlan* g);
 void gen_destroy(GenPlan* g);
