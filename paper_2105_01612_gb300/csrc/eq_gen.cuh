@@ -783,7 +783,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
 // FP64 plans in double-float arithmetic (FP64 in HBM at the pipeline's ends: the first pass
 // converts its loads, the last its stores and the residual's re-read input; double-float pairs
 // between the passes).  Same items, partial records and modes as k_gen_strided.  One block of
-// SD_WARPS warps per SM (254 registers, no spills).  A tile of SD_COLS adjacent columns (n points
+// SD_WARPS warps per SM.  A tile of SD_COLS adjacent columns (n points
 // each) comes into shared memory by coalesced loads (SD_COLS consecutive elements of a plane per
 // point), eight loads in flight a thread; each warp then takes whole columns: lane l
 // holds points l + 32 e of a length-wm register transform (radix-8 stages through the warp's own
@@ -791,76 +791,137 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
 // the chirp transform, inverse transform, post-chirp; the inverse direction by conjugation), and
 // writes the n outputs back into the tile, which leaves by coalesced stores (with the L-infinity
 // residual of the last pass).  All fields of a launch have their axis served (wm in {256, 512}).
-constexpr int SD_COLS = 16, SD_WARPS = 8, SD_THREADS = 32 * SD_WARPS, SD_PITCH = SD_COLS + 1;
+constexpr int SD_COLS = 16, SD_WARPS = 16, SD_THREADS = 32 * SD_WARPS, SD_PITCH = SD_COLS + 1;
 constexpr int SD_MAXN = 512;          // longest column (n = wm = 512)
 template <typename T> constexpr size_t scold_smem() {
-  return 2 * sizeof(T) * (size_t(SD_MAXN) * SD_PITCH + 256 + 512) +   // tile, chirp, chirp transform
-         sizeof(T) * (size_t(SD_WARPS) * 2 * 512 + 2 * eqk::staged_size(512));
+  return 2 * sizeof(T) * (size_t(SD_MAXN) * SD_PITCH + 256 + 512 + 256) +  // tile, chirps, W512^j
+         sizeof(T) * (size_t(SD_WARPS) * 2 * 256 + 2 * eqk::staged_size(256));  // rows, twiddles
 }
 
-template <typename T, int M, bool INV>
-__device__ __forceinline__ void scold_transform(typename eqk::V2<T>::t* tile, int col, int n,
-                                               const eqk::SoaAcc<T>& acc,
-                                               const eqk::TwStaged<T>& tw,
-                                               const typename eqk::V2<T>::t* chs,
-                                               const typename eqk::V2<T>::t* bhs, int* err) {
-  using T2 = typename eqk::V2<T>::t;
-  constexpr int E = M / 32;
+// One sequence of a double-float pass (a tile column, or an x row), element j at base[j pitch]
+// (j pitch < lim), transformed in place through a single compiled
+// 256-point forward transform (its code, executed for each half, keeps the instruction working set
+// small): the inverse direction by conjugation of input and output; a 512-point column through
+// the decimation-in-frequency split a_j = u_j + u_{j+256}, b_j = (u_j - u_{j+256}) W512^j, the two
+// halves one after the other (outputs 2k and 2k + 1); Bluestein's convolution (n <= 256) with
+// transform length wm = 512 from the same split (u_{j+256} = 0), keeping only the outputs j < n
+// of its inverse transform, y_j = P_j + W512^-j Q_j, or with wm = 256 directly.
+template <bool INV>
+__device__ __forceinline__ void dd_seq(eqk::dd2* base, int pitch, long long lim, int n, int wm,
+                                       const eqk::SoaAcc<eqk::dd>& acc,
+                                       const eqk::TwStaged<eqk::dd>& tw, const eqk::dd2* w512,
+                                       const eqk::dd2* chs, const eqk::dd2* bhs, int* err) {
+  using T = eqk::dd;
+  using T2 = eqk::dd2;
   const int lane = threadIdx.x & 31;
-  const bool blue = n != M;
-  T2 x[E];
+  const bool blue = n != wm, split = wm == 512;
+  auto conj = [](T2 v) { return T2{v.x, -v.y}; };
+  auto ld = [&](int j) {
+    return eqk::in_bounds((long long)j * pitch, lim, err) ? base[j * pitch] : T2{T(0), T(0)};
+  };
+  // the forward 256-point transform of x, or with inv the unnormalised inverse by conjugation
+  auto fft = [&](T2 (&x)[8], bool inv) {
+    if (inv) {
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int j = lane + 32 * e;
-    x[e] = T2{T(0), T(0)};
-    if (j < n && eqk::in_bounds((long long)j * SD_PITCH + col, (long long)SD_MAXN * SD_PITCH, err)) {
-      x[e] = tile[j * SD_PITCH + col];
+      for (int e = 0; e < 8; ++e) x[e] = conj(x[e]);
+    }
+    __syncwarp();                                          // the warp's row is free
+    eqk::fft_column_acc<256, 8, false, 0, true>(x, lane, acc, tw);
+    if (inv) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) x[e] = conj(x[e]);
+    }
+  };
+  T2 keep[8];
+#pragma unroll 1
+  for (int h = 0; h < (split ? 2 : 1); ++h) {
+    T2 x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int j = lane + 32 * e;
+      T2 u0 = j < n ? ld(j) : T2{T(0), T(0)}, u1 = T2{T(0), T(0)};
       if (blue) {
-        if (INV) x[e].y = -x[e].y;
-        x[e] = cmul(x[e], chs[j]);
+        if (INV) u0 = conj(u0);
+        u0 = cmul(u0, chs[j < n ? j : 0]);
+      } else if (split) {
+        u1 = ld(j + 256);
+      }
+      if (split && h == 1) {
+        const T2 w = w512[j];
+        x[e] = cmul(csub(u0, u1), (INV && !blue) ? conj(w) : w);
+      } else {
+        x[e] = split ? cadd(u0, u1) : u0;
       }
     }
-  }
-  __syncwarp();                                             // the warp's row is free
-  if (blue) {
-    eqk::fft_column_acc<M, E, false, 0, true>(x, lane, acc, tw);
+    if (blue) {
+      fft(x, false);
 #pragma unroll
-    for (int e = 0; e < E; ++e) x[e] = cmul(x[e], bhs[lane + 32 * e]);
-    __syncwarp();
-    eqk::fft_column_acc<M, E, true, 0, true>(x, lane, acc, tw);
-  } else {
-    eqk::fft_column_acc<M, E, INV, 0, true>(x, lane, acc, tw);
-  }
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int k = lane + 32 * e;
-    if (k < n) {
-      T2 y = x[e];
-      if (blue) {
-        y = cmul(y, chs[k]);
-        if (INV) y.y = -y.y;
+      for (int e = 0; e < 8; ++e) {                    // the chirp transform at k (or 2k + h)
+        const int k = lane + 32 * e;
+        x[e] = cmul(x[e], bhs[split ? 2 * k + h : k]);
       }
-      tile[k * SD_PITCH + col] = y;
+      fft(x, true);
+    } else {
+      fft(x, INV);
+    }
+    if (h == 0) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) keep[e] = x[e];
+    }
+    if (!split || h == 1) {                            // all reads of the column are done
+      __syncwarp();
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = lane + 32 * e;
+        if (blue) {
+          if (k < n) {
+            T2 y = split ? cadd(keep[e], cmul(x[e], conj(w512[k]))) : x[e];
+            y = cmul(y, chs[k]);
+            base[k * pitch] = INV ? conj(y) : y;
+          }
+        } else if (split) {
+          base[(2 * k) * pitch] = keep[e];
+          base[(2 * k + 1) * pitch] = x[e];
+        } else {
+          base[k * pitch] = x[e];
+        }
+      }
     }
   }
   __syncwarp();
 }
 
+// running double-float sum (its 48-bit significand holds a thread's partial sums of a pass
+// without compensation); read out as FP64
+struct DdSum {
+  eqk::dd s = eqk::dd(0.f, 0.f);
+  __device__ __forceinline__ void add(eqk::dd v) { s = s + v; }
+  __device__ __forceinline__ double value() const { return double(s); }
+};
+
 template <typename T, bool INV>
 __global__ void __launch_bounds__(SD_THREADS, 1) k_gen_scold(const GenArgs a) {
   using T2 = typename eqk::V2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int TWS = eqk::staged_size(512);
+  constexpr int TWS = eqk::staged_size(256);
   T2* tile = reinterpret_cast<T2*>(smem_raw);               // [point][SD_PITCH]
   T2* chs = tile + SD_MAXN * SD_PITCH;
   T2* bhs = chs + 256;
-  T* rows = reinterpret_cast<T*>(bhs + 512);                // [warp][re 512 | im 512]
-  T* twc = rows + SD_WARPS * 2 * 512;
+  T2* w512 = bhs + 512;
+  T* rows = reinterpret_cast<T*>(w512 + 256);               // [warp][re 256 | im 256]
+  T* twc = rows + SD_WARPS * 2 * 256;
   T* tws = twc + TWS;
   const T2* cpool = reinterpret_cast<const T2*>(a.cpool);
-  const int tid = threadIdx.x, w = tid >> 5, nw = SD_WARPS;
+  const int tid = threadIdx.x, w = tid >> 5;
   const int lc = tid % SD_COLS, lj = tid / SD_COLS, jstep = SD_THREADS / SD_COLS;
-  const eqk::SoaAcc<T> acc{rows + w * 2 * 512, rows + w * 2 * 512 + 512};
+  const eqk::SoaAcc<T> acc{rows + w * 2 * 256, rows + w * 2 * 256 + 256};
+  for (int i = tid; i < TWS; i += blockDim.x) {          // the 256-point transform's twiddles
+    const T2 t = cpool[a.tw256 + i];
+    twc[i] = t.x;
+    tws[i] = t.y;
+  }
+  for (int i = tid; i < 256; i += blockDim.x) w512[i] = cpool[a.w512 + i];
+  const eqk::TwStaged<T> tw{twc, tws};
   int cur_ax = -1;
   for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
     const int f = find_field(a.item0, a.nfields, item);
@@ -868,14 +929,8 @@ __global__ void __launch_bounds__(SD_THREADS, 1) k_gen_scold(const GenArgs a) {
     const int axi = fd.ax[a.axis];
     const AxisPlan& ap = a.axes[axi];
     const int n = ap.n, wm = ap.wm;
-    if (axi != cur_ax) {                  // tables of this axis length into shared memory
+    if (axi != cur_ax) {                  // chirp tables of this axis length into shared memory
       __syncthreads();
-      const int ts = eqk::staged_size(wm);
-      for (int i = tid; i < ts; i += blockDim.x) {
-        const T2 t = cpool[ap.wtw + i];
-        twc[i] = t.x;
-        tws[i] = t.y;
-      }
       if (wm != n) {
         for (int i = tid; i < n; i += blockDim.x) chs[i] = cpool[ap.wchirp + i];
         for (int i = tid; i < wm; i += blockDim.x) bhs[i] = cpool[ap.wbhat + i];
@@ -883,7 +938,6 @@ __global__ void __launch_bounds__(SD_THREADS, 1) k_gen_scold(const GenArgs a) {
       __syncthreads();
       cur_ax = axi;
     }
-    const eqk::TwStaged<T> tw{twc, tws};
     long long inner, nstride, outer_stride, ncols;
     if (a.axis == 2) { inner = (long long)fd.nx * fd.ny; nstride = inner; outer_stride = 0; ncols = inner; }
     else { inner = fd.nx; nstride = fd.nx; outer_stride = (long long)fd.nx * fd.ny; ncols = (long long)fd.nz * fd.nx; }
@@ -898,7 +952,7 @@ __global__ void __launch_bounds__(SD_THREADS, 1) k_gen_scold(const GenArgs a) {
     T* out_im = out_re + fd.V;
     const T* ref_re = a.ref ? reinterpret_cast<const T*>(a.ref) + fd.in_off + 2LL * comp * fd.V : nullptr;
     const T wa = comp == 2 ? T(2) : T(1), wb = comp == 0 ? T(1) : T(2);
-    Kahan<T> sa, sb, sq;
+    DdSum sa, sb, sq;                     // double-float sums: 48 bits need no compensation
     T nonfinite = T(0), linf = T(0);
     const bool in64 = a.io & 1, out64 = a.io & 2;
     for (long long tl = chunk * a.tiles_per_item; tl < ntiles && tl < (chunk + 1) * a.tiles_per_item; ++tl) {
@@ -932,10 +986,10 @@ __global__ void __launch_bounds__(SD_THREADS, 1) k_gen_scold(const GenArgs a) {
         }
       }
       __syncthreads();
-      for (int cc = w; cc < SD_COLS; cc += nw) {
+      for (int cc = w; cc < SD_COLS; cc += SD_WARPS) {
         if (tl * SD_COLS + cc >= ncols) continue;             // warp-uniform
-        if (wm == 512) scold_transform<T, 512, INV>(tile, cc, n, acc, tw, chs, bhs, a.err);
-        else scold_transform<T, 256, INV>(tile, cc, n, acc, tw, chs, bhs, a.err);
+        dd_seq<INV>(tile + cc, SD_PITCH, (long long)SD_MAXN * SD_PITCH - cc, n, wm, acc, tw, w512, chs,
+                    bhs, a.err);
       }
       __syncthreads();
       // coalesced tile store (+ the residual of the last pass against the input)
@@ -973,16 +1027,136 @@ __global__ void __launch_bounds__(SD_THREADS, 1) k_gen_scold(const GenArgs a) {
     if (a.mode == 1) {
       double v[4] = {sa.value(), sb.value(), sq.value(), double(nonfinite)};
       warp_partials<4>(v, a.partials + item * WARPS_MAX * 4);
-      for (int k = nw * 4 + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
+      for (int k = SD_WARPS * 4 + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
         a.partials[item * WARPS_MAX * 4 + k] = 0.0;
     } else if (a.mode == 2) {
       double v = double(linf);
 #pragma unroll
       for (int o2 = 16; o2 > 0; o2 >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o2));
       if ((threadIdx.x & 31) == 0) a.partials[item * WARPS_MAX * 4 + (threadIdx.x >> 5)] = v;
-      for (int k = nw + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
+      for (int k = SD_WARPS + threadIdx.x; k < WARPS_MAX * 4; k += blockDim.x)
         a.partials[item * WARPS_MAX * 4 + k] = 0.0;
     }
+  }
+}
+
+// ---- x pass of double-float plans, a warp per row (wm in {256, 512}) --------------------------
+//
+// Item = (field, tiles_per_item row pairs), the items of k_gen_xrows.  A block of six warps takes
+// a row pair (k, -k): warp w copies row A (w < 3) or B of plane pair w mod 3 into its shared row,
+// transforms it in place with dd_seq (one compiled 256-point transform, both halves of a 512-point
+// row in turn), the block meets, the mode pairs are projected across the six rows (the generic
+// projector in double-float), the block meets again, and every warp takes its row's inverse
+// transform in place and stores it.  Rows are double-float pairs in HBM (a middle pass).
+constexpr int XD_THREADS = 192, XD_MAXN = 512;
+template <typename T> constexpr size_t xdd_smem() {
+  return 2 * sizeof(T) * (6 * size_t(XD_MAXN) + 256 + 512 + 256) +     // rows, chirps, W512^j
+         sizeof(T) * (6 * 2 * 256 + 2 * eqk::staged_size(256) + XD_MAXN);  // exchange, twiddles, xi_x
+}
+
+template <typename T>
+__global__ void __launch_bounds__(XD_THREADS, 2) k_gen_xdd(const GenArgs a) {
+  static_assert(sizeof(T) == 8, "double-float kernel");
+  using T2 = eqk::dd2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int TWS = eqk::staged_size(256);
+  T2* rows = reinterpret_cast<T2*>(smem_raw);                // [warp][XD_MAXN]
+  T2* chs = rows + 6 * XD_MAXN;
+  T2* bhs = chs + 256;
+  T2* w512 = bhs + 512;
+  T* xch = reinterpret_cast<T*>(w512 + 256);                 // [warp][re 256 | im 256]
+  T* twc = xch + 6 * 2 * 256;
+  T* tws = twc + TWS;
+  T* xix = tws + TWS;
+  const T2* cpool = reinterpret_cast<const T2*>(a.cpool);
+  const T* xipool = reinterpret_cast<const T*>(a.xipool);
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int side = w / 3, comp = w % 3;
+  for (int i = tid; i < TWS; i += blockDim.x) {
+    const T2 t = cpool[a.tw256 + i];
+    twc[i] = t.x;
+    tws[i] = t.y;
+  }
+  for (int i = tid; i < 256; i += blockDim.x) w512[i] = cpool[a.w512 + i];
+  const eqk::TwStaged<T> tw{twc, tws};
+  const eqk::SoaAcc<T> acc{xch + w * 2 * 256, xch + w * 2 * 256 + 256};
+  T2* row = rows + w * XD_MAXN;
+  int cur_f = -1;
+  for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+    const int f = find_field(a.item0, a.nfields, item);
+    const FieldDesc fd = a.fields[f];
+    const AxisPlan& ap = a.axes[fd.ax[0]];
+    const int n = fd.nx, wm = ap.wm, ny = fd.ny, nz = fd.nz;
+    if (f != cur_f) {                     // this field's x tables into shared memory
+      __syncthreads();
+      for (int i = tid; i < n; i += blockDim.x) xix[i] = xipool[fd.xi[0] + i];
+      if (wm != n) {
+        for (int i = tid; i < n; i += blockDim.x) chs[i] = cpool[ap.wchirp + i];
+        for (int i = tid; i < wm; i += blockDim.x) bhs[i] = cpool[ap.wbhat + i];
+      }
+      __syncthreads();
+      cur_f = f;
+    }
+    T* base = reinterpret_cast<T*>(a.out) + fd.out_off;
+    const T* xiy = xipool + fd.xi[1];
+    const T* xiz = xipool + fd.xi[2];
+    T zmv[6];
+    eqk::zero_mode_values(a.mean + f * 6, double(fd.V), zmv);
+    const T inv_v = T(1.0 / double(fd.V));
+    DdSum r2, di2, do2, o2;
+    const long long local = item - a.item0[f];
+    const long long lim = 6 * fd.V;
+    for (int g = (int)(local * a.tiles_per_item);
+         g < fd.npairs && g < (local + 1) * a.tiles_per_item; ++g) {
+      const int rA = a.pairpool[fd.pairs + g];
+      const int kz = rA / ny, ky = rA - kz * ny;
+      const int rB = (kz == 0 ? 0 : nz - kz) * ny + (ky == 0 ? 0 : ny - ky);
+      const bool self = rA == rB;
+      const bool active = !(side == 1 && self);              // warp-uniform
+      const long long roff = (long long)(side == 0 ? rA : rB) * n + 2LL * comp * fd.V;
+      if (active) {
+        for (int j = lane; j < n; j += 32)
+          row[j] = eqk::in_bounds(roff + j + fd.V, lim, a.err) ? T2{base[roff + j], base[roff + j + fd.V]}
+                                                             : T2{T(0), T(0)};
+        __syncwarp();
+        dd_seq<false>(row, 1, XD_MAXN, n, wm, acc, tw, w512, chs, bhs, a.err);
+      }
+      __syncthreads();
+      const T xi_y = xiy[ky], xi_z = xiz[kz];
+      for (int kx = tid; kx < n; kx += blockDim.x) {
+        const int kxm = kx == 0 ? 0 : n - kx;
+        if (self && kx > kxm) continue;
+        T2 av[3], bv[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          av[c] = rows[c * XD_MAXN + kx];
+          bv[c] = rows[(self ? c : 3 + c) * XD_MAXN + kxm];
+        }
+        const bool selfmode = self && kx == kxm;
+        eqk::project_pair<T>(av, bv, xix[kx], xi_y, xi_z, rA == 0 && kx == 0, zmv, a.nyq_zero != 0,
+                             a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          rows[c * XD_MAXN + kx] = av[c];
+          if (!selfmode) rows[(self ? c : 3 + c) * XD_MAXN + kxm] = bv[c];
+        }
+      }
+      __syncthreads();
+      if (active) {
+        dd_seq<true>(row, 1, XD_MAXN, n, wm, acc, tw, w512, chs, bhs, a.err);
+        for (int j = lane; j < n; j += 32) {
+          if (eqk::in_bounds(roff + j + fd.V, lim, a.err)) {
+            base[roff + j] = row[j].x;
+            base[roff + j + fd.V] = row[j].y;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
+    warp_partials<4>(v, a.partials + item * WARPS_MAX * 4);
+    for (int k = 6 * 4 + tid; k < WARPS_MAX * 4; k += blockDim.x)
+      a.partials[item * WARPS_MAX * 4 + k] = 0.0;
   }
 }
 

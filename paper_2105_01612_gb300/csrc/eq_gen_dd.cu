@@ -1,6 +1,6 @@
 // eq_gen_dd.cu - the runtime-length passes of FP64 plans in double-float arithmetic (FP64 in HBM
 // at the pipeline's ends, pairs of FP32 values between the passes): the warp-per-column strided
-// kernel (kinds 4, 5) and the warp-per-row x kernel (kind 3); every axis length of such a plan
+// kernel (kinds 4, 5) and the warp-per-row x kernel (kind 7); every axis length of such a plan
 // has a 256- or 512-point register transform.
 #include "eq_gen.cuh"
 #include "eq_gen_host.h"
@@ -8,7 +8,7 @@
 namespace eqg {
 namespace {
 const void* dd_fn(int kind) {
-  if (kind == 3) return reinterpret_cast<const void*>(&k_gen_xrows<eqk::dd>);
+  if (kind == 7) return reinterpret_cast<const void*>(&k_gen_xdd<eqk::dd>);
   if (kind == 4) return reinterpret_cast<const void*>(&k_gen_scold<eqk::dd, false>);
   if (kind == 5) return reinterpret_cast<const void*>(&k_gen_scold<eqk::dd, true>);
   return nullptr;
@@ -27,7 +27,7 @@ cudaError_t gen_occupancy_dd(int kind, int threads, size_t smem, int* blocks) {
 }
 
 cudaError_t gen_launch_dd(int kind, const GenArgs& a, int grid, int threads, size_t smem, cudaStream_t s) {
-  if (kind == 3) k_gen_xrows<eqk::dd><<<grid, threads, smem, s>>>(a);
+  if (kind == 7) k_gen_xdd<eqk::dd><<<grid, threads, smem, s>>>(a);
   else if (kind == 4) k_gen_scold<eqk::dd, false><<<grid, threads, smem, s>>>(a);
   else if (kind == 5) k_gen_scold<eqk::dd, true><<<grid, threads, smem, s>>>(a);
   else return cudaErrorInvalidValue;

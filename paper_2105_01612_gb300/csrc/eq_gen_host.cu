@@ -140,8 +140,9 @@ k_gen_finalize_norms(const double* __restrict__ partx, const long long* __restri
 // ---- plan ------------------------------------------------------------------------------
 
 struct PassShape {
-  int kind = 0;            // strided passes: 0 (k_gen_strided) or 4 (k_gen_scols), the inverse
-                           // launching kind + 1; x pass: 2 (k_gen_xproj) or 3 (k_gen_xrows)
+  int kind = 0;            // strided passes: 0 (k_gen_strided) or 4 (k_gen_scols / k_gen_scold),
+                           // the inverse launching kind + 1; x pass: 2 (k_gen_xproj), 3
+                           // (k_gen_xrows), 6 (k_gen_xpair) or 7 (k_gen_xdd)
   int cols = 16, pitch = 16, tpi = 1, threads = 256, mmax = 1, grid = 1;
   size_t smem = 0;
   long long nitems = 0;
@@ -588,7 +589,9 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
     *err = "x pass: unknown kernel choice";
     return EQ_ERR_INVALID;
   }
-  if (t.xp == 0) {
+  if (t.xp == 0 && g->dd) {
+    x.kind = 7; x.mmax = g->mx[0]; x.cols = 6; x.pitch = 0; x.threads = XD_THREADS;
+  } else if (t.xp == 0) {
     x.kind = 3; x.mmax = g->mx[0]; x.cols = 6; x.pitch = 0; x.threads = XR_THREADS;
   } else if (t.xp == 4) {
     x.kind = 6; x.mmax = g->mx[0]; x.cols = 6; x.pitch = 0; x.threads = XQ_THREADS;
@@ -601,6 +604,7 @@ eq_status gen_configure(GenPlan* g, const GenTune& t, std::string* err) {
                                 : g->dd ? xrows_smem<eqk::dd>() : xrows_smem<double>())
               : p->kind == 4 ? (g->dd ? scold_smem<eqk::dd>() : scols_smem())
               : p->kind == 6 ? xpair_smem()
+              : p->kind == 7 ? xdd_smem<eqk::dd>()
                              : (2 * (size_t)p->mmax * p->pitch + 3 * (size_t)p->mmax) * cs;
     if (p->smem > limit || p->threads > 512 || p->threads % p->cols != 0 || p->cols < 1) {
       *err = "pass shape does not fit (tile columns, threads or shared memory)";
