@@ -492,6 +492,23 @@ __device__ __forceinline__ eqk::CPair pmul_lanes(eqk::CPair v, float2 w0, float2
                     __ffma2_rn(v.r, S, __fmul2_rn(v.i, C))};
 }
 
+// The paired 256-point transform, forward, or with inv the unnormalised inverse as the conjugate
+// of the forward transform of the conjugate: one compiled transform serves both directions (a
+// small instruction working set)
+__device__ __forceinline__ void pfft256(eqk::CPair (&v)[8], bool inv, int lane, const eqk::PairAcc& acc,
+                                        const eqk::TwStaged<float>& tw) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  if (inv) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e].i = __fmul2_rn(v[e].i, m1);
+  }
+  eqk::pfft_column<256, 8, false>(v, lane, acc, tw);
+  if (inv) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e].i = __fmul2_rn(v[e].i, m1);
+  }
+}
+
 // Length-n DFT of one sequence through the 512-point split (wm = 512: n = 512 directly, or
 // Bluestein for n <= 256).  in(j) gives x_j (j < n); out(k, X_k) takes the n outputs; INV: the
 // exponent's sign is +, unnormalised.  All reads of in() precede every call of out().  On entry no
@@ -518,13 +535,13 @@ __device__ __forceinline__ void dft_split512(int n, IN in, OUT out, const eqk::P
     v[e] = cpair(cadd(u0, u1), cmul(csub(u0, u1), w));
   }
   if (blue) {
-    eqk::pfft_column<256, 8, false>(v, lane, acc, tw);
+    pfft256(v, false, lane, acc, tw);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {                 // U_{2k} (lane 0) and U_{2k+1} (lane 1) times b^
       const float4 b = bhs2[lane + 32 * e];
       v[e] = pmul_lanes(v[e], make_float2(b.x, b.y), make_float2(b.z, b.w));
     }
-    eqk::pfft_column<256, 8, true>(v, lane, acc, tw);
+    pfft256(v, true, lane, acc, tw);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int j = lane + 32 * e;
@@ -537,7 +554,7 @@ __device__ __forceinline__ void dft_split512(int n, IN in, OUT out, const eqk::P
       }
     }
   } else {
-    eqk::pfft_column<256, 8, INV>(v, lane, acc, tw);
+    pfft256(v, INV, lane, acc, tw);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {                 // outputs 2k and 2k + 1, k = lane + 32 e
       const int k = lane + 32 * e;
@@ -572,13 +589,13 @@ __device__ __forceinline__ void dft_pair256(int n, IN0 in0, IN1 in1, OUT0 out0, 
     v[e] = cpair(x0, x1);
   }
   if (blue) {
-    eqk::pfft_column<256, 8, false>(v, lane, acc, tw);
+    pfft256(v, false, lane, acc, tw);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const float2 b = bhs[lane + 32 * e];
       v[e] = eqk::pmul_cs(v[e], b.x, b.y);
     }
-    eqk::pfft_column<256, 8, true>(v, lane, acc, tw);
+    pfft256(v, true, lane, acc, tw);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int j = lane + 32 * e;
@@ -591,7 +608,7 @@ __device__ __forceinline__ void dft_pair256(int n, IN0 in0, IN1 in1, OUT0 out0, 
       }
     }
   } else {
-    eqk::pfft_column<256, 8, INV>(v, lane, acc, tw);
+    pfft256(v, INV, lane, acc, tw);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int k = lane + 32 * e;
@@ -1248,8 +1265,9 @@ __global__ void __launch_bounds__(XQ_THREADS, 4) k_gen_xpair(const GenArgs a) {
         dft_pair256<false>(n, load(oA), load(oB), keep(sA), keep(sB), acc, tw, chs, bhs, lane);
       } else {
         const float4* bh2 = reinterpret_cast<const float4*>(bhs);
-        dft_split512<false>(n, load(oA), keep(sA), acc, tw, w512, chs, bh2, lane);
-        if (!self) dft_split512<false>(n, load(oB), keep(sB), acc, tw, w512, chs, bh2, lane);
+#pragma unroll 1
+        for (int r = 0; r < (self ? 1 : 2); ++r)                // rows A and B in turn
+          dft_split512<false>(n, load(r ? oB : oA), keep(r ? sB : sA), acc, tw, w512, chs, bh2, lane);
       }
       __syncthreads();
       // projector over the mode pairs (kx, B at -kx)
@@ -1294,8 +1312,9 @@ __global__ void __launch_bounds__(XQ_THREADS, 4) k_gen_xpair(const GenArgs a) {
         else dft_pair256<true>(n, read(sA), read(sB), store(oA), store(oB), acc, tw, chs, bhs, lane);
       } else {
         const float4* bh2 = reinterpret_cast<const float4*>(bhs);
-        dft_split512<true>(n, read(sA), store(oA), acc, tw, w512, chs, bh2, lane);
-        if (!self) dft_split512<true>(n, read(sB), store(oB), acc, tw, w512, chs, bh2, lane);
+#pragma unroll 1
+        for (int r = 0; r < (self ? 1 : 2); ++r)
+          dft_split512<true>(n, read(r ? sB : sA), store(r ? oB : oA), acc, tw, w512, chs, bh2, lane);
       }
     }
     double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
