@@ -192,6 +192,19 @@ __host__ __device__ __forceinline__ double dd_to_bits(dd x) {
   return d_of(sgn | (static_cast<unsigned long long>(ex + 1023) << 52) | (mant & 0xfffffffffffffull));
 }
 
+// The same conversions with FP64 instructions (the FP64 units are otherwise idle in the
+// double-float passes, while the integer forms take FP32 / integer issue slots): hi = the double
+// rounded to FP32, lo = the exact remainder d - hi rounded to FP32; the way back one FP64 add of
+// the exact widenings.  Beyond FP32's range: infinities with lo = 0.
+__device__ __forceinline__ dd dd_from_f64(double d) {
+  const float hi = __double2float_rn(d);
+  const float lo = ::isfinite(hi) ? __double2float_rn(d - static_cast<double>(hi)) : 0.f;
+  return dd(hi, lo);
+}
+__device__ __forceinline__ double dd_to_f64(dd x) {
+  return __dadd_rn(static_cast<double>(x.hi), static_cast<double>(x.lo));
+}
+
 // complex double-float (the register and shared-memory type of the FP64 transforms that run in
 // double-float arithmetic)
 struct dd2 {

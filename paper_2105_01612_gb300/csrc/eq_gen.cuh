@@ -88,14 +88,15 @@ struct GenArgs {
 };
 
 // Element loads and stores of the strided passes: the plan's type, or for double-float
-// arithmetic FP64 at the pipeline's ends, converted on the bits.
+// arithmetic FP64 at the pipeline's ends (loads converted on the bits with integer instructions,
+// stores with the FP64 units' exact widen-and-add, the faster of the two forms for each measured).
 template <typename T> __device__ __forceinline__ T ld_elem(const T* p, long long i, bool) { return p[i]; }
 template <> __device__ __forceinline__ eqk::dd ld_elem<eqk::dd>(const eqk::dd* p, long long i, bool f64) {
   return f64 ? eqk::dd_from_bits(reinterpret_cast<const double*>(p)[i]) : p[i];
 }
 template <typename T> __device__ __forceinline__ void st_elem(T* p, long long i, T v, bool) { p[i] = v; }
 template <> __device__ __forceinline__ void st_elem<eqk::dd>(eqk::dd* p, long long i, eqk::dd v, bool f64) {
-  if (f64) reinterpret_cast<double*>(p)[i] = eqk::dd_to_bits(v);
+  if (f64) reinterpret_cast<double*>(p)[i] = eqk::dd_to_f64(v);
   else p[i] = v;
 }
 
