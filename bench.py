@@ -45,6 +45,9 @@ def parse():
                     help="profiling cases: a non-cubic grid instead of size^3")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64, cuFFT, e2e and CPU comparison legs")
+    ap.add_argument("--fp64-only", action="store_true",
+                    help="profiling case: only the FP64 projection of the --grid / --size field "
+                         "(synthetic Voronoi input), its time and per-pass times")
     ap.add_argument("--batch-fields", type=int, default=0, metavar="K",
                     help="profiling case: only the uneven-batch leg, on the first K of its 64 "
                          "fields, with the plan's default pass shapes (no autotuning)")
@@ -294,6 +297,36 @@ def fp64_native_ms(x64, o64, n, dev, stream, k: int = 2) -> float:
     p.close()
     del y
     return f0.elapsed_time(f1) / k
+
+
+def fp64_case(args):
+    """The FP64 plain projection alone on the --grid (or --size^3) field: the profiling case of
+    the double-float passes."""
+    import torch
+    from fieldgen import voronoi_stress_field
+    import paper_2105_01612_gb300 as eq
+    nx, ny, nz = args.grid if args.grid else (args.size,) * 3
+    dev = torch.device("cuda", 0)
+    grains = max(8, int(round(GRAINS * nx * ny * nz / N ** 3)))
+    x = voronoi_stress_field((nz, ny, nx), grains, 200.0, 20.0, SEED, dtype=torch.float64,
+                             device=dev).unsqueeze(0)
+    y = torch.empty_like(x)
+    p = eq.Plan(nx, ny, nz, torch.float64, 1, "ddo", device=dev)
+    for _ in range(max(1, args.warmup)):
+        p.project(x, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        p.project(x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    p.set_timing(1)
+    p.project(x, y)
+    per_pass, _ = p.pass_ms()
+    p.close()
+    return {"case": f"FP64 {nx}x{ny}x{nz} Voronoi, DDO", "ms_per_step": e0.elapsed_time(e1) / args.steps,
+            "pass_ms": per_pass}
 
 
 def fp64_leg(x, out, n, dev, stream):
@@ -828,6 +861,9 @@ def serving_leg(dev, rate: float = 200.0, warm: int = 200, measured: int = 2000,
 
 def main():
     args = parse()
+    if args.fp64_only:
+        print(json.dumps(fp64_case(args)), flush=True)
+        return
     if args.batch_fields:
         import torch
         print(json.dumps(batch_leg(torch.device("cuda", 0), args.steps, args.batch_fields,

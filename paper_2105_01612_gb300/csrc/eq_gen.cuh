@@ -800,20 +800,19 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
 //
 // FP64 plans in double-float arithmetic (FP64 in HBM at the pipeline's ends: the first pass
 // converts its loads, the last its stores and the residual's re-read input; double-float pairs
-// between the passes).  Same items, partial records and modes as k_gen_strided.  One block of
-// SD_WARPS warps per SM.  A tile of SD_COLS adjacent columns (n points
-// each) comes into shared memory by coalesced loads (SD_COLS consecutive elements of a plane per
-// point), eight loads in flight a thread; each warp then takes whole columns: lane l
-// holds points l + 32 e of a length-wm register transform (radix-8 stages through the warp's own
-// row), directly when n = wm, else Bluestein's convolution (pre-chirp, transform, product with
-// the chirp transform, inverse transform, post-chirp; the inverse direction by conjugation), and
-// writes the n outputs back into the tile, which leaves by coalesced stores (with the L-infinity
-// residual of the last pass).  All fields of a launch have their axis served (wm in {256, 512}).
-constexpr int SD_COLS = 16, SD_WARPS = 16, SD_THREADS = 32 * SD_WARPS, SD_PITCH = SD_COLS + 1;
+// between the passes).  Same items, partial records and modes as k_gen_strided.  Two blocks of
+// SD_WARPS warps per SM (one loads while the other transforms).  A tile of SD_COLS adjacent
+// columns (n points each) comes into shared memory by coalesced loads (SD_COLS consecutive
+// elements of a plane per point), eight loads in flight a thread; each warp then transforms a
+// column in place with dd_seq (below) and the tile leaves by coalesced stores (with the
+// L-infinity residual of the last pass).  All fields of a launch have their axis served (wm in
+// {256, 512}); Bluestein lengths are at most 256, so their chirp tables sit in the tile's upper
+// rows, reloaded with every item.
+constexpr int SD_COLS = 8, SD_WARPS = 8, SD_THREADS = 32 * SD_WARPS, SD_PITCH = SD_COLS + 1;
 constexpr int SD_MAXN = 512;          // longest column (n = wm = 512)
 template <typename T> constexpr size_t scold_smem() {
-  return 2 * sizeof(T) * (size_t(SD_MAXN) * SD_PITCH + 256 + 512 + 256) +  // tile, chirps, W512^j
-         sizeof(T) * (size_t(SD_WARPS) * 2 * 256 + 2 * eqk::staged_size(256));  // rows, twiddles
+  return 2 * sizeof(T) * (size_t(SD_MAXN) * SD_PITCH + 256) +
+         sizeof(T) * (size_t(SD_WARPS) * 2 * 256 + 2 * eqk::staged_size(256));
 }
 
 // One sequence of a double-float pass (a tile column, or an x row), element j at base[j pitch]
@@ -824,8 +823,7 @@ template <typename T> constexpr size_t scold_smem() {
 // halves one after the other (outputs 2k and 2k + 1); Bluestein's convolution (n <= 256) with
 // transform length wm = 512 from the same split (u_{j+256} = 0), keeping only the outputs j < n
 // of its inverse transform, y_j = P_j + W512^-j Q_j, or with wm = 256 directly.
-template <bool INV>
-__device__ __forceinline__ void dd_seq(eqk::dd2* base, int pitch, long long lim, int n, int wm,
+__device__ __forceinline__ void dd_seq(bool INV, eqk::dd2* base, int pitch, long long lim, int n, int wm,
                                        const eqk::SoaAcc<eqk::dd>& acc,
                                        const eqk::TwStaged<eqk::dd>& tw, const eqk::dd2* w512,
                                        const eqk::dd2* chs, const eqk::dd2* bhs, int* err) {
@@ -918,14 +916,14 @@ struct DdSum {
 };
 
 template <typename T, bool INV>
-__global__ void __launch_bounds__(SD_THREADS, 1) k_gen_scold(const GenArgs a) {
+__global__ void __launch_bounds__(SD_THREADS, 2) k_gen_scold(const GenArgs a) {
   using T2 = typename eqk::V2<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int TWS = eqk::staged_size(256);
   T2* tile = reinterpret_cast<T2*>(smem_raw);               // [point][SD_PITCH]
-  T2* chs = tile + SD_MAXN * SD_PITCH;
-  T2* bhs = chs + 256;
-  T2* w512 = bhs + 512;
+  T2* chs = tile + 256 * SD_PITCH;                          // Bluestein (n <= 256): rows 256..
+  T2* bhs = chs + 256;                                       //   of the tile hold the chirps
+  T2* w512 = tile + SD_MAXN * SD_PITCH;
   T* rows = reinterpret_cast<T*>(w512 + 256);               // [warp][re 256 | im 256]
   T* twc = rows + SD_WARPS * 2 * 256;
   T* tws = twc + TWS;
@@ -940,21 +938,17 @@ __global__ void __launch_bounds__(SD_THREADS, 1) k_gen_scold(const GenArgs a) {
   }
   for (int i = tid; i < 256; i += blockDim.x) w512[i] = cpool[a.w512 + i];
   const eqk::TwStaged<T> tw{twc, tws};
-  int cur_ax = -1;
   for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
     const int f = find_field(a.item0, a.nfields, item);
     const FieldDesc fd = a.fields[f];
     const int axi = fd.ax[a.axis];
     const AxisPlan& ap = a.axes[axi];
     const int n = ap.n, wm = ap.wm;
-    if (axi != cur_ax) {                  // chirp tables of this axis length into shared memory
+    if (wm != n) {                        // chirps into the tile's upper rows, every item
       __syncthreads();
-      if (wm != n) {
-        for (int i = tid; i < n; i += blockDim.x) chs[i] = cpool[ap.wchirp + i];
-        for (int i = tid; i < wm; i += blockDim.x) bhs[i] = cpool[ap.wbhat + i];
-      }
+      for (int i = tid; i < n; i += blockDim.x) chs[i] = cpool[ap.wchirp + i];
+      for (int i = tid; i < wm; i += blockDim.x) bhs[i] = cpool[ap.wbhat + i];
       __syncthreads();
-      cur_ax = axi;
     }
     long long inner, nstride, outer_stride, ncols;
     if (a.axis == 2) { inner = (long long)fd.nx * fd.ny; nstride = inner; outer_stride = 0; ncols = inner; }
@@ -1006,7 +1000,7 @@ __global__ void __launch_bounds__(SD_THREADS, 1) k_gen_scold(const GenArgs a) {
       __syncthreads();
       for (int cc = w; cc < SD_COLS; cc += SD_WARPS) {
         if (tl * SD_COLS + cc >= ncols) continue;             // warp-uniform
-        dd_seq<INV>(tile + cc, SD_PITCH, (long long)SD_MAXN * SD_PITCH - cc, n, wm, acc, tw, w512, chs,
+        dd_seq(INV, tile + cc, SD_PITCH, (long long)SD_MAXN * SD_PITCH - cc, n, wm, acc, tw, w512, chs,
                     bhs, a.err);
       }
       __syncthreads();
@@ -1132,43 +1126,51 @@ __global__ void __launch_bounds__(XD_THREADS, 2) k_gen_xdd(const GenArgs a) {
       const bool self = rA == rB;
       const bool active = !(side == 1 && self);              // warp-uniform
       const long long roff = (long long)(side == 0 ? rA : rB) * n + 2LL * comp * fd.V;
-      if (active) {
-        for (int j = lane; j < n; j += 32)
-          row[j] = eqk::in_bounds(roff + j + fd.V, lim, a.err) ? T2{base[roff + j], base[roff + j + fd.V]}
-                                                             : T2{T(0), T(0)};
-        __syncwarp();
-        dd_seq<false>(row, 1, XD_MAXN, n, wm, acc, tw, w512, chs, bhs, a.err);
-      }
-      __syncthreads();
       const T xi_y = xiy[ky], xi_z = xiz[kz];
-      for (int kx = tid; kx < n; kx += blockDim.x) {
-        const int kxm = kx == 0 ? 0 : n - kx;
-        if (self && kx > kxm) continue;
-        T2 av[3], bv[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          av[c] = rows[c * XD_MAXN + kx];
-          bv[c] = rows[(self ? c : 3 + c) * XD_MAXN + kxm];
-        }
-        const bool selfmode = self && kx == kxm;
-        eqk::project_pair<T>(av, bv, xix[kx], xi_y, xi_z, rA == 0 && kx == 0, zmv, a.nyq_zero != 0,
-                             a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2, di2, do2, o2);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          rows[c * XD_MAXN + kx] = av[c];
-          if (!selfmode) rows[(self ? c : 3 + c) * XD_MAXN + kxm] = bv[c];
-        }
-      }
-      __syncthreads();
-      if (active) {
-        dd_seq<true>(row, 1, XD_MAXN, n, wm, acc, tw, w512, chs, bhs, a.err);
-        for (int j = lane; j < n; j += 32) {
-          if (eqk::in_bounds(roff + j + fd.V, lim, a.err)) {
-            base[roff + j] = row[j].x;
-            base[roff + j + fd.V] = row[j].y;
+      // phase 0: load and forward transform, then the projector; phase 1: inverse transform and
+      // store (one call site of the transform: one inlined copy of its code)
+#pragma unroll 1
+      for (int ph = 0; ph < 2; ++ph) {
+        if (active) {
+          if (ph == 0) {
+            for (int j = lane; j < n; j += 32)
+              row[j] = eqk::in_bounds(roff + j + fd.V, lim, a.err)
+                           ? T2{base[roff + j], base[roff + j + fd.V]} : T2{T(0), T(0)};
+            __syncwarp();
+          }
+          dd_seq(ph == 1, row, 1, XD_MAXN, n, wm, acc, tw, w512, chs, bhs, a.err);
+          if (ph == 1) {
+            for (int j = lane; j < n; j += 32) {
+              if (eqk::in_bounds(roff + j + fd.V, lim, a.err)) {
+                base[roff + j] = row[j].x;
+                base[roff + j + fd.V] = row[j].y;
+              }
+            }
+            __syncwarp();
           }
         }
-        __syncwarp();
+        if (ph == 1) break;
+        __syncthreads();
+        for (int kx = tid; kx < n; kx += blockDim.x) {
+          const int kxm = kx == 0 ? 0 : n - kx;
+          if (self && kx > kxm) continue;
+          T2 av[3], bv[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            av[c] = rows[c * XD_MAXN + kx];
+            bv[c] = rows[(self ? c : 3 + c) * XD_MAXN + kxm];
+          }
+          const bool selfmode = self && kx == kxm;
+          eqk::project_pair<T>(av, bv, xix[kx], xi_y, xi_z, rA == 0 && kx == 0, zmv,
+                               a.nyq_zero != 0, a.compat != 0, inv_v, selfmode ? T(1) : T(2), r2,
+                               di2, do2, o2);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            rows[c * XD_MAXN + kx] = av[c];
+            if (!selfmode) rows[(self ? c : 3 + c) * XD_MAXN + kxm] = bv[c];
+          }
+        }
+        __syncthreads();
       }
     }
     double v[4] = {r2.value(), di2.value(), do2.value(), o2.value()};
