@@ -41,6 +41,13 @@ typedef enum {
   EQ_ERR_NOT_FOUND = 7   /* unknown ticket */
 } eq_status;
 
+/* Element type at the boundary.  EQ_F64 fields are read and written as FP64; where every axis
+ * length of the plan is 512 or at most 256, the plain projection (eq_project and its host forms)
+ * computes in double-float arithmetic: each value an unevaluated sum of two FP32 numbers, about
+ * 48 significant bits, relative error about 1e-14 against an exact-arithmetic result (FP64
+ * instructions run at a small fraction of the FP32 rate on this GPU).  The Hodge and padded forms,
+ * other lengths, and every call when the environment variable EQ_F64_ARITH=native is set at plan
+ * creation use FP64 instructions for the transforms. */
 typedef enum { EQ_F32 = 0, EQ_F64 = 1 } eq_dtype;
 
 /* Derivative symbol: DDO = central-difference modified wavevector (Sec. 4.2, eq. eq:diff);
