@@ -88,11 +88,17 @@ struct GenArgs {
 };
 
 // Element loads and stores of the strided passes: the plan's type, or for double-float
-// arithmetic FP64 at the pipeline's ends (loads converted on the bits with integer instructions,
-// stores with the FP64 units' exact widen-and-add, the faster of the two forms for each measured).
+// arithmetic FP64 at the pipeline's ends (the first pass's loads converted on the bits with
+// integer instructions, stores and the last pass's re-read of the input on the FP64 units, the
+// faster form for each as measured).
 template <typename T> __device__ __forceinline__ T ld_elem(const T* p, long long i, bool) { return p[i]; }
 template <> __device__ __forceinline__ eqk::dd ld_elem<eqk::dd>(const eqk::dd* p, long long i, bool f64) {
   return f64 ? eqk::dd_from_bits(reinterpret_cast<const double*>(p)[i]) : p[i];
+}
+// the last pass's re-read of the input (FP64 for double-float plans), converted on the FP64 units
+template <typename T> __device__ __forceinline__ T ld_ref(const T* p, long long i) { return p[i]; }
+template <> __device__ __forceinline__ eqk::dd ld_ref<eqk::dd>(const eqk::dd* p, long long i) {
+  return eqk::dd_from_f64(reinterpret_cast<const double*>(p)[i]);
 }
 template <typename T> __device__ __forceinline__ void st_elem(T* p, long long i, T v, bool) { p[i] = v; }
 template <> __device__ __forceinline__ void st_elem<eqk::dd>(eqk::dd* p, long long i, eqk::dd v, bool f64) {
@@ -1014,7 +1020,7 @@ __global__ void __launch_bounds__(SD_THREADS, 2) k_gen_scold(const GenArgs a) {
               const int k = kb + u * jstep;
               const long long off = base + (long long)k * nstride;
               rb[u] = (k < n && eqk::in_bounds(off, fd.V, a.err))
-                          ? T2{ld_elem(ref_re, off, true), ld_elem(ref_re, off + fd.V, true)}
+                          ? T2{ld_ref(ref_re, off), ld_ref(ref_re, off + fd.V)}
                           : T2{T(0), T(0)};
             }
           }
