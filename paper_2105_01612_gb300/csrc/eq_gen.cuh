@@ -459,10 +459,10 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
 // FP32.  Same items, partial records and modes as k_gen_strided.  A tile of C adjacent columns
 // (n points each; C = 32 for n <= 256, else 16) comes into shared memory by coalesced loads (C
 // consecutive elements of a plane per point), eight loads in flight a thread; the warps then
-// transform whole
-// columns with paired 256-point transforms (two sequences in one warp, packed two-lane
-// arithmetic, eq_pfft.cuh) and write the n outputs back into the tile, which leaves by
-// coalesced stores (with the L-infinity residual of the last pass).  Every field of a launch has
+// transform whole columns with paired 256-point transforms (two sequences in one warp, packed
+// two-lane arithmetic, eq_pfft.cuh; one compiled forward transform, the inverse by conjugation)
+// and write the n outputs back into the tile, which leaves by coalesced stores (with the
+// L-infinity residual of the last pass).  Two blocks of 8 warps per SM.  Every field of a launch has
 // its axis served by a transform length wm in {256, 512}:
 //   wm = 256: a warp takes two adjacent columns as the pair, either transformed directly (n = 256)
 //     or by Bluestein's chirp-z convolution (n <= 128: pre-chirp, forward transform, product with
@@ -822,9 +822,9 @@ template <typename T> constexpr size_t scold_smem() {
 }
 
 // One sequence of a double-float pass (a tile column, or an x row), element j at base[j pitch]
-// (j pitch < lim), transformed in place through a single compiled
-// 256-point forward transform (its code, executed for each half, keeps the instruction working set
-// small): the inverse direction by conjugation of input and output; a 512-point column through
+// (j pitch < lim), transformed in place through a single compiled 256-point forward transform
+// (its code, executed for each half, keeps the instruction working set small): the inverse
+// direction (INV) by conjugation of input and output; a 512-point column through
 // the decimation-in-frequency split a_j = u_j + u_{j+256}, b_j = (u_j - u_{j+256}) W512^j, the two
 // halves one after the other (outputs 2k and 2k + 1); Bluestein's convolution (n <= 256) with
 // transform length wm = 512 from the same split (u_{j+256} = 0), keeping only the outputs j < n
