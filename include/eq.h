@@ -45,9 +45,11 @@ typedef enum {
  * length of the plan is 512 or at most 256, the plain projection (eq_project and its host forms)
  * computes in double-float arithmetic: each value an unevaluated sum of two FP32 numbers, about
  * 48 significant bits, relative error about 1e-14 against an exact-arithmetic result (FP64
- * instructions run at a small fraction of the FP32 rate on this GPU).  The Hodge and padded forms,
- * other lengths, and every call when the environment variable EQ_F64_ARITH=native is set at plan
- * creation use FP64 instructions for the transforms. */
+ * instructions run at a small fraction of the FP32 rate on this GPU).  It keeps FP32's exponent
+ * range: spectra reach nx ny nz max|S| and the norm sums its square, so keep nx ny nz max|S| below
+ * about 1e18 (stresses below about 7e9 at 512^3; values below about 1e-30 lose precision).  The
+ * Hodge and padded forms, other lengths, and every call when the environment variable
+ * EQ_F64_ARITH=native is set at plan creation use FP64 instructions for the transforms. */
 typedef enum { EQ_F32 = 0, EQ_F64 = 1 } eq_dtype;
 
 /* Derivative symbol: DDO = central-difference modified wavevector (Sec. 4.2, eq. eq:diff);
