@@ -1385,6 +1385,13 @@ eq_status eq_plan_autotune(eq_plan* p, const void* d_in, void* d_out, void* stre
   float ms[NCFG][EQ_NUM_PASSES] = {};
   bool ok[NCFG][3] = {};                                // [config][axis z, y, x] available
   const int saved_cap = p->tcap, saved_used = p->tused;
+  // the variants are those of this plan's own passes (an FP64 plan's double-float sub-plan, which
+  // runs its plain projections, has none to choose): time them
+  p->native_only = true;
+  struct Restore {
+    eq_plan* p;
+    ~Restore() { p->native_only = false; }
+  } restore{p};
   // configs: 0 wide tiles, 1 narrow tiles, 2 plain kernels, 3 and 4 warp-per-row x pass through
   // a bulk-copy stage (three and four blocks per SM asked of the register allocator), 5 the 16 x 32
   // strided kernel (where it exists; its config counts for an axis only if the axis really ran

@@ -226,3 +226,22 @@ def test_fp64_runtime_length_plans_in_double_float_match_the_oracle(monkeypatch)
         for k in ("norm_in", "norm_out", "resid_l2"):
             assert abs(nrm[k] - ref_n[k]) <= 1e-12 * ref_n["norm_in"], (dims[i], k)
         assert nrm["div_out_l2"] <= 1e-12 * nrm["div_in_l2"]
+
+
+def test_fp64_power_of_two_plan_autotune_then_plain_and_hodge():
+    """An FP64 power-of-two plan tunes the variants of its own (FP64-instruction) passes, which
+    its Hodge form runs, while plain projections go through its double-float sub-plan: both stay
+    within 1e-12 of the oracle after tuning."""
+    s = voronoi_stress_field((64, 64, 64), 9, 100.0, 5.0, 67).numpy()
+    x = torch.as_tensor(s).cuda().unsqueeze(0)
+    p = eq.Plan(64, 64, 64, torch.float64)
+    y = torch.empty_like(x)
+    p.autotune(x, y)
+    p.project(x, y)
+    ref = oracle.project(s, "ddo")
+    assert rel(y[0].cpu().numpy(), ref) <= 1e-12
+    out, pot = p.project_hodge(x)
+    assert rel(out[0].cpu().numpy(), ref) <= 1e-12
+    yref = oracle.hodge_potential(s, "ddo")
+    assert np.linalg.norm(pot[0, :3].cpu().numpy() - yref) <= 1e-11 * np.linalg.norm(yref)
+    p.close()
