@@ -245,3 +245,16 @@ def test_fp64_power_of_two_plan_autotune_then_plain_and_hodge():
     yref = oracle.hodge_potential(s, "ddo")
     assert np.linalg.norm(pot[0, :3].cpu().numpy() - yref) <= 1e-11 * np.linalg.norm(yref)
     p.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_lengths_beyond_the_register_transforms_take_the_shared_memory_kernels(dtype):
+    """Lengths between 256 and 1024 other than 512 have no 256- or 512-point register transform:
+    such plans run the shared-memory mixed-radix / Bluestein kernels (and FP64 keeps FP64
+    instructions) and still give the oracle's result."""
+    dims = [(300, 4, 5), (6, 7, 263), (9, 270, 3)]
+    fields, outs, nrm = _varlen_run(dims, dtype, 7700)
+    for i, f in enumerate(fields):
+        ref = oracle.project(f.astype(np.float64), "ddo")
+        assert rel(outs[i], ref) <= TOL[dtype], dims[i]
+        assert nrm[i]["div_out_l2"] <= (1e-12 if dtype == torch.float64 else 1e-5) * nrm[i]["div_in_l2"]
