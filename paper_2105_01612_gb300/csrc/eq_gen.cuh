@@ -808,8 +808,9 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
 // converts its loads, the last its stores and the residual's re-read input; double-float pairs
 // between the passes).  Same items, partial records and modes as k_gen_strided.  Two blocks of
 // SD_WARPS warps per SM (one loads while the other transforms).  A tile of SD_COLS adjacent
-// columns (n points each) comes into shared memory by coalesced loads (SD_COLS consecutive
-// elements of a plane per point), eight loads in flight a thread; each warp then transforms a
+// columns (n points each) comes into shared memory by 8-byte asynchronous copies (SD_COLS
+// consecutive elements of a plane per point, all of a thread's points in flight at once); each
+// warp then transforms a
 // column in place with dd_seq (below) and the tile leaves by coalesced stores (with the
 // L-infinity residual of the last pass).  All fields of a launch have their axis served (wm in
 // {256, 512}); Bluestein lengths are at most 256, so their chirp tables sit in the tile's upper
@@ -913,6 +914,11 @@ __device__ __forceinline__ void dd_seq(bool INV, eqk::dd2* base, int pitch, long
   __syncwarp();
 }
 
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+
 // running double-float sum (its 48-bit significand holds a thread's partial sums of a pass
 // without compensation); read out as FP64
 struct DdSum {
@@ -978,29 +984,34 @@ __global__ void __launch_bounds__(SD_THREADS, 2) k_gen_scold(const GenArgs a) {
       const bool valid = c < ncols;
       const long long o = valid ? c / inner : 0;
       const long long base = o * outer_stride + (valid ? c - o * inner : 0);
-      // coalesced tile load, eight loads in flight; statistics of the first pass
-      constexpr int LB = 8;
-      for (int jb = lj; jb < n; jb += LB * jstep) {
-        T2 xb[LB];
-#pragma unroll
-        for (int u = 0; u < LB; ++u) {
-          const int j = jb + u * jstep;
+      constexpr int LB = 8;                  // store phase: residual loads in flight a thread
+      // the tile by 8-byte asynchronous copies, every point of this thread in flight at once (the
+      // raw bytes: FP64 values in the first pass, double-float pairs otherwise); then each thread
+      // converts its own points in place and takes the first pass's statistics
+      if (valid) {
+        for (int j = lj; j < n; j += jstep) {
           const long long off = base + (long long)j * nstride;
-          xb[u] = (j < n && valid && eqk::in_bounds(off, fd.V, a.err))
-                      ? T2{ld_elem(in_re, off, in64), ld_elem(in_im, off, in64)} : T2{T(0), T(0)};
+          if (eqk::in_bounds(off, fd.V, a.err) && eqk::in_bounds((long long)j * SD_PITCH + lc, SD_MAXN * SD_PITCH, a.err)) {
+            cp_async8(&tile[j * SD_PITCH + lc].x, in_re + off);
+            cp_async8(&tile[j * SD_PITCH + lc].y, in_im + off);
+          }
         }
-#pragma unroll
-        for (int u = 0; u < LB; ++u) {
-          const int j = jb + u * jstep;
-          if (j >= n) break;
-          const T2 x = xb[u];
-          if (a.mode == 1 && valid) {
+      }
+      asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+      if (valid && (in64 || a.mode == 1)) {
+        for (int j = lj; j < n; j += jstep) {
+          T2 x = tile[j * SD_PITCH + lc];
+          if (in64) {
+            const double2 raw = *reinterpret_cast<const double2*>(&tile[j * SD_PITCH + lc]);
+            x = T2{eqk::dd_from_bits(raw.x), eqk::dd_from_bits(raw.y)};
+            tile[j * SD_PITCH + lc] = x;
+          }
+          if (a.mode == 1) {
             if (!isfinite(x.x) || !isfinite(x.y)) nonfinite += T(1);
             sa.add(x.x);
             sb.add(x.y);
             sq.add(wa * x.x * x.x + wb * x.y * x.y);
           }
-          tile[j * SD_PITCH + lc] = x;
         }
       }
       __syncthreads();
