@@ -454,11 +454,17 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
   }
 }
 
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
 // ---- strided pass, a warp per column (lengths served by a 256- or 512-point transform) ------
 //
 // FP32.  Same items, partial records and modes as k_gen_strided.  A tile of C adjacent columns
-// (n points each; C = 32 for n <= 256, else 16) comes into shared memory by coalesced loads (C
-// consecutive elements of a plane per point), eight loads in flight a thread; the warps then
+// (n points each; C = 32 for n <= 256, else 16) comes into shared memory by 4-byte asynchronous
+// copies (C consecutive elements of a plane per point, all of a thread's points in flight); the
+// warps then
 // transform whole columns with paired 256-point transforms (two sequences in one warp, packed
 // two-lane arithmetic, eq_pfft.cuh; one compiled forward transform, the inverse by conjugation)
 // and write the n outputs back into the tile, which leaves by coalesced stores (with the
@@ -717,30 +723,26 @@ __global__ void __launch_bounds__(SC_THREADS, 2) k_gen_scols(const GenArgs a) {
       const bool valid = c < ncols;
       const long long o = valid ? c / inner : 0;
       const long long base = o * outer_stride + (valid ? c - o * inner : 0);
-      // coalesced tile load, eight loads in flight; statistics of the first pass
-      constexpr int LB = 8;
-      for (int jb = lj; jb < n; jb += LB * jstep) {
-        T2 xb[LB];
-#pragma unroll
-        for (int u = 0; u < LB; ++u) {
-          const int j = jb + u * jstep;
+      constexpr int LB = 8;                  // store phase: residual loads in flight a thread
+      // the tile by 4-byte asynchronous copies, all of this thread's points in flight at once;
+      // then the first pass's statistics from the thread's own points
+      if (valid) {
+        for (int j = lj; j < n; j += jstep) {
           const long long off = base + (long long)j * nstride;
-          xb[u] = (j < n && valid && eqk::in_bounds(off, fd.V, a.err)) ? T2{in_re[off], in_im[off]}
-                                                                       : T2{T(0), T(0)};
-        }
-#pragma unroll
-        for (int u = 0; u < LB; ++u) {
-          const int j = jb + u * jstep;
-          if (j < n) {
-            const T2 x = xb[u];
-            if (a.mode == 1 && valid) {
-              if (!isfinite(x.x) || !isfinite(x.y)) nonfinite += T(1);
-              sa.add(x.x);
-              sb.add(x.y);
-              sq.add(wa * x.x * x.x + wb * x.y * x.y);
-            }
-            tile[j * pitch + lc] = x;
+          if (eqk::in_bounds(off, fd.V, a.err) && eqk::in_bounds((long long)j * pitch + lc, SC_TILE, a.err)) {
+            cp_async4(&tile[j * pitch + lc].x, in_re + off);
+            cp_async4(&tile[j * pitch + lc].y, in_im + off);
           }
+        }
+      }
+      asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+      if (valid && a.mode == 1) {
+        for (int j = lj; j < n; j += jstep) {
+          const T2 x = tile[j * pitch + lc];
+          if (!isfinite(x.x) || !isfinite(x.y)) nonfinite += T(1);
+          sa.add(x.x);
+          sb.add(x.y);
+          sq.add(wa * x.x * x.x + wb * x.y * x.y);
         }
       }
       __syncthreads();
