@@ -87,21 +87,13 @@ struct GenArgs {
                            // (the pipeline's ends); the passes between hold double-float pairs
 };
 
-// Element loads and stores of the strided passes: the plan's type, or for double-float
-// arithmetic FP64 at the pipeline's ends (the first pass's loads converted on the bits with
-// integer instructions, stores and the last pass's re-read of the input on the FP64 units, the
-// faster form for each as measured).
-template <typename T> __device__ __forceinline__ T ld_elem(const T* p, long long i, bool) { return p[i]; }
-template <> __device__ __forceinline__ eqk::dd ld_elem<eqk::dd>(const eqk::dd* p, long long i, bool f64) {
-  return f64 ? eqk::dd_from_bits(reinterpret_cast<const double*>(p)[i]) : p[i];
-}
-// the last pass's re-read of the input (FP64 for double-float plans), converted on the FP64 units
-template <typename T> __device__ __forceinline__ T ld_ref(const T* p, long long i) { return p[i]; }
-template <> __device__ __forceinline__ eqk::dd ld_ref<eqk::dd>(const eqk::dd* p, long long i) {
+// FP64 at the ends of a double-float pipeline (the first pass's loads are converted on the bits
+// in k_gen_scold): the last pass's re-read of the input and its stores, converted on the FP64
+// units (the faster form for each, as measured); between the passes, double-float pairs.
+__device__ __forceinline__ eqk::dd ld_f64(const eqk::dd* p, long long i) {
   return eqk::dd_from_f64(reinterpret_cast<const double*>(p)[i]);
 }
-template <typename T> __device__ __forceinline__ void st_elem(T* p, long long i, T v, bool) { p[i] = v; }
-template <> __device__ __forceinline__ void st_elem<eqk::dd>(eqk::dd* p, long long i, eqk::dd v, bool f64) {
+__device__ __forceinline__ void st_dd(eqk::dd* p, long long i, eqk::dd v, bool f64) {
   if (f64) reinterpret_cast<double*>(p)[i] = eqk::dd_to_f64(v);
   else p[i] = v;
 }
@@ -368,7 +360,6 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
     Kahan<T> sa, sb, sq;
     T nonfinite = T(0), linf = T(0);
     const bool inv = INV;
-    const bool in64 = a.io & 1, out64 = a.io & 2;
     for (long long tile = chunk * a.tiles_per_item;
          tile < ntiles && tile < (chunk + 1) * a.tiles_per_item; ++tile) {
       const long long c = tile * C + col;
@@ -385,7 +376,7 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
           const int j = jb + u * jstep;
           const long long off = base + (long long)j * nstride;
           xb[u] = (j < n && valid && eqk::in_bounds(off, fd.V, a.err))
-                      ? T2{ld_elem(in_re, off, in64), ld_elem(in_im, off, in64)} : T2{T(0), T(0)};
+                      ? T2{in_re[off], in_im[off]} : T2{T(0), T(0)};
         }
 #pragma unroll
         for (int u = 0; u < LB; ++u) {
@@ -416,8 +407,7 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
               const int k = kb + u * jstep;
               const long long off = base + (long long)k * nstride;
               rb[u] = (k < n && eqk::in_bounds(off, fd.V, a.err))
-                          ? T2{ld_elem(ref_re, off, true), ld_elem(ref_re, off + fd.V, true)}
-                          : T2{T(0), T(0)};
+                          ? T2{ref_re[off], ref_re[off + fd.V]} : T2{T(0), T(0)};
             }
           }
 #pragma unroll
@@ -427,8 +417,8 @@ __global__ void __launch_bounds__(512) k_gen_strided(const GenArgs a) {
             const long long off = base + (long long)k * nstride;
             if (!eqk::in_bounds(off, fd.V, a.err)) continue;
             const T2 y = post(r[k * pitch + col], k, ap, sm.ch, inv);
-            st_elem(out_re, off, y.x, out64);
-            st_elem(out_im, off, y.y, out64);
+            out_re[off] = y.x;
+            out_im[off] = y.y;
             if (ref_re) {
               linf = fmax(linf, fabs(rb[u].x - y.x));
               linf = fmax(linf, fabs(rb[u].y - y.y));
@@ -1033,7 +1023,7 @@ __global__ void __launch_bounds__(SD_THREADS, 2) k_gen_scold(const GenArgs a) {
               const int k = kb + u * jstep;
               const long long off = base + (long long)k * nstride;
               rb[u] = (k < n && eqk::in_bounds(off, fd.V, a.err))
-                          ? T2{ld_ref(ref_re, off), ld_ref(ref_re, off + fd.V)}
+                          ? T2{ld_f64(ref_re, off), ld_f64(ref_re, off + fd.V)}
                           : T2{T(0), T(0)};
             }
           }
@@ -1044,8 +1034,8 @@ __global__ void __launch_bounds__(SD_THREADS, 2) k_gen_scold(const GenArgs a) {
             const long long off = base + (long long)k * nstride;
             if (!eqk::in_bounds(off, fd.V, a.err)) continue;
             const T2 y = tile[k * SD_PITCH + lc];
-            st_elem(out_re, off, y.x, out64);
-            st_elem(out_im, off, y.y, out64);
+            st_dd(out_re, off, y.x, out64);
+            st_dd(out_im, off, y.y, out64);
             if (ref_re) {
               linf = fmax(linf, fabs(rb[u].x - y.x));
               linf = fmax(linf, fabs(rb[u].y - y.y));
