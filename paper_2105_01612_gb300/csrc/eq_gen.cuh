@@ -1141,10 +1141,14 @@ __global__ void __launch_bounds__(XD_THREADS, 2) k_gen_xdd(const GenArgs a) {
 #pragma unroll 1
       for (int ph = 0; ph < 2; ++ph) {
         if (active) {
-          if (ph == 0) {
-            for (int j = lane; j < n; j += 32)
-              row[j] = eqk::in_bounds(roff + j + fd.V, lim, a.err)
-                           ? T2{base[roff + j], base[roff + j + fd.V]} : T2{T(0), T(0)};
+          if (ph == 0) {                  // the row by 8-byte asynchronous copies, all in flight
+            for (int j = lane; j < n; j += 32) {
+              if (eqk::in_bounds(roff + j + fd.V, lim, a.err)) {
+                cp_async8(&row[j].x, base + roff + j);
+                cp_async8(&row[j].y, base + roff + j + fd.V);
+              }
+            }
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
             __syncwarp();
           }
           dd_seq(ph == 1, row, 1, XD_MAXN, n, wm, acc, tw, w512, chs, bhs, a.err);
