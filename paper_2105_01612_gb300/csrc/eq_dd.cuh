@@ -196,13 +196,22 @@ __host__ __device__ __forceinline__ double dd_to_bits(dd x) {
 // double-float passes, while the integer forms take FP32 / integer issue slots): hi = the double
 // rounded to FP32, lo = the exact remainder d - hi rounded to FP32; the way back one FP64 add of
 // the exact widenings.  Beyond FP32's range: infinities with lo = 0.
-__device__ __forceinline__ dd dd_from_f64(double d) {
+__host__ __device__ __forceinline__ dd dd_from_f64(double d) {
+#if defined(__CUDA_ARCH__)
   const float hi = __double2float_rn(d);
   const float lo = ::isfinite(hi) ? __double2float_rn(d - static_cast<double>(hi)) : 0.f;
+#else
+  const float hi = static_cast<float>(d);
+  const float lo = std::isfinite(hi) ? static_cast<float>(d - static_cast<double>(hi)) : 0.f;
+#endif
   return dd(hi, lo);
 }
-__device__ __forceinline__ double dd_to_f64(dd x) {
+__host__ __device__ __forceinline__ double dd_to_f64(dd x) {
+#if defined(__CUDA_ARCH__)
   return __dadd_rn(static_cast<double>(x.hi), static_cast<double>(x.lo));
+#else
+  return static_cast<double>(x.hi) + static_cast<double>(x.lo);
+#endif
 }
 
 // complex double-float (the register and shared-memory type of the FP64 transforms that run in

@@ -47,3 +47,17 @@ def test_special_values(report):
         else:
             assert abs(back - v) <= U48 * abs(v)
     assert report["nan"][0][0] == "1"
+
+
+def test_fp64_instruction_conversions(report):
+    """The FP64-unit forms (used for the last pass's stores and re-read input): round to nearest
+    for hi, the exact remainder rounded for lo (error below 2^-48 relative), the way back exact
+    to one FP64 rounding (agreeing with the bit form); out of FP32's range they give infinities
+    or zero."""
+    assert float(report["conv2"][0][0]) <= U48
+    assert float(report["agree"][0][0]) <= 2.0 ** -52
+    got = {float(v): float(b) for v, b in report["special2"]}
+    assert got[float("inf")] == float("inf")
+    assert got[-1e300] == float("-inf")
+    assert got[1e-300] == 0.0
+
